@@ -1,0 +1,366 @@
+"""Benchmark: synaptic events/s and realtime factor of the work-queue SNN
+timestep on one B300 (or N, one process per GPU).
+
+Default workload: the batched sweep of 256 independent Brunel networks
+(1,000-50,000 neurons, log-uniform; in-degree 10 % capped at 1,000;
+g ~ U[3,7]; nu_ext/nu_thr ~ U[0.9,4]; 15-step delay) with 16-bit weights,
+all stepped together.  One bench "step" is one simulation timestep of every
+network (Update Neurons -> delay FIFO -> Receive Spikes).  The same line
+reports the plain binary32-weight path with the global-atomic receive on
+the same networks, the roofline of the dominant kernel, the end-to-end rate
+through the C ABI from host buffers, and the CPU oracle on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import snn_inputs as si  # noqa: E402
+
+DT_MS = 0.1
+METRIC = "synaptic events/s and realtime factor on 1 B300, batched+int16 vs plain FP32"
+# algorithmic bytes (what the method must move): per delivered event a
+# 4-byte target and a 2-byte (int16) or 4-byte (binary32) weight; per
+# delivered spike its two row offsets (16 B) and its queue entry (4 B); per
+# emitted spike the queue write (4 B) and the log entry (8 B); per neuron and
+# step the state the update reads and writes (Brunel: V 4+4, refractory 1+1,
+# input 4 read + 4 cleared = 18 B; Vogels 44 B; STDP traces +16 B).
+B_EVENT_W16, B_EVENT_F32 = 6, 8
+B_SPIKE_DELIVERED, B_SPIKE_EMITTED = 20, 12
+B_NEURON = {si.BRUNEL: 18, si.VOGELS: 44}
+B_NEURON_STDP = 16
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def workload(name: str, rank: int):
+    if name == "batched_sweep_256":
+        return si.batched_sweep(256, base_seed=1 + 1000 * rank, n_steps=0)
+    if name == "vogels_1m":
+        return si.vogels_1m(seed=1 + rank, n_steps=0)
+    if name == "brunel_12k5":
+        return si.brunel_12k5(seed=1 + rank, n_steps=0)
+    if name == "vogels_4k":
+        return si.vogels_4k(seed=1 + rank, n_steps=0)
+    if name == "brunel_stdp_100k":
+        return si.brunel_stdp_100k(seed=1 + rank, n_steps=0)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def oracle_sample(prob, max_neurons=170_000, max_inst=12):
+    """A deterministic sample of the workload the oracle can step in
+    milliseconds: its first instances (or the whole problem if small)."""
+    if len(prob.instances) == 1:
+        return prob, "the whole network"
+    b, n = 0, 0
+    while b < min(max_inst, len(prob.instances)) and n + prob.instances[b].n <= max_neurons:
+        n += prob.instances[b].n
+        b += 1
+    b = max(b, 1)
+    lo, hi = 0, int(prob.inst_off[b])
+    e1 = int(prob.row_off[hi])
+    sub = si.Problem(model=prob.model, instances=prob.instances[:b], delay=prob.delay, seed=prob.seed, n_steps=0,
+                     stdp=prob.stdp, inst_off=prob.inst_off[:b + 1].copy(), row_off=prob.row_off[:hi + 1].copy(),
+                     tgt=prob.tgt[:e1], w=prob.w[:e1])
+    return sub, f"instances 0-{b - 1} of the sweep ({n} neurons, {e1} synapses)"
+
+
+def cpu_baseline(prob, steps: int, target_s: float = 15.0):
+    import oracle
+    sub, desc = oracle_sample(prob)
+    sub.n_steps = 200
+    t0 = time.perf_counter()
+    r = oracle.run(sub)
+    dt = time.perf_counter() - t0
+    if dt < target_s / 4:
+        sub.n_steps = int(min(steps, 200 * target_s / max(dt, 1e-3)))
+        t0 = time.perf_counter()
+        r = oracle.run(sub)
+        dt = time.perf_counter() - t0
+    return {"value": r["events"] / dt, "unit": "synaptic events/s", "cores": 1, "kind": "oracle",
+            "sample": f"{desc}, {sub.n_steps} steps from step 0, single-threaded C oracle",
+            "seconds": round(dt, 3), "realtime_factor": sub.n_steps * DT_MS * 1e-3 / dt}
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def delivered_spikes(net, prob, t0: int, t1: int) -> int:
+    """Spikes delivered by the receives of steps [t0, t1) (queue S_{t-d+1})."""
+    a, b = max(0, t0 - prob.delay + 1), max(0, t1 - prob.delay + 1)
+    if b <= a:
+        return 0
+    steps, _ = net.spikes(a, b)
+    return len(steps)
+
+
+def step_bytes(prob, w16: bool, events: int, delivered: int, emitted: int, steps: int) -> float:
+    per_neuron = B_NEURON[prob.model] + (B_NEURON_STDP if prob.stdp else 0)
+    return (events * (B_EVENT_W16 if w16 else B_EVENT_F32) + delivered * B_SPIKE_DELIVERED +
+            emitted * B_SPIKE_EMITTED + per_neuron * prob.n * steps)
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    import paper_1912_07423_b300 as snn
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    t_gen = time.perf_counter()
+    prob = workload(args.workload, rank)
+    t_gen = time.perf_counter() - t_gen
+    hbm, peak_kind = peaks()
+    cap = int(prob.n * (args.warmup + args.steps + args.profile_steps) * 0.05) + (1 << 20)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def timed(net, steps):
+        stream = net.stream
+        c0 = net.counters()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        net.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        net.sync()
+        c1 = net.counters()
+        return e0.elapsed_time(e1) / 1e3, c1["events"] - c0["events"], c1["spikes"] - c0["spikes"]
+
+    # ---- headline: batched + int16, timed on the device
+    net = snn.Network(prob, w16=True, receive=snn.RECV_AUTO, log_capacity=cap)
+    info = net.info()
+    recv_kind = info["receive"]
+    net.step(args.warmup)
+    net.sync()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    t_main, ev_main, sp_main = timed(net, args.steps)
+    clk = clocks.stop()
+    t_a = args.warmup
+    deliv_main = delivered_spikes(net, prob, t_a, t_a + args.steps)
+    # ---- per-kernel times (CUDA events around every kernel, same stream)
+    n_prof = min(args.steps, args.profile_steps)
+    c0 = net.counters()
+    phases = net.step_profiled(n_prof)
+    c1 = net.counters()
+    t_p0 = t_a + args.steps
+    ev_p, sp_p = c1["events"] - c0["events"], c1["spikes"] - c0["spikes"]
+    deliv_p = delivered_spikes(net, prob, t_p0, t_p0 + n_prof)
+    mem = info["device_bytes"]
+    net.close()
+    del net
+    torch.cuda.empty_cache()
+
+    t_max = max_over_ranks(t_main)
+    ev_total = sum_over_ranks(ev_main)
+    value = ev_total / t_max
+    recv_ms = phases["receive"] / n_prof
+    recv_bytes = (ev_p * B_EVENT_W16 + deliv_p * B_SPIKE_DELIVERED) / n_prof
+    achieved = recv_bytes / (recv_ms * 1e-3) / 1e9
+    step_b = step_bytes(prob, True, ev_main, deliv_main, sp_main, args.steps)
+    step_frac = (step_b / (hbm * 1e9)) / t_main
+
+    out = {"metric": METRIC, "value": value, "unit": "synaptic events/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "int16 weights, int32 input, f32 state",
+           "data": "synthetic (seeded graphs, no dataset)",
+           "config": {"workload": args.workload, "networks": len(prob.instances), "neurons": prob.n,
+                      "synapses": prob.n_edges, "delay_steps": prob.delay, "dt_ms": DT_MS,
+                      "receive": recv_kind, "tiles": info["n_tiles"], "weights": "int16 x 2^shift(row)",
+                      "l2": "inputs larger than L2 (edge arrays %.1f GB >> 126 MB)" % (prob.n_edges * 6 / 1e9),
+                      "parallelism": f"replicas x{world} (independent networks, no collective)",
+                      "graph_gen_s": round(t_gen, 1), "device_bytes": mem},
+           "realtime_factor": args.steps * DT_MS * 1e-3 / t_max,
+           "spikes": int(sp_main), "events": int(ev_main),
+           "roofline": {"kernel": f"k_receive_{recv_kind}", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                        "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
+                        "traffic": None, "launch_ms": recv_ms,
+                        "bytes_per_launch": recv_bytes, "launches": n_prof},
+           "step_roofline": {"bytes_per_step": step_b / args.steps, "frac": step_frac, "peak": hbm,
+                             "unit": "GB/s", "achieved": step_b / t_main / 1e9},
+           "phase_ms_per_step": {k: v / n_prof for k, v in phases.items()},
+           "gpu_launches": int(args.steps * (3 if not prob.stdp else 5)),
+           "clocks": clk}
+
+    # ---- plain single-precision weights + global-atomic receive, same networks
+    if not args.no_plain:
+        net = snn.Network(prob, w16=False, receive=snn.RECV_GLOBAL, log_capacity=cap)
+        net.step(args.warmup)
+        net.sync()
+        t_pl, ev_pl, sp_pl = timed(net, args.steps)
+        net.close()
+        del net
+        torch.cuda.empty_cache()
+        out["plain_fp32"] = {"value": sum_over_ranks(ev_pl) / max_over_ranks(t_pl), "unit": "synaptic events/s",
+                             "receive": "global", "weights": "binary32",
+                             "ms_per_step": t_pl * 1e3 / args.steps,
+                             "realtime_factor": args.steps * DT_MS * 1e-3 / t_pl}
+        out["speedup_vs_plain_fp32"] = out["value"] / out["plain_fp32"]["value"]
+
+    # ---- end to end through the C ABI from host buffers
+    if not args.no_e2e:
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        net = snn.Network(prob, w16=True, receive=snn.RECV_AUTO, log_capacity=cap)  # h2d of the graph
+        net.step(args.steps)
+        steps_h, ids_h = net.spikes()  # d2h of the raster
+        t_e2e = time.perf_counter() - t0
+        c = net.counters()
+        net.close()
+        del net
+        torch.cuda.empty_cache()
+        h2d = prob.row_off.nbytes + prob.tgt.nbytes + prob.w.nbytes
+        d2h = 8 * int(c["spikes"])
+        out["e2e"] = {"value": sum_over_ranks(c["events"]) / max_over_ranks(t_e2e), "unit": "synaptic events/s",
+                      "seconds": t_e2e, "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                      "includes": "snn_create + snn_build_graph from host arrays + snn_step(K) + snn_read_spikes"}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(prob, args.steps)
+    return out
+
+
+def run_reference(args, rank):
+    """The oracle, as it stands, on a bounded sample of the same workload,
+    on the host cores."""
+    import oracle
+    prob = workload(args.workload, rank)
+    sub, desc = oracle_sample(prob)
+    sub.n_steps = args.warmup + args.steps
+    t0 = time.perf_counter()
+    r = oracle.run(sub)
+    dt = time.perf_counter() - t0
+    value = r["events"] / dt
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "synaptic events/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / sub.n_steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 state, int32 input",
+            "data": "synthetic (seeded graphs, no dataset)",
+            "config": {"workload": args.workload, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "synaptic events/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{desc}, {sub.n_steps} steps"},
+            "e2e": {"value": value, "unit": "synaptic events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="batched_sweep_256")
+    ap.add_argument("--profile-steps", type=int, default=500)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank)), flush=True)
+        return
+
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    out = run_ours(args, rank, world, dist)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

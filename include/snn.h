@@ -1,0 +1,217 @@
+/*
+ * snn.h -- C ABI of the B300 work-queue SNN library (libsnn.so).
+ *
+ * The library simulates a directed graph of leaky integrate-and-fire
+ * neurons, clock-driven, one timestep at a time, and returns its firing
+ * pattern.  The problem statement follows the paper: neurons and synapses
+ * with weights and a synaptic delay, simulated for T steps, whose output is
+ * the spike raster (Section I; Section III-A-1).  One timestep is the
+ * paper's pipeline (Fig. 1):
+ *   Update Neurons   -- every neuron is advanced from N_t to N'_{t+1}; the
+ *                       ids of the neurons that spike go to the spike queue
+ *                       S_t (Section III-A-1, III-A-2: an array with an
+ *                       atomic insertion index),
+ *   delay FIFO       -- S_t waits in a ring of d queues (d+1 with
+ *                       plasticity) (Section III-A-1),
+ *   Update Synapses  -- with plasticity, pair STDP from S_{t-d} (pre) and
+ *                       S_t (post) (Section III-A-1),
+ *   Receive Spikes   -- every spike of S_{t-d+1} is delivered along its
+ *                       out-edge row into the input accumulators of its
+ *                       targets (Section III-A-2: sorted adjacency rows).
+ * Many independent networks ("instances") of uneven size are stepped
+ * together over one concatenated graph.
+ *
+ * Units and exactness.  Synaptic weights are int32 multiples of 2^-16 mV
+ * (the lattice); input accumulates in int32 in any order with the same
+ * result.  The neuron update is a fixed binary32 operation sequence without
+ * fused multiply-add, so two runs of the same input give the same raster
+ * and state bit for bit.
+ *
+ * Threading.  A context is used by one host thread at a time.  All device
+ * work is enqueued on the stream given at creation; calls that return data
+ * to the host synchronise that stream.
+ *
+ * Errors.  Every call returns an snn_status; no exception crosses the ABI.
+ * snn_last_error() gives a one-line description of the last failure.
+ */
+#ifndef SNN_H
+#define SNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct snn_ctx snn_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    SNN_OK = 0,
+    SNN_E_ARG = -1,      /* invalid argument; nothing was changed */
+    SNN_E_NOMEM = -2,    /* a device or host allocation failed */
+    SNN_E_CUDA = -3,     /* a CUDA call failed; the context is unusable */
+    SNN_E_OVERFLOW = -4, /* the spike log filled up; the simulation itself is intact */
+    SNN_E_TIMEOUT = -5,  /* a bounded device-side wait gave up */
+    SNN_E_STATE = -6     /* call out of order (e.g. snn_step before snn_build_graph) */
+} snn_status;
+
+typedef enum {
+    SNN_VOGELS_CUBA = 0, /* LIF with exponential exc/inh currents and constant drive (Section IV) */
+    SNN_BRUNEL = 1       /* LIF with delta synapses and Poisson drive (Section IV) */
+} snn_model;
+
+/* snn_config.flags */
+#define SNN_F_STDP 1u  /* pair STDP on exc -> exc synapses (Brunel only; "Brunel+") */
+#define SNN_F_W16 2u   /* weights stored as int16 codes x 2^shift(row); else binary32 */
+#define SNN_F_STATS 4u /* keep per-neuron spike counts and ISI moments for snn_stats */
+
+/* snn_config.receive */
+#define SNN_RECV_AUTO 0u   /* the library picks: tiled when the rows are sorted, else global */
+#define SNN_RECV_GLOBAL 1u /* warp per spike, red.global.add into L2-resident accumulators */
+#define SNN_RECV_TILED 2u  /* target-tiled, accumulators in shared memory; needs sorted rows */
+
+typedef struct {
+    uint32_t model;        /* snn_model */
+    uint32_t flags;        /* SNN_F_* */
+    uint32_t delay;        /* d >= 1 steps; a spike of step t reaches the update of step t+d */
+    uint32_t n_inst;       /* number of network instances, >= 1 */
+    uint64_t seed;         /* Philox key word 0 (word 1 is the instance index) */
+    uint64_t log_capacity; /* spikes the raster log keeps (0: no log) */
+    uint32_t receive;      /* SNN_RECV_* */
+    uint32_t steps_per_graph; /* steps captured per CUDA graph (0: library default) */
+} snn_config;
+
+/* Model constants of one instance.  Times in ms, potentials in mV, integer
+ * weights in lattice units (2^-16 mV).  Every binary32 constant the update
+ * uses is the binary64 expression below rounded once to nearest. */
+typedef struct {
+    uint32_t n;                /* neurons of this instance (local ids 0..n-1) */
+    uint32_t n_exc;            /* local ids < n_exc are excitatory */
+    uint32_t refractory_steps; /* R <= 255: steps clamped at v_reset after a spike */
+    int32_t jext_q;            /* Brunel: lattice units per external Poisson spike */
+    int32_t w_max_q;           /* STDP: plastic weights are clipped to [0, w_max_q] */
+    uint32_t reserved;
+    double dt, tau_m;          /* Pm = exp(-dt/tau_m) */
+    double v_th, v_reset;
+    double e_l, tau_e, tau_i;  /* Vogels: resting drive, Pe = exp(-dt/tau_e), Pi = exp(-dt/tau_i) */
+    double lambda;             /* Brunel: Poisson mean of external spikes per step */
+    double v0_lo, v0_span;     /* V0 = v0_lo + v0_span * u, u uniform on [0,1) in steps of 2^-24 */
+    double tau_plus, tau_minus;/* STDP trace time constants */
+    double a_plus, a_minus;    /* STDP amplitudes as fractions of w_max_q */
+} snn_params;
+
+/* Device memory and stream.  alloc/free may be NULL (then cudaMalloc and
+ * cudaFree are used).  stream is a cudaStream_t (NULL: the legacy default
+ * stream).  The library calls alloc/free only inside snn_create,
+ * snn_build_graph and snn_destroy. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* user);
+    void (*free)(void* ptr, void* stream, void* user);
+    void* user;
+    void* stream;
+} snn_device;
+
+/* Create a context for n_inst instances (params is an array of n_inst).
+ * The instances are concatenated in order: global neuron id = sum of the
+ * sizes of the earlier instances + local id.  Returns SNN_E_ARG for an
+ * invalid config (delay 0 or > 1000, refractory > 255, STDP without
+ * Brunel, non-positive time constants, lambda < 0 or so large that the
+ * Poisson table would exceed 64 entries).  *out is NULL on failure. */
+snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn_device* dev,
+                      snn_ctx** out);
+
+/* Load the graph (host pointers; the library copies them and keeps no
+ * reference).  row_off[N+1] are CSR row offsets over global neuron ids
+ * (row_off[0] == 0, non-decreasing), tgt[E] the targets of each row, w_q[E]
+ * the weights in lattice units.  Targets must lie in the source's instance.
+ * With SNN_F_W16 every row must be representable as int16 codes times one
+ * power of two, 2^s with s <= 15 (plastic rows with s == 0); without it
+ * every weight must satisfy |w| <= 2^24.  Rows need not be sorted; sorted
+ * rows give better locality (Section III-A-2).  Violations give SNN_E_ARG
+ * and leave no graph loaded.  On success the neuron state is initialised
+ * (the paper's Init stage, Fig. 1) and the step counter is 0. */
+snn_status snn_build_graph(snn_ctx* ctx, const uint64_t* row_off, const uint32_t* tgt, const int32_t* w_q);
+
+/* (Re)initialise the neuron state N_0 and restore the weights loaded by
+ * snn_build_graph; the step counter returns to 0 and the log is cleared. */
+snn_status snn_reset(snn_ctx* ctx);
+
+/* Enqueue n_steps timesteps on the context's stream and return without
+ * waiting.  Device-side errors surface at the next call that synchronises. */
+snn_status snn_step(snn_ctx* ctx, uint32_t n_steps);
+
+/* Run n_steps timesteps without the CUDA graph, with CUDA events around
+ * every kernel of the step, and wait for them.  phase_ms[5] receives the
+ * summed device time of each phase: [0] Update Synapses (depression),
+ * [1] Update Neurons, [2] Update Synapses (potentiation), [3] Receive
+ * Spikes, [4] end-of-step bookkeeping.  Used to measure one kernel's share
+ * of the step; the simulation advances exactly as with snn_step. */
+snn_status snn_step_profiled(snn_ctx* ctx, uint32_t n_steps, double* phase_ms);
+
+/* Wait for the enqueued work; returns the first pending device-side error. */
+snn_status snn_sync(snn_ctx* ctx);
+
+/* Spikes of steps [t0, t1) from the raster log, sorted by (step, global
+ * id), written to steps[] and ids[] (each of capacity cap).  *n_out gets the
+ * number of such spikes; with cap == 0 only the count is returned, with
+ * cap < count SNN_E_OVERFLOW is returned and nothing is written.
+ * Synchronises. */
+snn_status snn_read_spikes(snn_ctx* ctx, uint32_t t0, uint32_t t1, uint32_t* steps, uint32_t* ids,
+                           uint64_t cap, uint64_t* n_out);
+
+/* Drop the logged spikes; logging continues from the current step. */
+snn_status snn_log_clear(snn_ctx* ctx);
+
+/* State fields for snn_read_state / snn_write_state (N entries in global
+ * id order unless noted). */
+typedef enum {
+    SNN_FIELD_V = 0,    /* float, mV */
+    SNN_FIELD_GE = 1,   /* float, mV (Vogels) */
+    SNN_FIELD_GI = 2,   /* float, mV (Vogels) */
+    SNN_FIELD_R = 3,    /* int32, refractory steps left */
+    SNN_FIELD_X = 4,    /* float, presynaptic STDP trace */
+    SNN_FIELD_Y = 5,    /* float, postsynaptic STDP trace */
+    SNN_FIELD_ACC0 = 6, /* int32, pending input (channel 0: excitatory / all) */
+    SNN_FIELD_ACC1 = 7, /* int32, pending input (channel 1: Vogels inhibitory) */
+    SNN_FIELD_W = 8     /* int32[E], weights in lattice units, CSR order of snn_build_graph */
+} snn_field;
+
+/* Copy a state field to / from host memory (synchronises).  Writing takes
+ * effect before the next step; it is how tests force a spike.  The queues
+ * of the delay FIFO are not part of these fields. */
+snn_status snn_read_state(snn_ctx* ctx, snn_field field, void* host);
+snn_status snn_write_state(snn_ctx* ctx, snn_field field, const void* host);
+
+/* Counters since the last reset: steps done, spikes emitted and synaptic
+ * events delivered (sum of the row lengths of the delivered spikes). */
+snn_status snn_counters(snn_ctx* ctx, uint64_t* steps, uint64_t* spikes, uint64_t* events);
+
+/* Population rate (Hz) of one instance since the statistics window began
+ * (step 0 or the last snn_stats_clear), and the mean ISI coefficient of
+ * variation over its neurons with at least 3 spikes in the window (needs
+ * SNN_F_STATS; reductions in binary64 on the device). */
+snn_status snn_stats(snn_ctx* ctx, uint32_t inst, double* rate_hz, double* isi_cv);
+
+/* Start the statistics window at the current step. */
+snn_status snn_stats_clear(snn_ctx* ctx);
+
+/* What the context chose and holds. */
+typedef struct {
+    uint32_t receive;      /* SNN_RECV_GLOBAL or SNN_RECV_TILED (after snn_build_graph) */
+    uint32_t n_tiles;      /* target tiles of the tiled receive (0: global) */
+    uint32_t n_padded;     /* neuron slots on the device (instances padded to 256) */
+    uint32_t rows_sorted;  /* 1 if every row's targets ascend */
+    uint64_t edges;        /* synapses loaded */
+    uint64_t device_bytes; /* device memory held */
+} snn_info;
+snn_status snn_get_info(snn_ctx* ctx, snn_info* info);
+
+const char* snn_last_error(const snn_ctx* ctx); /* never NULL; ctx may be NULL */
+const char* snn_status_string(snn_status s);
+void snn_destroy(snn_ctx* ctx); /* NULL-safe */
+
+#ifdef __cplusplus
+}
+#endif
+#endif

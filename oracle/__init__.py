@@ -63,7 +63,8 @@ class _Problem(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("stdp", ctypes.c_int32), ("n_inst", ctypes.c_uint32),
                 ("delay", ctypes.c_uint32), ("inst_off", _vp), ("params", _vp), ("seed", ctypes.c_uint64),
                 ("row_off", _vp), ("tgt", _vp), ("w", _vp), ("n_steps", ctypes.c_uint32),
-                ("n_over", ctypes.c_uint32), ("over_step", _vp), ("over_id", _vp), ("over_v", _vp)]
+                ("n_over", ctypes.c_uint32), ("over_step", _vp), ("over_id", _vp), ("over_v", _vp),
+                ("inst_key0", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 class _State(ctypes.Structure):
@@ -138,7 +139,7 @@ def poisson_sample(T: np.ndarray, u: int) -> int:
 class _Marshalled:
     """Keeps the numpy buffers alive while C holds pointers into them."""
 
-    def __init__(self, prob, overrides=None):
+    def __init__(self, prob, overrides=None, inst_key0=0):
         B = len(prob.instances)
         self.params = (_Params * B)()
         for b, inst in enumerate(prob.instances):
@@ -163,6 +164,7 @@ class _Marshalled:
         P.row_off, P.tgt, P.w, P.n_steps = _ptr(self.row_off), _ptr(self.tgt), _ptr(self.w), prob.n_steps
         P.n_over = len(ov)
         P.over_step, P.over_id, P.over_v = _ptr(self.over_step), _ptr(self.over_id), _ptr(self.over_v)
+        P.inst_key0 = inst_key0
         self.P = P
 
 
@@ -174,16 +176,18 @@ def _take_raster(lib, R):
     return steps, ids
 
 
-def run(prob, overrides=None, state=None) -> dict:
+def run(prob, overrides=None, state=None, inst_key0: int = 0) -> dict:
     """Simulate prob.n_steps steps in binary32.
 
     overrides: list of (step, neuron, V) applied before that step's update.
     state: optional dict of initial arrays (V, ge, gi, r, x, y, acc0, acc1,
     w); default draws N_0 as documented in snn_oracle.c.
+    inst_key0: Philox instance key of the problem's first instance (to re-run
+    instance b of a batch alone, pass a one-instance problem and b).
     Returns the raster (steps, ids sorted by (step, id)), the delivered event
     count and the final state."""
     lib = _load()
-    m = _Marshalled(prob, overrides)
+    m = _Marshalled(prob, overrides, inst_key0)
     N, E = prob.n, prob.n_edges
     st = {
         "V": np.zeros(N, np.float32), "ge": np.zeros(N, np.float32), "gi": np.zeros(N, np.float32),

@@ -49,7 +49,8 @@
  *     pmf recursion p_k = p_{k-1} lambda / k in binary64), u one 32-bit
  *     Philox word per neuron per step.
  *   - Random words: Philox4x64-10 (Salmon et al., SC'11), key = (seed,
- *     instance), counter = (local_neuron >> 3, step, tag, 0); the word for a
+ *     instance; a problem may start its instance count at inst_key0 so that
+ *     one network of a batch can be re-run alone), counter = (local_neuron >> 3, step, tag, 0); the word for a
  *     neuron is 32-bit half (local & 7) of the 256-bit block, low half first.
  *     tag 0 draws the initial potential (step 0), tag 1 the Poisson drive.
  *   - Initial state: V0 = v0_lo + v0_span*u01, u01 = (word >> 8)*2^-24.
@@ -291,7 +292,7 @@ int orc_run(const orc_problem* P, orc_state* S, orc_raster* R)
     if (!S->init_given) {
         for (uint32_t b = 0; b < P->n_inst; ++b)
             for (uint32_t i = P->inst_off[b]; i < P->inst_off[b + 1]; ++i) {
-                uint32_t u = orc_rand_word(P->seed, b, i - P->inst_off[b], 0, 0);
+                uint32_t u = orc_rand_word(P->seed, P->inst_key0 + b, i - P->inst_off[b], 0, 0);
                 float u01 = (float)(u >> 8) * (1.0f / 16777216.0f);
                 float t = C[b].v0_span * u01;
                 S->V[i] = C[b].v0_lo + t;
@@ -387,7 +388,7 @@ int orc_run(const orc_problem* P, orc_state* S, orc_raster* R)
                         r -= 1;
                         V = c->v_reset;
                     } else {
-                        uint32_t u = orc_rand_word(P->seed, b, i - P->inst_off[b], t, 1);
+                        uint32_t u = orc_rand_word(P->seed, P->inst_key0 + b, i - P->inst_off[b], t, 1);
                         int64_t n_ext = orc_poisson_sample(c->T, c->nT, u);
                         int64_t I = acc0[i] + n_ext * (int64_t)p->jext_q;
                         if (I > INT32_MAX || I < INT32_MIN) { st = ORC_E_RANGE; goto done; }
@@ -510,7 +511,7 @@ int orc_run_f64(const orc_problem* P, const double* w_mV, double* V_out, orc_ras
         nT[b] = orc_poisson_table(P->params[b].lambda, T + (size_t)b * ORC_POISSON_CAP, ORC_POISSON_CAP);
         if (nT[b] < 0) { st = ORC_E_ARG; goto done; }
         for (uint32_t i = P->inst_off[b]; i < P->inst_off[b + 1]; ++i) {
-            uint32_t u = orc_rand_word(P->seed, b, i - P->inst_off[b], 0, 0);
+            uint32_t u = orc_rand_word(P->seed, P->inst_key0 + b, i - P->inst_off[b], 0, 0);
             V[i] = P->params[b].v0_lo + P->params[b].v0_span * ((double)(u >> 8) / 16777216.0);
         }
     }
@@ -540,7 +541,7 @@ int orc_run_f64(const orc_problem* P, const double* w_mV, double* V_out, orc_ras
                         r[i] -= 1;
                         V[i] = p->v_reset;
                     } else {
-                        uint32_t u = orc_rand_word(P->seed, b, i - P->inst_off[b], t, 1);
+                        uint32_t u = orc_rand_word(P->seed, P->inst_key0 + b, i - P->inst_off[b], t, 1);
                         double n_ext = orc_poisson_sample(T + (size_t)b * ORC_POISSON_CAP, nT[b], u);
                         V[i] = V[i] * Pm + in0[i] + n_ext * p->jext_q / 65536.0;
                         if (V[i] >= p->v_th) spike = 1;

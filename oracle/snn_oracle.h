@@ -45,6 +45,8 @@ typedef struct {
     const uint32_t* over_step;
     const uint32_t* over_id;
     const float* over_v;
+    uint32_t inst_key0; /* Philox key word 1 of instance b is inst_key0 + b */
+    uint32_t pad;
 } orc_problem;
 
 /* Neuron and synapse state; arrays of N (w: E) owned by the caller. */

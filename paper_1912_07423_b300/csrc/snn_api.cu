@@ -1,0 +1,930 @@
+// snn_api.cu -- host side of the libsnn C ABI (include/snn.h).
+//
+// The context owns the device arrays described in snn_device.cuh.  A
+// timestep is a fixed sequence of kernel launches that read the step index
+// from the device control block, so the sequence is captured once into a
+// CUDA graph (several steps per graph) and replayed by snn_step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/snn.h"
+#include "snn_device.cuh"
+#include "snn_kernels.cuh"
+#include "snn_tiled.cuh"
+
+using namespace snn;
+
+struct snn_ctx {
+    snn_config cfg{};
+    std::vector<snn_params> params;
+    snn_device dev{};
+    cudaStream_t stream = nullptr;   // user stream (may be the legacy default)
+    cudaStream_t cap_stream = nullptr;
+    std::string err;
+
+    // sizes and host mirrors of the layout
+    uint32_t N = 0, Np = 0, D = 0;
+    uint64_t E = 0;
+    std::vector<uint32_t> g_off;   // global instance offsets (n_inst+1)
+    std::vector<uint32_t> pbase;   // padded bases (n_inst+1)
+    bool vogels = false, stdp = false, w16 = false, stats = false;
+    bool graph_loaded = false;
+    uint64_t host_steps = 0;       // steps enqueued since reset
+
+    // device allocations
+    struct Alloc {
+        void* p;
+        size_t bytes;
+    };
+    std::vector<Alloc> allocs;
+    size_t bytes_held = 0;
+
+    Net net{};
+    Ctl* ctl = nullptr;
+    uint32_t cr = 0;               // count-ring length
+    bool rows_sorted = true;
+    InstDev* inst = nullptr;
+    uint32_t* inst_of_w32 = nullptr;
+    uint32_t* pois = nullptr;
+    uint64_t* roff = nullptr;
+    uint32_t* tgt = nullptr;
+    int16_t* w16p = nullptr;
+    float* w32p = nullptr;
+    int32_t* w_init = nullptr;     // weights at load time (lattice), for snn_reset with STDP
+    uint8_t* meta = nullptr;
+    uint64_t* coff = nullptr;
+    uint32_t* cedge = nullptr;
+    uint32_t* cpre = nullptr;
+    TiledPlan tiled{};
+    bool use_tiled = false;
+
+    // CUDA graphs: one step, and steps_per_graph steps
+    cudaGraphExec_t g1 = nullptr, gk = nullptr;
+    uint32_t k_steps = 0;
+};
+
+namespace {
+
+snn_status fail(snn_ctx* c, snn_status s, const char* fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define CUDA_TRY(c, call)                                                                         \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return fail(c, SNN_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+void* dev_alloc(snn_ctx* c, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (c->dev.alloc) {
+        p = c->dev.alloc(bytes, c->dev.stream, c->dev.user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        c->allocs.push_back({p, bytes});
+        c->bytes_held += bytes;
+    }
+    return p;
+}
+
+void dev_free(snn_ctx* c, void* p)
+{
+    if (!p) return;
+    for (size_t i = 0; i < c->allocs.size(); ++i)
+        if (c->allocs[i].p == p) {
+            c->bytes_held -= c->allocs[i].bytes;
+            c->allocs.erase(c->allocs.begin() + i);
+            if (c->dev.free)
+                c->dev.free(p, c->dev.stream, c->dev.user);
+            else
+                cudaFree(p);
+            return;
+        }
+}
+
+template <class T>
+T* alloc_n(snn_ctx* c, size_t n)
+{
+    return static_cast<T*>(dev_alloc(c, n * sizeof(T)));
+}
+
+// Poisson thresholds T_k = floor(CDF(k) * 2^32) while below 2^32 - 1, with
+// the CDF summed from p_k = p_{k-1} * lambda / k in binary64.
+int poisson_table(double lambda, uint32_t* T, int cap)
+{
+    double p = std::exp(-lambda);
+    double cdf = p;
+    int n = 0;
+    for (int k = 0; k < 1000000; ++k) {
+        if (k > 0) {
+            p = p * lambda / (double)k;
+            cdf = cdf + p;
+        }
+        const double s = std::floor(cdf * 4294967296.0);
+        if (s >= 4294967295.0) return n;
+        if (n == cap) return -1;
+        T[n++] = (uint32_t)s;
+    }
+    return -1;
+}
+
+InstDev make_inst(const snn_params& p, uint32_t pbase, uint32_t pois_off, int pois_n)
+{
+    InstDev d{};
+    d.pbase = pbase;
+    d.n = p.n;
+    d.n_exc = p.n_exc;
+    d.R = p.refractory_steps;
+    d.jext = p.jext_q;
+    d.wmax = p.w_max_q;
+    d.pois_off = pois_off;
+    d.pois_n = (uint32_t)pois_n;
+    d.Pm = (float)std::exp(-p.dt / p.tau_m);
+    d.Pe = (float)(p.tau_e > 0 ? std::exp(-p.dt / p.tau_e) : 0.0);
+    d.Pi = (float)(p.tau_i > 0 ? std::exp(-p.dt / p.tau_i) : 0.0);
+    d.Pp = (float)(p.tau_plus > 0 ? std::exp(-p.dt / p.tau_plus) : 0.0);
+    d.Pn = (float)(p.tau_minus > 0 ? std::exp(-p.dt / p.tau_minus) : 0.0);
+    d.Ap = (float)(p.a_plus * (double)p.w_max_q);
+    d.Am = (float)(p.a_minus * (double)p.w_max_q);
+    d.v_th = (float)p.v_th;
+    d.v_reset = (float)p.v_reset;
+    d.e_l = (float)p.e_l;
+    d.v0_lo = (float)p.v0_lo;
+    d.v0_span = (float)p.v0_span;
+    return d;
+}
+
+uint32_t grid_for(uint64_t threads, uint32_t block) { return (uint32_t)std::max<uint64_t>(1, (threads + block - 1) / block); }
+
+int sm_count()
+{
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+// The kernels of one timestep, in pipeline order (Fig. 1).  ev, if given,
+// holds 6 events recorded between the phases.
+snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr)
+{
+    const Net& n = c->net;
+    if (ev) cudaEventRecord(ev[0], s);
+    const uint32_t ublocks = grid_for(c->Np / 8, 256);
+    const uint32_t wblocks = (uint32_t)sm_count() * 8;
+    if (c->stdp) {
+        if (c->w16)
+            k_stdp_depress<true><<<wblocks, 256, 0, s>>>(n);
+        else
+            k_stdp_depress<false><<<wblocks, 256, 0, s>>>(n);
+    }
+    if (ev) cudaEventRecord(ev[1], s);
+    if (c->vogels) {
+        if (c->stats)
+            k_update<0, false, true><<<ublocks, 256, 0, s>>>(n);
+        else
+            k_update<0, false, false><<<ublocks, 256, 0, s>>>(n);
+    } else if (c->stdp) {
+        if (c->stats)
+            k_update<1, true, true><<<ublocks, 256, 0, s>>>(n);
+        else
+            k_update<1, true, false><<<ublocks, 256, 0, s>>>(n);
+    } else {
+        if (c->stats)
+            k_update<1, false, true><<<ublocks, 256, 0, s>>>(n);
+        else
+            k_update<1, false, false><<<ublocks, 256, 0, s>>>(n);
+    }
+    if (ev) cudaEventRecord(ev[2], s);
+    if (c->stdp) {
+        if (c->w16)
+            k_stdp_potentiate<true><<<wblocks, 256, 0, s>>>(n);
+        else
+            k_stdp_potentiate<false><<<wblocks, 256, 0, s>>>(n);
+    }
+    if (ev) cudaEventRecord(ev[3], s);
+    if (c->use_tiled) {
+        CUDA_TRY(c, enqueue_tiled_receive(c->tiled, n, c->w16, s));
+    } else if (c->w16) {
+        k_receive_global<true><<<wblocks, 256, 0, s>>>(n);
+    } else {
+        k_receive_global<false><<<wblocks, 256, 0, s>>>(n);
+    }
+    if (ev) cudaEventRecord(ev[4], s);
+    k_step_end<<<1, 256, 0, s>>>(n);
+    if (ev) cudaEventRecord(ev[5], s);
+    CUDA_TRY(c, cudaGetLastError());
+    return SNN_OK;
+}
+
+snn_status capture(snn_ctx* c, uint32_t steps, cudaGraphExec_t* out)
+{
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    snn_status st = SNN_OK;
+    for (uint32_t i = 0; i < steps && st == SNN_OK; ++i) st = enqueue_step(c, c->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (st != SNN_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(c, SNN_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(c, SNN_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return SNN_OK;
+}
+
+void drop_graphs(snn_ctx* c)
+{
+    if (c->g1) cudaGraphExecDestroy(c->g1);
+    if (c->gk) cudaGraphExecDestroy(c->gk);
+    c->g1 = c->gk = nullptr;
+}
+
+snn_status check_device_errors(snn_ctx* c)
+{
+    unsigned int err = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&err, &c->ctl->err, sizeof err, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (err & kErrTimeout) return fail(c, SNN_E_TIMEOUT, "a bounded device-side wait gave up");
+    if (err & kErrLogOverflow)
+        return fail(c, SNN_E_OVERFLOW, "the spike log is full (log_capacity = %llu)",
+                    (unsigned long long)c->cfg.log_capacity);
+    return SNN_OK;
+}
+
+snn_status init_state(snn_ctx* c)
+{
+    k_init_state<<<grid_for(c->Np / 8, 256), 256, 0, c->stream>>>(c->net, c->vogels ? 1 : 0, c->stdp ? 1 : 0);
+    CUDA_TRY(c, cudaGetLastError());
+    // control block: step 0, empty queues and log
+    CUDA_TRY(c, cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), c->stream));
+    if (c->stdp)
+        CUDA_TRY(c, cudaMemsetAsync(c->net.bits, 0, (size_t)c->D * (c->Np / 32) * sizeof(uint32_t), c->stream));
+    if (c->stats) {
+        CUDA_TRY(c, cudaMemsetAsync(c->net.st_cnt, 0, (size_t)c->Np * 4, c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(c->net.st_sum, 0, (size_t)c->Np * 8, c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(c->net.st_sq, 0, (size_t)c->Np * 8, c->stream));
+    }
+    CUDA_TRY(c, cudaMemsetAsync(c->net.count, 0, (size_t)c->cr * 4, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->net.icount, 0, (size_t)c->cr * c->cfg.n_inst * 4, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->net.lbase, 0, (size_t)c->cr * 8, c->stream));
+    c->host_steps = 0;
+    return SNN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* snn_status_string(snn_status s)
+{
+    switch (s) {
+    case SNN_OK: return "ok";
+    case SNN_E_ARG: return "invalid argument";
+    case SNN_E_NOMEM: return "out of memory";
+    case SNN_E_CUDA: return "CUDA error";
+    case SNN_E_OVERFLOW: return "overflow";
+    case SNN_E_TIMEOUT: return "device-side timeout";
+    case SNN_E_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+const char* snn_last_error(const snn_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn_device* dev, snn_ctx** out)
+{
+    if (!out) return SNN_E_ARG;
+    *out = nullptr;
+    if (!cfg || !params || cfg->n_inst == 0) return SNN_E_ARG;
+    if (cfg->model > SNN_BRUNEL || cfg->delay < 1 || cfg->delay > 1000) return SNN_E_ARG;
+    if ((cfg->flags & SNN_F_STDP) && cfg->model != SNN_BRUNEL) return SNN_E_ARG;
+    if (cfg->receive > SNN_RECV_TILED) return SNN_E_ARG;
+    uint64_t N = 0, Np = 0;
+    for (uint32_t b = 0; b < cfg->n_inst; ++b) {
+        const snn_params& p = params[b];
+        if (p.n_exc > p.n || p.refractory_steps > 255) return SNN_E_ARG;
+        if (!(p.dt > 0) || !(p.tau_m > 0) || !(p.lambda >= 0)) return SNN_E_ARG;
+        if (cfg->model == SNN_VOGELS_CUBA && (!(p.tau_e > 0) || !(p.tau_i > 0))) return SNN_E_ARG;
+        if ((cfg->flags & SNN_F_STDP) &&
+            (!(p.tau_plus > 0) || !(p.tau_minus > 0) || p.w_max_q < 0 || p.w_max_q > 32767))
+            return SNN_E_ARG;
+        uint32_t T[kPoissonCap];
+        if (cfg->model == SNN_BRUNEL && poisson_table(p.lambda, T, kPoissonCap) < 0) return SNN_E_ARG;
+        N += p.n;
+        Np += (p.n + kPad - 1) / kPad * kPad;
+    }
+    if (Np >= (1ull << 31)) return SNN_E_ARG;
+
+    snn_ctx* c = new (std::nothrow) snn_ctx();
+    if (!c) return SNN_E_NOMEM;
+    c->cfg = *cfg;
+    c->params.assign(params, params + cfg->n_inst);
+    if (dev) c->dev = *dev;
+    c->stream = (cudaStream_t)c->dev.stream;
+    c->vogels = cfg->model == SNN_VOGELS_CUBA;
+    c->stdp = (cfg->flags & SNN_F_STDP) != 0;
+    c->w16 = (cfg->flags & SNN_F_W16) != 0;
+    c->stats = (cfg->flags & SNN_F_STATS) != 0;
+    c->N = (uint32_t)N;
+    c->Np = (uint32_t)std::max<uint64_t>(Np, kPad);
+    c->D = cfg->delay + (c->stdp ? 1 : 0);
+    c->g_off.assign(cfg->n_inst + 1, 0);
+    c->pbase.assign(cfg->n_inst + 1, 0);
+    for (uint32_t b = 0; b < cfg->n_inst; ++b) {
+        c->g_off[b + 1] = c->g_off[b] + params[b].n;
+        c->pbase[b + 1] = c->pbase[b] + (params[b].n + kPad - 1) / kPad * kPad;
+    }
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return SNN_E_CUDA;
+    }
+
+    // per-instance constants and Poisson tables
+    std::vector<InstDev> hinst(cfg->n_inst);
+    std::vector<uint32_t> hpois((size_t)cfg->n_inst * kPoissonCap, 0);
+    for (uint32_t b = 0; b < cfg->n_inst; ++b) {
+        int np = 0;
+        if (cfg->model == SNN_BRUNEL) np = poisson_table(params[b].lambda, &hpois[(size_t)b * kPoissonCap], kPoissonCap);
+        hinst[b] = make_inst(params[b], c->pbase[b], b * kPoissonCap, np);
+    }
+    std::vector<uint32_t> hmap(c->Np / 32, 0);
+    for (uint32_t b = 0; b < cfg->n_inst; ++b)
+        for (uint32_t w = c->pbase[b] / 32; w < c->pbase[b + 1] / 32; ++w) hmap[w] = b;
+
+    const size_t Npz = c->Np;
+    Net& n = c->net;
+    n.Np = c->Np;
+    n.D = c->D;
+    n.d = cfg->delay;
+    n.n_inst = cfg->n_inst;
+    n.seed = cfg->seed;
+    c->cr = 4;
+    while (c->cr < c->D + 2) c->cr <<= 1;
+    n.cr = c->cr;
+    n.count = alloc_n<unsigned int>(c, c->cr);
+    n.icount = alloc_n<unsigned int>(c, (size_t)c->cr * cfg->n_inst);
+    n.lbase = alloc_n<unsigned long long>(c, c->cr);
+    c->ctl = alloc_n<Ctl>(c, 1);
+    c->inst = alloc_n<InstDev>(c, cfg->n_inst);
+    c->inst_of_w32 = alloc_n<uint32_t>(c, Npz / 32);
+    c->pois = alloc_n<uint32_t>(c, hpois.size());
+    n.V = alloc_n<float>(c, Npz);
+    n.r = alloc_n<uint8_t>(c, Npz);
+    n.acc0 = alloc_n<int32_t>(c, Npz);
+    n.q = alloc_n<uint32_t>(c, (size_t)c->D * Npz);
+    bool ok = c->ctl && c->inst && c->inst_of_w32 && c->pois && n.V && n.r && n.acc0 && n.q && n.count && n.icount && n.lbase;
+    if (c->vogels) {
+        n.ge = alloc_n<float>(c, Npz);
+        n.gi = alloc_n<float>(c, Npz);
+        n.acc1 = alloc_n<int32_t>(c, Npz);
+        ok = ok && n.ge && n.gi && n.acc1;
+    }
+    if (c->stdp) {
+        n.x = alloc_n<float>(c, Npz);
+        n.y = alloc_n<float>(c, Npz);
+        n.bits = alloc_n<uint32_t>(c, (size_t)c->D * (Npz / 32));
+        ok = ok && n.x && n.y && n.bits;
+    }
+    if (c->stats) {
+        n.st_cnt = alloc_n<uint32_t>(c, Npz);
+        n.st_last = alloc_n<uint32_t>(c, Npz);
+        n.st_sum = alloc_n<unsigned long long>(c, Npz);
+        n.st_sq = alloc_n<unsigned long long>(c, Npz);
+        ok = ok && n.st_cnt && n.st_last && n.st_sum && n.st_sq;
+    }
+    if (cfg->log_capacity) {
+        n.log = alloc_n<unsigned long long>(c, cfg->log_capacity);
+        n.log_cap = cfg->log_capacity;
+        ok = ok && n.log;
+    }
+    if (!ok) {
+        snn_destroy(c);
+        return SNN_E_NOMEM;
+    }
+    n.ctl = c->ctl;
+    n.inst = c->inst;
+    n.inst_of_w32 = c->inst_of_w32;
+    n.pois = c->pois;
+    cudaError_t e = cudaMemcpyAsync(c->inst, hinst.data(), hinst.size() * sizeof(InstDev), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->inst_of_w32, hmap.data(), hmap.size() * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->pois, hpois.data(), hpois.size() * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        snn_destroy(c);
+        return SNN_E_CUDA;
+    }
+    *out = c;
+    return SNN_OK;
+}
+
+snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* tgt_h, const int32_t* w_q)
+{
+    if (!c) return SNN_E_ARG;
+    if (!row_off) return fail(c, SNN_E_ARG, "row_off is NULL");
+    const uint32_t N = c->N;
+    if (row_off[0] != 0) return fail(c, SNN_E_ARG, "row_off[0] must be 0");
+    for (uint32_t j = 0; j < N; ++j)
+        if (row_off[j + 1] < row_off[j]) return fail(c, SNN_E_ARG, "row_off decreases at row %u", j);
+    const uint64_t E = row_off[N];
+    if (E && (!tgt_h || !w_q)) return fail(c, SNN_E_ARG, "tgt/w_q is NULL");
+    if (c->stdp && E >= (1ull << 32)) return fail(c, SNN_E_ARG, "STDP needs fewer than 2^32 edges");
+
+    // drop a previous graph
+    drop_graphs(c);
+    tiled_free(c->tiled, [c](void* p) { dev_free(c, p); });
+    c->use_tiled = false;
+    for (void* p : {(void*)c->roff, (void*)c->tgt, (void*)c->w16p, (void*)c->w32p, (void*)c->meta, (void*)c->coff,
+                    (void*)c->cedge, (void*)c->cpre, (void*)c->w_init})
+        dev_free(c, p);
+    c->roff = nullptr; c->tgt = nullptr; c->w16p = nullptr; c->w32p = nullptr; c->meta = nullptr;
+    c->coff = nullptr; c->cedge = nullptr; c->cpre = nullptr; c->w_init = nullptr;
+    c->graph_loaded = false;
+
+    // padded row offsets and the row -> (source, instance) maps
+    const uint32_t Np = c->Np;
+    std::vector<uint64_t> hroff((size_t)Np + 1, 0);
+    std::vector<uint32_t> hsrc((size_t)Np, 0xffffffffu), hinst((size_t)Np, 0);
+    {
+        uint32_t b = 0;
+        for (uint32_t pj = 0; pj < Np; ++pj) {
+            while (b + 1 < c->cfg.n_inst && pj >= c->pbase[b + 1]) ++b;
+            hinst[pj] = b;
+            const uint32_t local = pj - c->pbase[b];
+            if (pj < c->pbase[b + 1] && local < c->params[b].n) {
+                const uint32_t j = c->g_off[b] + local;
+                hsrc[pj] = j;
+                hroff[pj] = row_off[j];
+            } else {
+                // padding: an empty row at the offset of the next real row
+                const uint32_t next_g = c->g_off[b] + std::min(local, c->params[b].n);
+                hroff[pj] = row_off[std::min(next_g, N)];
+            }
+        }
+        hroff[Np] = E;
+        for (uint32_t pj = Np; pj-- > 0;)
+            if (hsrc[pj] == 0xffffffffu) hroff[pj] = hroff[pj + 1];
+    }
+
+    c->E = E;
+    c->roff = alloc_n<uint64_t>(c, (size_t)Np + 1);
+    c->tgt = alloc_n<uint32_t>(c, E);
+    c->meta = alloc_n<uint8_t>(c, Np);
+    if (c->w16)
+        c->w16p = alloc_n<int16_t>(c, E);
+    else
+        c->w32p = alloc_n<float>(c, E);
+    if (c->stdp) c->w_init = alloc_n<int32_t>(c, E);
+    int32_t* wtmp = c->stdp ? c->w_init : alloc_n<int32_t>(c, E);
+    uint32_t* dsrc = alloc_n<uint32_t>(c, Np);
+    uint32_t* dinst = alloc_n<uint32_t>(c, Np);
+    uint32_t* dgoff = alloc_n<uint32_t>(c, c->cfg.n_inst + 1);
+    uint32_t* dpb = alloc_n<uint32_t>(c, c->cfg.n_inst + 1);
+    uint32_t* dnexc = alloc_n<uint32_t>(c, c->cfg.n_inst);
+    unsigned int* dunsorted = alloc_n<unsigned int>(c, 1);
+    auto cleanup_tmp = [&]() {
+        if (!c->stdp) dev_free(c, wtmp);
+        dev_free(c, dsrc); dev_free(c, dinst); dev_free(c, dgoff); dev_free(c, dpb); dev_free(c, dnexc);
+        dev_free(c, dunsorted);
+    };
+    if (!c->roff || !c->tgt || !c->meta || (c->w16 ? !c->w16p : !c->w32p) || !wtmp || !dsrc || !dinst || !dgoff ||
+        !dpb || !dnexc || !dunsorted) {
+        cleanup_tmp();
+        return fail(c, SNN_E_NOMEM, "device allocation for a graph of %llu edges failed", (unsigned long long)E);
+    }
+    std::vector<uint32_t> hnexc(c->cfg.n_inst);
+    for (uint32_t b = 0; b < c->cfg.n_inst; ++b) hnexc[b] = c->params[b].n_exc;
+    cudaStream_t s = c->stream;
+    CUDA_TRY(c, cudaMemcpyAsync(c->roff, hroff.data(), hroff.size() * 8, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(dsrc, hsrc.data(), hsrc.size() * 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(dinst, hinst.data(), hinst.size() * 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(dgoff, c->g_off.data(), c->g_off.size() * 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(dpb, c->pbase.data(), c->pbase.size() * 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(dnexc, hnexc.data(), hnexc.size() * 4, cudaMemcpyHostToDevice, s));
+    if (E) {
+        CUDA_TRY(c, cudaMemcpyAsync(c->tgt, tgt_h, E * 4, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(c, cudaMemcpyAsync(wtmp, w_q, E * 4, cudaMemcpyHostToDevice, s));
+    }
+    CUDA_TRY(c, cudaMemsetAsync(&c->ctl->err, 0, sizeof(unsigned int), s));
+    CUDA_TRY(c, cudaMemsetAsync(dunsorted, 0, sizeof(unsigned int), s));
+    RowMapArgs a{};
+    a.roff = c->roff; a.row_src = dsrc; a.row_inst = dinst; a.g_inst_off = dgoff; a.pbase = dpb; a.n_exc = dnexc;
+    a.tgt = c->tgt; a.wq = wtmp; a.w16 = c->w16p; a.w32 = c->w32p; a.meta = c->meta; a.Np = Np;
+    a.w16_mode = c->w16 ? 1 : 0; a.vogels = c->vogels ? 1 : 0; a.stdp = c->stdp ? 1 : 0; a.err = &c->ctl->err;
+    a.unsorted = dunsorted;
+    k_map_rows<<<(uint32_t)sm_count() * 16, 256, 0, s>>>(a);
+    CUDA_TRY(c, cudaGetLastError());
+    unsigned int err = 0, unsorted = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&err, &c->ctl->err, 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaMemcpyAsync(&unsorted, dunsorted, 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    cleanup_tmp();
+    c->rows_sorted = unsorted == 0;
+    if (err) {
+        if (err & kErrBadTarget) return fail(c, SNN_E_ARG, "a row has a target outside its source's instance");
+        if (err & kErrPlasticShift)
+            return fail(c, SNN_E_ARG, "plastic (excitatory) rows need weights within int16 lattice units");
+        return fail(c, SNN_E_ARG, c->w16 ? "a row's weights are not int16 codes times one power of two"
+                                         : "a weight exceeds 2^24 lattice units");
+    }
+
+    // STDP column index: plastic in-edges (exc -> exc) of every padded post id
+    if (c->stdp) {
+        std::vector<uint64_t> hcoff((size_t)Np + 1, 0);
+        for (uint32_t b = 0; b < c->cfg.n_inst; ++b)
+            for (uint32_t jl = 0; jl < c->params[b].n_exc; ++jl) {
+                const uint32_t j = c->g_off[b] + jl;
+                for (uint64_t e = row_off[j]; e < row_off[j + 1]; ++e) {
+                    const uint32_t il = tgt_h[e] - c->g_off[b];
+                    if (il < c->params[b].n_exc) hcoff[c->pbase[b] + il + 1]++;
+                }
+            }
+        for (uint32_t i = 0; i < Np; ++i) hcoff[i + 1] += hcoff[i];
+        const uint64_t P = hcoff[Np];
+        std::vector<uint32_t> hce(P ? P : 1), hcp(P ? P : 1);
+        std::vector<uint64_t> fill(hcoff.begin(), hcoff.end() - 1);
+        for (uint32_t b = 0; b < c->cfg.n_inst; ++b)
+            for (uint32_t jl = 0; jl < c->params[b].n_exc; ++jl) {
+                const uint32_t j = c->g_off[b] + jl;
+                for (uint64_t e = row_off[j]; e < row_off[j + 1]; ++e) {
+                    const uint32_t il = tgt_h[e] - c->g_off[b];
+                    if (il < c->params[b].n_exc) {
+                        const uint64_t k = fill[c->pbase[b] + il]++;
+                        hce[k] = (uint32_t)e;
+                        hcp[k] = c->pbase[b] + jl;
+                    }
+                }
+            }
+        c->coff = alloc_n<uint64_t>(c, (size_t)Np + 1);
+        c->cedge = alloc_n<uint32_t>(c, P);
+        c->cpre = alloc_n<uint32_t>(c, P);
+        if (!c->coff || !c->cedge || !c->cpre) return fail(c, SNN_E_NOMEM, "STDP column index allocation failed");
+        CUDA_TRY(c, cudaMemcpyAsync(c->coff, hcoff.data(), hcoff.size() * 8, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(c, cudaMemcpyAsync(c->cedge, hce.data(), P * 4, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(c, cudaMemcpyAsync(c->cpre, hcp.data(), P * 4, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+    }
+
+    Net& n = c->net;
+    n.roff = c->roff;
+    n.tgt = c->tgt;
+    n.w16 = c->w16p;
+    n.w32 = c->w32p;
+    n.meta = c->meta;
+    n.coff = c->coff;
+    n.cedge = c->cedge;
+    n.cpre = c->cpre;
+
+    // receive strategy: the target-tiled form needs sorted rows
+    c->use_tiled = false;
+    if (c->cfg.receive != SNN_RECV_GLOBAL) {
+        snn_status st = SNN_E_ARG;
+        if (c->rows_sorted)
+            st = tiled_plan(c->tiled, c->net, c->params.data(), c->pbase.data(), c->cfg.n_inst, c->vogels ? 2 : 1,
+                            c->vogels ? 7168u : 14336u, nullptr, [c](size_t b) { return dev_alloc(c, b); },
+                            [c](void* p) { dev_free(c, p); }, s);
+        if (st == SNN_OK) {
+            c->use_tiled = true;
+        } else {
+            tiled_free(c->tiled, [c](void* p) { dev_free(c, p); });
+            if (c->cfg.receive == SNN_RECV_TILED)
+                return fail(c, st, c->rows_sorted ? "the tiled receive does not fit this graph"
+                                                  : "the tiled receive needs rows sorted by target");
+        }
+    }
+    c->graph_loaded = true;
+    snn_status st = init_state(c);
+    if (st != SNN_OK) return st;
+    c->k_steps = c->cfg.steps_per_graph ? c->cfg.steps_per_graph : 16;
+    st = capture(c, 1, &c->g1);
+    if (st == SNN_OK && c->k_steps > 1) st = capture(c, c->k_steps, &c->gk);
+    if (st != SNN_OK) return st;
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    return SNN_OK;
+}
+
+snn_status snn_reset(snn_ctx* c)
+{
+    if (!c) return SNN_E_ARG;
+    if (!c->graph_loaded) return fail(c, SNN_E_STATE, "no graph loaded");
+    if (c->stdp) {
+        k_weights_in<<<(uint32_t)sm_count() * 16, 256, 0, c->stream>>>(c->roff, c->meta, c->w_init, c->w16 ? 1 : 0,
+                                                                        c->Np, c->w16p, c->w32p, &c->ctl->err);
+        CUDA_TRY(c, cudaGetLastError());
+    }
+    snn_status st = init_state(c);
+    if (st != SNN_OK) return st;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return SNN_OK;
+}
+
+snn_status snn_step(snn_ctx* c, uint32_t n_steps)
+{
+    if (!c) return SNN_E_ARG;
+    if (!c->graph_loaded) return fail(c, SNN_E_STATE, "snn_step before snn_build_graph");
+    uint32_t left = n_steps;
+    while (c->gk && left >= c->k_steps) {
+        CUDA_TRY(c, cudaGraphLaunch(c->gk, c->stream));
+        left -= c->k_steps;
+    }
+    while (left--) CUDA_TRY(c, cudaGraphLaunch(c->g1, c->stream));
+    c->host_steps += n_steps;
+    return SNN_OK;
+}
+
+snn_status snn_step_profiled(snn_ctx* c, uint32_t n_steps, double* phase_ms)
+{
+    if (!c || !phase_ms) return SNN_E_ARG;
+    if (!c->graph_loaded) return fail(c, SNN_E_STATE, "snn_step_profiled before snn_build_graph");
+    for (int k = 0; k < 5; ++k) phase_ms[k] = 0.0;
+    std::vector<cudaEvent_t> ev((size_t)n_steps * 6);
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            e = nullptr;
+        }
+    snn_status st = SNN_OK;
+    for (uint32_t i = 0; i < n_steps && st == SNN_OK; ++i) {
+        for (int k = 0; k < 6; ++k)
+            if (!ev[(size_t)i * 6 + k]) st = fail(c, SNN_E_CUDA, "cudaEventCreate failed");
+        if (st == SNN_OK) st = enqueue_step(c, c->stream, &ev[(size_t)i * 6]);
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (st == SNN_OK && e != cudaSuccess) st = fail(c, SNN_E_CUDA, "profiled steps: %s", cudaGetErrorString(e));
+    for (uint32_t i = 0; i < n_steps && st == SNN_OK; ++i)
+        for (int k = 0; k < 5; ++k) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[(size_t)i * 6 + k], ev[(size_t)i * 6 + k + 1]) == cudaSuccess)
+                phase_ms[k] += ms;
+        }
+    for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+    c->host_steps += n_steps;
+    return st;
+}
+
+snn_status snn_sync(snn_ctx* c)
+{
+    if (!c) return SNN_E_ARG;
+    return check_device_errors(c);
+}
+
+snn_status snn_read_spikes(snn_ctx* c, uint32_t t0, uint32_t t1, uint32_t* steps, uint32_t* ids, uint64_t cap,
+                           uint64_t* n_out)
+{
+    if (!c || !n_out) return SNN_E_ARG;
+    *n_out = 0;
+    if (!c->cfg.log_capacity) return fail(c, SNN_E_STATE, "the context has no spike log (log_capacity = 0)");
+    if (cap && (!steps || !ids)) return fail(c, SNN_E_ARG, "NULL output with cap > 0");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    Ctl h;
+    CUDA_TRY(c, cudaMemcpy(&h, c->ctl, sizeof h, cudaMemcpyDeviceToHost));
+    unsigned long long total = 0;
+    CUDA_TRY(c, cudaMemcpy(&total, c->net.lbase + (h.t & (c->cr - 1)), 8, cudaMemcpyDeviceToHost));
+    const uint64_t avail = std::min<uint64_t>(total, c->cfg.log_capacity);
+    std::vector<unsigned long long> L(avail);
+    if (avail) CUDA_TRY(c, cudaMemcpy(L.data(), c->net.log, avail * 8, cudaMemcpyDeviceToHost));
+    std::vector<std::pair<uint32_t, uint32_t>> out;
+    out.reserve(avail);
+    for (uint64_t k = 0; k < avail; ++k) {
+        const uint32_t st = (uint32_t)(L[k] >> 32), pid = (uint32_t)L[k];
+        if (st < t0 || st >= t1) continue;
+        const auto it = std::upper_bound(c->pbase.begin(), c->pbase.end(), pid);
+        const uint32_t b = (uint32_t)(it - c->pbase.begin()) - 1;
+        out.emplace_back(st, pid - c->pbase[b] + c->g_off[b]);
+    }
+    std::sort(out.begin(), out.end());
+    *n_out = out.size();
+    if (total > c->cfg.log_capacity)
+        return fail(c, SNN_E_OVERFLOW, "the spike log overflowed (%llu spikes, capacity %llu)",
+                    (unsigned long long)total, (unsigned long long)c->cfg.log_capacity);
+    if (cap == 0) return SNN_OK;
+    if (cap < out.size()) return fail(c, SNN_E_OVERFLOW, "output capacity %llu < %llu spikes", (unsigned long long)cap,
+                                      (unsigned long long)out.size());
+    for (size_t k = 0; k < out.size(); ++k) {
+        steps[k] = out[k].first;
+        ids[k] = out[k].second;
+    }
+    return SNN_OK;
+}
+
+snn_status snn_log_clear(snn_ctx* c)
+{
+    if (!c) return SNN_E_ARG;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    Ctl* d = c->ctl;
+    unsigned long long t = 0;
+    CUDA_TRY(c, cudaMemcpy(&t, &d->t, 8, cudaMemcpyDeviceToHost));
+    const unsigned long long zero = 0;
+    unsigned int err = 0;
+    CUDA_TRY(c, cudaMemcpy(&d->t_log0, &t, 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->net.lbase + (t & (c->cr - 1)), &zero, 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(&err, &d->err, 4, cudaMemcpyDeviceToHost));
+    err &= ~kErrLogOverflow;
+    CUDA_TRY(c, cudaMemcpy(&d->err, &err, 4, cudaMemcpyHostToDevice));
+    return SNN_OK;
+}
+
+static snn_status field_ptr(snn_ctx* c, snn_field f, void** p, size_t* elem, bool* u8)
+{
+    *u8 = false;
+    *elem = 4;
+    switch (f) {
+    case SNN_FIELD_V: *p = c->net.V; break;
+    case SNN_FIELD_GE: *p = c->net.ge; break;
+    case SNN_FIELD_GI: *p = c->net.gi; break;
+    case SNN_FIELD_R: *p = c->net.r; *u8 = true; break;
+    case SNN_FIELD_X: *p = c->net.x; break;
+    case SNN_FIELD_Y: *p = c->net.y; break;
+    case SNN_FIELD_ACC0: *p = c->net.acc0; break;
+    case SNN_FIELD_ACC1: *p = c->net.acc1; break;
+    default: return fail(c, SNN_E_ARG, "unknown field %d", (int)f);
+    }
+    if (!*p) return fail(c, SNN_E_ARG, "field %d does not exist for this model", (int)f);
+    return SNN_OK;
+}
+
+snn_status snn_read_state(snn_ctx* c, snn_field f, void* host)
+{
+    if (!c || !host) return SNN_E_ARG;
+    if (!c->graph_loaded) return fail(c, SNN_E_STATE, "no graph loaded");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (f == SNN_FIELD_W) {
+        int32_t* tmp = alloc_n<int32_t>(c, c->E);
+        if (!tmp) return fail(c, SNN_E_NOMEM, "temporary weight buffer");
+        k_weights_out<<<(uint32_t)sm_count() * 16, 256, 0, c->stream>>>(c->roff, c->meta, c->w16p, c->w32p,
+                                                                         c->w16 ? 1 : 0, c->Np, tmp);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && c->E) e = cudaMemcpyAsync(host, tmp, c->E * 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        dev_free(c, tmp);
+        if (e != cudaSuccess) return fail(c, SNN_E_CUDA, "weight readback: %s", cudaGetErrorString(e));
+        return SNN_OK;
+    }
+    void* p;
+    size_t elem;
+    bool u8;
+    snn_status st = field_ptr(c, f, &p, &elem, &u8);
+    if (st != SNN_OK) return st;
+    std::vector<uint8_t> buf((size_t)c->Np * (u8 ? 1 : 4));
+    CUDA_TRY(c, cudaMemcpy(buf.data(), p, buf.size(), cudaMemcpyDeviceToHost));
+    for (uint32_t b = 0; b < c->cfg.n_inst; ++b)
+        for (uint32_t l = 0; l < c->params[b].n; ++l) {
+            const uint32_t pid = c->pbase[b] + l, g = c->g_off[b] + l;
+            if (u8)
+                static_cast<int32_t*>(host)[g] = buf[pid];
+            else
+                std::memcpy(static_cast<uint8_t*>(host) + (size_t)g * 4, buf.data() + (size_t)pid * 4, 4);
+        }
+    return SNN_OK;
+}
+
+snn_status snn_write_state(snn_ctx* c, snn_field f, const void* host)
+{
+    if (!c || !host) return SNN_E_ARG;
+    if (!c->graph_loaded) return fail(c, SNN_E_STATE, "no graph loaded");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (f == SNN_FIELD_W) {
+        int32_t* tmp = alloc_n<int32_t>(c, c->E);
+        if (!tmp) return fail(c, SNN_E_NOMEM, "temporary weight buffer");
+        unsigned int err = 0;
+        cudaError_t e = c->E ? cudaMemcpyAsync(tmp, host, c->E * 4, cudaMemcpyHostToDevice, c->stream) : cudaSuccess;
+        if (e == cudaSuccess) e = cudaMemsetAsync(&c->ctl->err, 0, 4, c->stream);
+        if (e == cudaSuccess) {
+            k_weights_in<<<(uint32_t)sm_count() * 16, 256, 0, c->stream>>>(c->roff, c->meta, tmp, c->w16 ? 1 : 0,
+                                                                            c->Np, c->w16p, c->w32p, &c->ctl->err);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &c->ctl->err, 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        dev_free(c, tmp);
+        if (e != cudaSuccess) return fail(c, SNN_E_CUDA, "weight upload: %s", cudaGetErrorString(e));
+        if (err & kErrBadWeight) return fail(c, SNN_E_ARG, "a weight does not fit its row's int16 code and shift");
+        return SNN_OK;
+    }
+    void* p;
+    size_t elem;
+    bool u8;
+    snn_status st = field_ptr(c, f, &p, &elem, &u8);
+    if (st != SNN_OK) return st;
+    std::vector<uint8_t> buf((size_t)c->Np * (u8 ? 1 : 4));
+    CUDA_TRY(c, cudaMemcpy(buf.data(), p, buf.size(), cudaMemcpyDeviceToHost));
+    for (uint32_t b = 0; b < c->cfg.n_inst; ++b)
+        for (uint32_t l = 0; l < c->params[b].n; ++l) {
+            const uint32_t pid = c->pbase[b] + l, g = c->g_off[b] + l;
+            if (u8) {
+                const int32_t v = static_cast<const int32_t*>(host)[g];
+                if (v < 0 || v > 255) return fail(c, SNN_E_ARG, "refractory count out of range");
+                buf[pid] = (uint8_t)v;
+            } else {
+                std::memcpy(buf.data() + (size_t)pid * 4, static_cast<const uint8_t*>(host) + (size_t)g * 4, 4);
+            }
+        }
+    CUDA_TRY(c, cudaMemcpy(p, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+    return SNN_OK;
+}
+
+snn_status snn_counters(snn_ctx* c, uint64_t* steps, uint64_t* spikes, uint64_t* events)
+{
+    if (!c) return SNN_E_ARG;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    Ctl h;
+    CUDA_TRY(c, cudaMemcpy(&h, c->ctl, sizeof h, cudaMemcpyDeviceToHost));
+    if (steps) *steps = h.t;
+    if (spikes) *spikes = h.spikes;
+    if (events) *events = h.events;
+    return SNN_OK;
+}
+
+snn_status snn_stats(snn_ctx* c, uint32_t inst, double* rate_hz, double* isi_cv)
+{
+    if (!c || inst >= c->cfg.n_inst) return SNN_E_ARG;
+    if (!c->stats) return fail(c, SNN_E_STATE, "the context was created without SNN_F_STATS");
+    double* d = alloc_n<double>(c, 3);
+    if (!d) return fail(c, SNN_E_NOMEM, "stats buffer");
+    double h[3] = {0, 0, 0};
+    Ctl hc;
+    cudaError_t e = cudaMemsetAsync(d, 0, 3 * sizeof(double), c->stream);
+    if (e == cudaSuccess) {
+        k_stats<<<64, 256, 0, c->stream>>>(c->net.st_cnt, c->net.st_sum, c->net.st_sq, c->pbase[inst],
+                                           c->pbase[inst] + c->params[inst].n, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, c->ctl, sizeof hc, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, d);
+    if (e != cudaSuccess) return fail(c, SNN_E_CUDA, "stats: %s", cudaGetErrorString(e));
+    const double window = (double)(hc.t - hc.t_stat0) * c->params[inst].dt * 1e-3;
+    if (rate_hz) *rate_hz = (window > 0 && c->params[inst].n) ? h[0] / c->params[inst].n / window : 0.0;
+    if (isi_cv) *isi_cv = h[2] > 0 ? h[1] / h[2] : 0.0;
+    return SNN_OK;
+}
+
+snn_status snn_stats_clear(snn_ctx* c)
+{
+    if (!c) return SNN_E_ARG;
+    if (!c->stats) return fail(c, SNN_E_STATE, "the context was created without SNN_F_STATS");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    unsigned long long t = 0;
+    CUDA_TRY(c, cudaMemcpy(&t, &c->ctl->t, 8, cudaMemcpyDeviceToHost));
+    CUDA_TRY(c, cudaMemcpy(&c->ctl->t_stat0, &t, 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemset(c->net.st_cnt, 0, (size_t)c->Np * 4));
+    CUDA_TRY(c, cudaMemset(c->net.st_sum, 0, (size_t)c->Np * 8));
+    CUDA_TRY(c, cudaMemset(c->net.st_sq, 0, (size_t)c->Np * 8));
+    return SNN_OK;
+}
+
+snn_status snn_get_info(snn_ctx* c, snn_info* info)
+{
+    if (!c || !info) return SNN_E_ARG;
+    info->receive = c->use_tiled ? SNN_RECV_TILED : SNN_RECV_GLOBAL;
+    info->n_tiles = c->use_tiled ? c->tiled.n_tiles : 0;
+    info->n_padded = c->Np;
+    info->rows_sorted = c->rows_sorted ? 1 : 0;
+    info->edges = c->E;
+    info->device_bytes = c->bytes_held;
+    return SNN_OK;
+}
+
+void snn_destroy(snn_ctx* c)
+{
+    if (!c) return;
+    if (c->stream || c->cap_stream) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    while (!c->allocs.empty()) dev_free(c, c->allocs.back().p);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    cudaGetLastError();
+    delete c;
+}
+
+}  // extern "C"

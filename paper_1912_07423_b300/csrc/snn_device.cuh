@@ -1,0 +1,138 @@
+// snn_device.cuh -- device-side data layout and helpers of libsnn.
+//
+// Layout in HBM (structure of arrays, Section III-A-2):
+//   neurons  : instance b occupies padded ids [pbase_b, pbase_b + n_b) with
+//              pbase_b a multiple of 256, so the 256 neurons one warp of the
+//              update kernel advances (8 per thread) never straddle two
+//              instances.
+//              V, ge, gi, x, y: float[Np]; r: uint8[Np]; acc0, acc1: int32[Np].
+//   graph    : CSR over padded ids, roff: uint64[Np+1], tgt: uint32[E]
+//              (padded ids, sorted rows), weights int16[E] (code, value =
+//              code << shift(row)) or float[E] (exact lattice integers),
+//              meta: uint8[Np] = shift | exc_source << 6 | channel << 7.
+//   queues   : the delay FIFO is a ring of D spike queues, uint32[D][Np]
+//              (Section III-A-2: arrays with an atomic insertion index).  In
+//              every slot instance b owns the region [pbase_b, pbase_b+n_b)
+//              with its own index icount[t % CR][b], so a consumer can take
+//              one network's spikes alone.  With STDP a ring of D spike
+//              bitmasks uint32[D][Np/32] sits beside it (Section III-A-1).
+#pragma once
+#include <cstdint>
+
+namespace snn {
+
+constexpr int kPad = 256;         // instance alignment in neurons
+constexpr int kPoissonCap = 64;   // Poisson threshold table entries per instance
+constexpr float kLattice = 1.0f / 65536.0f;  // 2^-16 mV
+
+enum : uint32_t {
+    kErrLogOverflow = 1u,
+    kErrBadTarget = 2u,
+    kErrBadWeight = 4u,
+    kErrPlasticShift = 8u,
+    kErrTimeout = 16u,
+};
+
+// Per-instance constants, each binary32 value the binary64 expression
+// rounded once (see snn_params in snn.h).
+struct InstDev {
+    uint32_t pbase, n, n_exc, R;
+    int32_t jext, wmax;
+    uint32_t pois_off, pois_n;
+    float Pm, Pe, Pi, Pp, Pn, Ap, Am;
+    float v_th, v_reset, e_l, v0_lo, v0_span;
+};
+
+// Device control block: the step counter and the work-queue indices.
+struct Ctl {
+    unsigned long long t;       // current step
+    unsigned long long t_log0;  // first step of the raster log
+    unsigned long long t_stat0; // first step of the statistics window
+    unsigned long long events;  // delivered synaptic events
+    unsigned long long spikes;  // emitted spikes
+    unsigned int err;           // kErr* bits
+    unsigned int pad;
+};
+
+// Everything a kernel needs, passed by value.
+struct Net {
+    uint32_t Np, D, d, n_inst;
+    uint32_t cr;               // count-ring length, a power of two >= D + 2
+    uint32_t pad0;
+    uint64_t seed;
+    unsigned int* count;       // |S_t| over all instances at [t % cr]
+    unsigned int* icount;      // |S_t| of instance b at [(t % cr) * n_inst + b]
+    unsigned long long* lbase; // log position of S_t's first spike at [t % cr]
+    const InstDev* inst;
+    const uint32_t* inst_of_w32;  // instance of each 32-neuron word
+    const uint32_t* pois;         // Poisson thresholds, kPoissonCap per instance
+    float* V;
+    float* ge;
+    float* gi;
+    float* x;
+    float* y;
+    uint8_t* r;
+    int32_t* acc0;
+    int32_t* acc1;
+    const uint64_t* roff;
+    const uint32_t* tgt;
+    int16_t* w16;
+    float* w32;
+    const uint8_t* meta;
+    const uint64_t* coff;   // STDP: plastic in-edges per padded post id
+    const uint32_t* cedge;  // STDP: edge index of each plastic in-edge
+    const uint32_t* cpre;   // STDP: padded presynaptic id of each plastic in-edge
+    uint32_t* q;            // D * Np
+    uint32_t* bits;         // D * Np/32
+    unsigned long long* log;
+    unsigned long long log_cap;
+    uint32_t* st_cnt;
+    uint32_t* st_last;
+    unsigned long long* st_sum;
+    unsigned long long* st_sq;
+    Ctl* ctl;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11), written from its
+// published definition: 10 rounds of two 64x64->128 multiplications with a
+// Weyl-sequence key schedule.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x64_10(uint64_t& c0, uint64_t& c1, uint64_t& c2, uint64_t& c3, uint64_t k0,
+                                              uint64_t k1)
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        const uint64_t n0 = hi1 ^ c1 ^ k0;
+        const uint64_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+}
+
+// The 8 words of the block at counter (group, step, tag, 0), key (seed,
+// instance): word k belongs to local neuron 8*group + k, low half first.
+__device__ __forceinline__ void philox_words8(uint64_t seed, uint32_t inst, uint32_t group, uint64_t step,
+                                              uint32_t tag, uint32_t w[8])
+{
+    uint64_t c0 = group, c1 = step, c2 = tag, c3 = 0;
+    philox4x64_10(c0, c1, c2, c3, seed, inst);
+    w[0] = (uint32_t)c0; w[1] = (uint32_t)(c0 >> 32);
+    w[2] = (uint32_t)c1; w[3] = (uint32_t)(c1 >> 32);
+    w[4] = (uint32_t)c2; w[5] = (uint32_t)(c2 >> 32);
+    w[6] = (uint32_t)c3; w[7] = (uint32_t)(c3 >> 32);
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+}  // namespace snn

@@ -1,0 +1,562 @@
+// snn_kernels.cuh -- the per-step kernels of libsnn (Update Neurons with
+// spike compaction, Update Synapses, Receive Spikes) and the set-up kernels.
+//
+// Arithmetic of the neuron update: binary32, one rounding per operation, no
+// contraction (explicit __f*_rn intrinsics; the file is also compiled with
+// -fmad=false), in the order documented in snn.h / the oracle's header.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "snn_device.cuh"
+
+namespace snn {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Update Neurons (Section III-A-1): N_t -> N'_{t+1}, spikers -> S_t.
+// One thread advances 8 consecutive neurons (two 128-bit loads per float
+// field, one Philox block for the 8 Poisson words).  Spiking ids are
+// compacted per warp with a shuffle scan and one atomicAdd on the queue
+// index (Section III-A-2: queues are arrays with an atomic index).
+// ---------------------------------------------------------------------------
+template <int MODEL, bool STDP, bool STATS>
+__global__ void __launch_bounds__(256) k_update(Net n)
+{
+    const unsigned long long t = n.ctl->t;
+    const uint32_t G = n.Np >> 3;
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = g < G;  // whole warps: Np is a multiple of 256
+    const uint32_t id0 = g * 8u;
+    uint32_t spk = 0;  // bit k: neuron id0 + k spiked
+    const uint32_t b = active ? __ldg(n.inst_of_w32 + (g >> 2)) : 0u;  // uniform across the warp
+    const InstDev* I = n.inst + b;
+    const uint32_t pbase = active ? __ldg(&I->pbase) : 0u;
+
+    if (active) {
+        const uint32_t nloc = __ldg(&I->n);
+        const uint32_t local0 = id0 - pbase;
+        if (local0 < nloc) {
+            const float v_th = __ldg(&I->v_th), v_reset = __ldg(&I->v_reset), Pm = __ldg(&I->Pm);
+            const uint32_t R = __ldg(&I->R);
+            float V[8];
+            *reinterpret_cast<float4*>(V) = *reinterpret_cast<const float4*>(n.V + id0);
+            *reinterpret_cast<float4*>(V + 4) = *reinterpret_cast<const float4*>(n.V + id0 + 4);
+            uint2 rr = *reinterpret_cast<const uint2*>(n.r + id0);
+            uint8_t r[8];
+            *reinterpret_cast<uint2*>(r) = rr;
+            int32_t a0[8];
+            *reinterpret_cast<int4*>(a0) = *reinterpret_cast<const int4*>(n.acc0 + id0);
+            *reinterpret_cast<int4*>(a0 + 4) = *reinterpret_cast<const int4*>(n.acc0 + id0 + 4);
+
+            if (MODEL == 0) {  // Vogels-Abbott CUBA
+                const float Pe = __ldg(&I->Pe), Pi = __ldg(&I->Pi), e_l = __ldg(&I->e_l);
+                float ge[8], gi[8];
+                int32_t a1[8];
+                *reinterpret_cast<float4*>(ge) = *reinterpret_cast<const float4*>(n.ge + id0);
+                *reinterpret_cast<float4*>(ge + 4) = *reinterpret_cast<const float4*>(n.ge + id0 + 4);
+                *reinterpret_cast<float4*>(gi) = *reinterpret_cast<const float4*>(n.gi + id0);
+                *reinterpret_cast<float4*>(gi + 4) = *reinterpret_cast<const float4*>(n.gi + id0 + 4);
+                *reinterpret_cast<int4*>(a1) = *reinterpret_cast<const int4*>(n.acc1 + id0);
+                *reinterpret_cast<int4*>(a1 + 4) = *reinterpret_cast<const int4*>(n.acc1 + id0 + 4);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (local0 + k >= nloc) continue;
+                    float e = __fadd_rn(ge[k], __fmul_rn(__int2float_rn(a0[k]), kLattice));
+                    float i = __fadd_rn(gi[k], __fmul_rn(__int2float_rn(a1[k]), kLattice));
+                    float v = V[k];
+                    uint32_t rk = r[k];
+                    if (rk > 0) {
+                        rk -= 1;
+                        v = v_reset;
+                    } else {
+                        const float u = __fadd_rn(e_l, __fadd_rn(e, i));
+                        v = __fadd_rn(u, __fmul_rn(__fsub_rn(v, u), Pm));
+                    }
+                    e = __fmul_rn(e, Pe);
+                    i = __fmul_rn(i, Pi);
+                    if (rk == 0 && v >= v_th) {
+                        spk |= 1u << k;
+                        v = v_reset;
+                        rk = R;
+                    }
+                    V[k] = v;
+                    ge[k] = e;
+                    gi[k] = i;
+                    r[k] = (uint8_t)rk;
+                }
+                *reinterpret_cast<float4*>(n.ge + id0) = *reinterpret_cast<float4*>(ge);
+                *reinterpret_cast<float4*>(n.ge + id0 + 4) = *reinterpret_cast<float4*>(ge + 4);
+                *reinterpret_cast<float4*>(n.gi + id0) = *reinterpret_cast<float4*>(gi);
+                *reinterpret_cast<float4*>(n.gi + id0 + 4) = *reinterpret_cast<float4*>(gi + 4);
+                *reinterpret_cast<int4*>(n.acc1 + id0) = make_int4(0, 0, 0, 0);
+                *reinterpret_cast<int4*>(n.acc1 + id0 + 4) = make_int4(0, 0, 0, 0);
+            } else {  // Brunel with Poisson drive
+                const int32_t jext = __ldg(&I->jext);
+                const uint32_t* T = n.pois + __ldg(&I->pois_off);
+                const uint32_t nT = __ldg(&I->pois_n);
+                uint32_t words[8];
+                philox_words8(n.seed, b, local0 >> 3, t, 1, words);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (local0 + k >= nloc) continue;
+                    float v = V[k];
+                    uint32_t rk = r[k];
+                    if (rk > 0) {
+                        rk -= 1;
+                        v = v_reset;
+                    } else {
+                        uint32_t next = 0;
+                        while (next < nT && __ldg(T + next) <= words[k]) ++next;
+                        const int32_t in = a0[k] + (int32_t)next * jext;
+                        v = __fadd_rn(__fmul_rn(v, Pm), __fmul_rn(__int2float_rn(in), kLattice));
+                        if (v >= v_th) {
+                            spk |= 1u << k;
+                            v = v_reset;
+                            rk = R;
+                        }
+                    }
+                    V[k] = v;
+                    r[k] = (uint8_t)rk;
+                }
+                if (STDP) {
+                    // traces of the excitatory neurons: x decays and counts
+                    // the arrivals of S_{t-d}; y decays and counts S_t
+                    const uint32_t n_exc = __ldg(&I->n_exc);
+                    const float Pp = __ldg(&I->Pp), Pn = __ldg(&I->Pn);
+                    uint32_t arr = 0;
+                    if (t >= n.d) {
+                        const uint32_t slot = (uint32_t)((t - n.d) % n.D);
+                        arr = (n.bits[(size_t)slot * (n.Np >> 5) + (id0 >> 5)] >> (id0 & 31u)) & 0xffu;
+                    }
+                    float xs[8], ys[8];
+                    *reinterpret_cast<float4*>(xs) = *reinterpret_cast<const float4*>(n.x + id0);
+                    *reinterpret_cast<float4*>(xs + 4) = *reinterpret_cast<const float4*>(n.x + id0 + 4);
+                    *reinterpret_cast<float4*>(ys) = *reinterpret_cast<const float4*>(n.y + id0);
+                    *reinterpret_cast<float4*>(ys + 4) = *reinterpret_cast<const float4*>(n.y + id0 + 4);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        if (local0 + k >= n_exc) continue;
+                        float xv = __fmul_rn(xs[k], Pp);
+                        if (arr >> k & 1u) xv = __fadd_rn(xv, 1.0f);
+                        float yv = __fmul_rn(ys[k], Pn);
+                        if (spk >> k & 1u) yv = __fadd_rn(yv, 1.0f);
+                        xs[k] = xv;
+                        ys[k] = yv;
+                    }
+                    *reinterpret_cast<float4*>(n.x + id0) = *reinterpret_cast<float4*>(xs);
+                    *reinterpret_cast<float4*>(n.x + id0 + 4) = *reinterpret_cast<float4*>(xs + 4);
+                    *reinterpret_cast<float4*>(n.y + id0) = *reinterpret_cast<float4*>(ys);
+                    *reinterpret_cast<float4*>(n.y + id0 + 4) = *reinterpret_cast<float4*>(ys + 4);
+                }
+            }
+            *reinterpret_cast<float4*>(n.V + id0) = *reinterpret_cast<float4*>(V);
+            *reinterpret_cast<float4*>(n.V + id0 + 4) = *reinterpret_cast<float4*>(V + 4);
+            *reinterpret_cast<uint2*>(n.r + id0) = *reinterpret_cast<uint2*>(r);
+            *reinterpret_cast<int4*>(n.acc0 + id0) = make_int4(0, 0, 0, 0);
+            *reinterpret_cast<int4*>(n.acc0 + id0 + 4) = make_int4(0, 0, 0, 0);
+            if (STATS && spk) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (spk >> k & 1u) {
+                        const uint32_t c = n.st_cnt[id0 + k];
+                        if (c > 0) {
+                            const unsigned long long isi = t - n.st_last[id0 + k];
+                            n.st_sum[id0 + k] += isi;
+                            n.st_sq[id0 + k] += isi * isi;
+                        }
+                        n.st_cnt[id0 + k] = c + 1;
+                        n.st_last[id0 + k] = (uint32_t)t;
+                    }
+            }
+        }
+    }
+
+    const uint32_t lane = lane_id();
+    const uint32_t slot_q = (uint32_t)(t % n.D);
+    const uint32_t slot_c = (uint32_t)(t & (n.cr - 1));
+    if (STDP) {
+        // the warp's 256 neurons = 8 bitmask words; lanes 4m..4m+3 form word m
+        uint32_t word = spk << (8u * (lane & 3u));
+        word |= __shfl_xor_sync(kFull, word, 1);
+        word |= __shfl_xor_sync(kFull, word, 2);
+        if (active && (lane & 3u) == 0) n.bits[(size_t)slot_q * (n.Np >> 5) + (id0 >> 5)] = word;
+    }
+    // warp compaction: exclusive scan of the per-thread spike counts, one
+    // atomicAdd on the instance's queue index and one on the step's total
+    const uint32_t c = __popc(spk);
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= (uint32_t)o) incl += v;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) return;
+    uint32_t wbase = 0, lpos = 0;
+    if (lane == 31) {
+        wbase = atomicAdd(&n.icount[(size_t)slot_c * n.n_inst + b], total);
+        lpos = atomicAdd(&n.count[slot_c], total);
+    }
+    wbase = __shfl_sync(kFull, wbase, 31);
+    lpos = __shfl_sync(kFull, lpos, 31);
+    if (!spk) return;
+    // log position of this step's first spike (written by the previous step's end)
+    const unsigned long long lb = n.log_cap ? n.lbase[slot_c] + lpos : 0ull;
+    const uint32_t off = incl - c;
+    uint32_t* q = n.q + (size_t)slot_q * n.Np + pbase + wbase + off;
+    uint32_t m = spk, k = 0;
+    while (m) {
+        const int bit = __ffs(m) - 1;
+        m &= m - 1;
+        const uint32_t id = id0 + bit;
+        q[k] = id;
+        if (n.log_cap) {
+            const unsigned long long lp = lb + off + k;
+            if (lp < n.log_cap)
+                n.log[lp] = (t << 32) | id;
+            else
+                atomicOr(&n.ctl->err, kErrLogOverflow);
+        }
+        ++k;
+    }
+}
+
+// End of a step: the log position of the next step's first spike follows
+// this step's; the queue indices of the next step start at zero; t += 1.
+__global__ void k_step_end(Net n)
+{
+    const unsigned long long t = n.ctl->t;
+    const uint32_t sc = (uint32_t)(t & (n.cr - 1)), sn = (uint32_t)((t + 1) & (n.cr - 1));
+    for (uint32_t b = threadIdx.x; b < n.n_inst; b += blockDim.x) n.icount[(size_t)sn * n.n_inst + b] = 0;
+    if (threadIdx.x == 0) {
+        const uint32_t c = n.count[sc];
+        n.ctl->spikes += c;
+        n.lbase[sn] = n.lbase[sc] + c;
+        n.count[sn] = 0;
+        n.ctl->t = t + 1;
+    }
+}
+
+// Visit the spikes of one queue slot, instance by instance, spreading them
+// over all warps of the grid: f(j) for every spiking padded id j.
+template <class F>
+__device__ __forceinline__ void for_each_spike(const Net& n, unsigned long long ts, F f)
+{
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t sc = (uint32_t)(ts & (n.cr - 1));
+    const uint32_t* qs = n.q + (size_t)(ts % n.D) * n.Np;
+    const unsigned int* ic = n.icount + (size_t)sc * n.n_inst;
+    uint32_t next = warp, base = 0;
+    for (uint32_t b = 0; b < n.n_inst; ++b) {
+        const uint32_t cnt = ic[b];
+        if (next < base + cnt) {
+            const uint32_t* qb = qs + __ldg(&n.inst[b].pbase);
+            for (; next < base + cnt; next += nwarps) f(qb[next - base]);
+        }
+        base += cnt;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Receive Spikes (Section III-A-2), global-accumulator form: one warp per
+// spike of S_{t-d+1} walks the spiker's row with coalesced target/weight
+// loads and adds the weights with red.global.add into the L2-resident
+// int32 accumulators of the targets (order-independent integer sums).
+// ---------------------------------------------------------------------------
+template <bool W16>
+__global__ void __launch_bounds__(256) k_receive_global(Net n)
+{
+    const unsigned long long t = n.ctl->t;
+    if (t + 1 < n.d) return;
+    const uint32_t lane = lane_id();
+    unsigned long long ev = 0;
+    for_each_spike(n, t + 1 - n.d, [&](uint32_t j) {
+        const uint64_t beg = __ldg(n.roff + j), end = __ldg(n.roff + j + 1);
+        const uint32_t meta = __ldg(n.meta + j);
+        const uint32_t shift = meta & 31u;
+        int32_t* acc = (meta & 0x80u) ? n.acc1 : n.acc0;
+        ev += end - beg;
+        uint64_t e = beg + lane;
+        for (; e + 96 < end; e += 128) {
+            uint32_t tg[4];
+            int32_t wv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                tg[u] = __ldg(n.tgt + e + 32 * u);
+                wv[u] = W16 ? ((int32_t)__ldg(n.w16 + e + 32 * u) << shift) : __float2int_rz(__ldg(n.w32 + e + 32 * u));
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) atomicAdd(acc + tg[u], wv[u]);
+        }
+        for (; e < end; e += 32) {
+            const uint32_t tg = __ldg(n.tgt + e);
+            const int32_t wv = W16 ? ((int32_t)__ldg(n.w16 + e) << shift) : __float2int_rz(__ldg(n.w32 + e));
+            atomicAdd(acc + tg, wv);
+        }
+    });
+    if (lane == 0 && ev) atomicAdd(&n.ctl->events, ev);
+}
+
+// ---------------------------------------------------------------------------
+// Update Synapses (Section III-A-1), pair STDP on exc -> exc synapses.
+// Depression for the rows of S_{t-d} (the presynaptic spikes reaching their
+// synapses at step t), run before the neuron update of step t so that the
+// postsynaptic trace it reads is y(t-1), decayed here by one step.
+// ---------------------------------------------------------------------------
+template <bool W16>
+__global__ void __launch_bounds__(256) k_stdp_depress(Net n)
+{
+    const unsigned long long t = n.ctl->t;
+    if (t < n.d) return;
+    const uint32_t lane = lane_id();
+    for_each_spike(n, t - n.d, [&](uint32_t j) {
+        const uint32_t meta = __ldg(n.meta + j);
+        if (!(meta & 0x40u)) return;  // inhibitory source: no plastic synapses
+        const InstDev* I = n.inst + __ldg(n.inst_of_w32 + (j >> 5));
+        const uint32_t pbase = __ldg(&I->pbase), n_exc = __ldg(&I->n_exc);
+        const float Pn = __ldg(&I->Pn), Am = __ldg(&I->Am);
+        const int32_t wmax = __ldg(&I->wmax);
+        const uint64_t beg = __ldg(n.roff + j), end = __ldg(n.roff + j + 1);
+        for (uint64_t e = beg + lane; e < end; e += 32) {
+            const uint32_t i = __ldg(n.tgt + e);
+            if (i - pbase >= n_exc) continue;
+            const float yd = __fmul_rn(n.y[i], Pn);
+            const int32_t dw = __float2int_rn(__fmul_rn(Am, yd));
+            if (W16) {
+                const int32_t w = min(max((int32_t)n.w16[e] + dw, 0), wmax);
+                n.w16[e] = (int16_t)w;
+            } else {
+                const int32_t w = min(max(__float2int_rz(n.w32[e]) + dw, 0), wmax);
+                n.w32[e] = (float)w;
+            }
+        }
+    });
+}
+
+// Potentiation for the in-edges of the excitatory spikers of S_t, after the
+// neuron update of step t (the presynaptic traces then include step t's
+// arrivals, so a coincident arrival counts as causal).
+template <bool W16>
+__global__ void __launch_bounds__(256) k_stdp_potentiate(Net n)
+{
+    const unsigned long long t = n.ctl->t;
+    const uint32_t lane = lane_id();
+    for_each_spike(n, t, [&](uint32_t i) {
+        const InstDev* I = n.inst + __ldg(n.inst_of_w32 + (i >> 5));
+        const float Ap = __ldg(&I->Ap);
+        const int32_t wmax = __ldg(&I->wmax);
+        const uint64_t beg = __ldg(n.coff + i), end = __ldg(n.coff + i + 1);
+        for (uint64_t k = beg + lane; k < end; k += 32) {
+            const uint32_t e = __ldg(n.cedge + k);
+            const uint32_t j = __ldg(n.cpre + k);
+            const int32_t dw = __float2int_rn(__fmul_rn(Ap, n.x[j]));
+            if (W16) {
+                const int32_t w = min(max((int32_t)n.w16[e] + dw, 0), wmax);
+                n.w16[e] = (int16_t)w;
+            } else {
+                const int32_t w = min(max(__float2int_rz(n.w32[e]) + dw, 0), wmax);
+                n.w32[e] = (float)w;
+            }
+        }
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Init stage (Fig. 1 caption): N -> N_0.
+// ---------------------------------------------------------------------------
+__global__ void k_init_state(Net n, int vogels, int stdp)
+{
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (n.Np >> 3)) return;
+    const uint32_t id0 = g * 8u;
+    const uint32_t b = n.inst_of_w32[g >> 2];
+    const InstDev* I = n.inst + b;
+    const uint32_t local0 = id0 - I->pbase;
+    uint32_t words[8];
+    philox_words8(n.seed, b, local0 >> 3, 0, 0, words);
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t id = id0 + k;
+        float v = 0.0f;
+        if (local0 + k < I->n) {
+            const float u01 = __fmul_rn(__uint2float_rn(words[k] >> 8), 1.0f / 16777216.0f);
+            v = __fadd_rn(I->v0_lo, __fmul_rn(I->v0_span, u01));
+        }
+        n.V[id] = v;
+        n.r[id] = 0;
+        n.acc0[id] = 0;
+        if (vogels) {
+            n.ge[id] = 0.0f;
+            n.gi[id] = 0.0f;
+            n.acc1[id] = 0;
+        }
+        if (stdp) {
+            n.x[id] = 0.0f;
+            n.y[id] = 0.0f;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Graph set-up: one warp per row.  Maps targets to padded ids (checking that
+// they stay inside the source's instance), picks the row's weight shift and
+// writes the stored weights.
+// ---------------------------------------------------------------------------
+struct RowMapArgs {
+    const uint64_t* roff;        // padded row offsets (Np+1)
+    const uint32_t* row_src;     // padded id -> global id (or ~0u for padding)
+    const uint32_t* row_inst;    // padded id -> instance
+    const uint32_t* g_inst_off;  // global instance offsets (n_inst+1)
+    const uint32_t* pbase;       // padded bases (n_inst)
+    const uint32_t* n_exc;       // per instance
+    uint32_t* tgt;               // in: global ids, out: padded ids
+    const int32_t* wq;           // lattice weights
+    int16_t* w16;
+    float* w32;
+    uint8_t* meta;
+    uint32_t Np;
+    int w16_mode, vogels, stdp;
+    unsigned int* err;
+    unsigned int* unsorted;      // set to 1 if some row's targets are not ascending
+};
+
+// smallest s with -32768 * 2^s <= w <= 32767 * 2^s (99 if none up to 15)
+__device__ __forceinline__ int shift_needed(int32_t w)
+{
+    int s = 0;
+    while ((long long)w > 32767LL * (1LL << s) || (long long)w < -32768LL * (1LL << s)) {
+        if (++s > 15) return 99;
+    }
+    return s;
+}
+
+__global__ void k_map_rows(RowMapArgs a)
+{
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t pj = warp; pj < a.Np; pj += nwarps) {
+        const uint64_t beg = a.roff[pj], end = a.roff[pj + 1];
+        const uint32_t j = a.row_src[pj];
+        if (j == 0xffffffffu) {
+            if (lane == 0) a.meta[pj] = 0;
+            continue;
+        }
+        const uint32_t b = a.row_inst[pj];
+        const uint32_t g0 = a.g_inst_off[b], g1 = a.g_inst_off[b + 1];
+        const uint32_t pb = a.pbase[b];
+        const bool exc = (j - g0) < a.n_exc[b];
+        int s = 0;
+        bool bad_t = false, bad_w = false;
+        for (uint64_t e = beg + lane; e < end; e += 32) {
+            const uint32_t tg = a.tgt[e];
+            if (tg < g0 || tg >= g1) bad_t = true;
+            const int32_t w = a.wq[e];
+            if (a.w16_mode) {
+                s = max(s, shift_needed(w));
+            } else if (w > (1 << 24) || w < -(1 << 24)) {
+                bad_w = true;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s = max(s, __shfl_xor_sync(kFull, s, o));
+        if (s > 15) bad_w = true;
+        const uint32_t mask = s >= 31 ? 0xffffffffu : ((1u << s) - 1u);
+        for (uint64_t e = beg + lane; e < end; e += 32) {
+            const uint32_t tg = a.tgt[e];
+            if (tg >= g0 && tg < g1) a.tgt[e] = tg - g0 + pb;
+            const int32_t w = a.wq[e];
+            if (a.w16_mode) {
+                if (s <= 15 && ((uint32_t)w & mask)) bad_w = true;
+                a.w16[e] = (int16_t)(s <= 15 ? (w >> s) : 0);
+            } else {
+                a.w32[e] = (float)w;
+            }
+        }
+        __syncwarp();
+        bool unsorted = false;
+        for (uint64_t e = beg + 1 + lane; e < end; e += 32)
+            if (a.tgt[e] < a.tgt[e - 1]) unsorted = true;
+        if (__any_sync(kFull, unsorted) && lane == 0) atomicOr(a.unsorted, 1u);
+        const bool any_bad_t = __any_sync(kFull, bad_t);
+        const bool any_bad_w = __any_sync(kFull, bad_w);
+        if (lane == 0) {
+            if (any_bad_t) atomicOr(a.err, kErrBadTarget);
+            if (any_bad_w) atomicOr(a.err, kErrBadWeight);
+            if (a.stdp && exc && s != 0) atomicOr(a.err, kErrPlasticShift);
+            a.meta[pj] = (uint8_t)((a.w16_mode ? s : 0) | (exc ? 0x40 : 0) | ((a.vogels && !exc) ? 0x80 : 0));
+        }
+    }
+}
+
+// Re-expand stored weights to int32 lattice units (CSR order).
+__global__ void k_weights_out(const uint64_t* roff, const uint8_t* meta, const int16_t* w16, const float* w32,
+                              int w16_mode, uint32_t Np, int32_t* out)
+{
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t pj = warp; pj < Np; pj += nwarps) {
+        const uint64_t beg = roff[pj], end = roff[pj + 1];
+        const uint32_t s = meta[pj] & 31u;
+        for (uint64_t e = beg + lane; e < end; e += 32)
+            out[e] = w16_mode ? ((int32_t)w16[e] << s) : __float2int_rz(w32[e]);
+    }
+}
+
+__global__ void k_weights_in(const uint64_t* roff, const uint8_t* meta, const int32_t* in, int w16_mode,
+                             uint32_t Np, int16_t* w16, float* w32, unsigned int* err)
+{
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t pj = warp; pj < Np; pj += nwarps) {
+        const uint64_t beg = roff[pj], end = roff[pj + 1];
+        const uint32_t s = meta[pj] & 31u;
+        for (uint64_t e = beg + lane; e < end; e += 32) {
+            const int32_t w = in[e];
+            if (w16_mode) {
+                const int32_t c = w >> s;
+                if ((c << s) != w || c > 32767 || c < -32768) atomicOr(err, kErrBadWeight);
+                w16[e] = (int16_t)c;
+            } else {
+                w32[e] = (float)w;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics (binary64 reductions): population rate and mean ISI CV of one
+// instance.  out[0] = spikes, out[1] = sum of CVs, out[2] = neurons with >= 3
+// spikes.
+// ---------------------------------------------------------------------------
+__global__ void k_stats(const uint32_t* cnt, const unsigned long long* sum, const unsigned long long* sq,
+                        uint32_t lo, uint32_t hi, double* out)
+{
+    double s_spk = 0.0, s_cv = 0.0, s_n = 0.0;
+    for (uint32_t i = lo + blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += gridDim.x * blockDim.x) {
+        const uint32_t c = cnt[i];
+        s_spk += (double)c;
+        if (c >= 3) {
+            const double m = (double)sum[i] / (double)(c - 1);
+            const double var = (double)sq[i] / (double)(c - 1) - m * m;
+            s_cv += sqrt(var > 0.0 ? var : 0.0) / m;
+            s_n += 1.0;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        s_spk += __shfl_xor_sync(kFull, s_spk, o);
+        s_cv += __shfl_xor_sync(kFull, s_cv, o);
+        s_n += __shfl_xor_sync(kFull, s_n, o);
+    }
+    if ((threadIdx.x & 31u) == 0) {
+        atomicAdd(out + 0, s_spk);
+        atomicAdd(out + 1, s_cv);
+        atomicAdd(out + 2, s_n);
+    }
+}
+
+}  // namespace snn

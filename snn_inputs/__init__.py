@@ -280,3 +280,29 @@ def batched_sweep(n_nets: int = 256, base_seed: int = 1, n_steps: int = 5000, th
                   **kw) -> Problem:
     return problem(BRUNEL, batched_sweep_params(n_nets, base_seed, **kw), delay=15, n_steps=n_steps,
                    seed=base_seed, threads=threads)
+
+
+def sub_problem(prob: Problem, b: int, n_steps: int | None = None) -> Problem:
+    """Instance b of a batch as a one-instance problem (ids rebased to 0)."""
+    lo, hi = int(prob.inst_off[b]), int(prob.inst_off[b + 1])
+    e0, e1 = int(prob.row_off[lo]), int(prob.row_off[hi])
+    return Problem(model=prob.model, instances=[prob.instances[b]], delay=prob.delay, seed=prob.seed,
+                   n_steps=prob.n_steps if n_steps is None else n_steps, stdp=prob.stdp,
+                   inst_off=np.array([0, hi - lo], np.uint32),
+                   row_off=(prob.row_off[lo:hi + 1] - np.uint64(e0)).astype(np.uint64),
+                   tgt=(prob.tgt[e0:e1] - np.uint32(lo)).astype(np.uint32), w=prob.w[e0:e1].copy())
+
+
+def from_edges(model: int, inst: Instance, edges, weights, *, delay: int, n_steps: int, seed: int = 1,
+               stdp: bool = False) -> Problem:
+    """A one-instance problem from an explicit edge list [(src, tgt)] and
+    per-edge lattice weights (rows sorted by target)."""
+    order = sorted(range(len(edges)), key=lambda k: edges[k])
+    row_off = np.zeros(inst.n + 1, np.uint64)
+    for s, _ in edges:
+        row_off[s + 1] += 1
+    row_off = np.cumsum(row_off).astype(np.uint64)
+    tgt = np.array([edges[k][1] for k in order], np.uint32)
+    w = np.array([weights[k] for k in order], np.int32)
+    return Problem(model=model, instances=[inst], delay=delay, seed=seed, n_steps=n_steps, stdp=stdp,
+                   inst_off=np.array([0, inst.n], np.uint32), row_off=row_off, tgt=tgt, w=w)

@@ -1,0 +1,282 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Rasters, neuron state, pending input and (with STDP) weights must agree bit
+for bit: the update is the same binary32 op sequence on both sides, input
+is integer, and the random draws come from the same counter-based
+generator implemented independently on each side.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import snn_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+RECV = {"global": 1, "tiled": 2}
+
+
+def _fields(prob):
+    f = ["V", "r", "acc0"]
+    if prob.model == si.VOGELS:
+        f += ["ge", "gi", "acc1"]
+    if prob.stdp:
+        f += ["x", "y", "w"]
+    return f
+
+
+def run_gpu(snn, prob, n_steps=None, *, w16=True, receive="global", overrides=(), state=None, chunk=None):
+    """Simulate through the C ABI; overrides (step, id, V) are written
+    between steps, before that step's update, like the oracle applies them."""
+    n_steps = prob.n_steps if n_steps is None else n_steps
+    cap = prob.n * max(n_steps, 1) // 10 + 4096
+    net = snn.Network(prob, w16=w16, receive=RECV[receive], log_capacity=cap)
+    try:
+        if state:
+            for k, v in state.items():
+                net.write(k, v)
+        t = 0
+        for (ts, i, v) in sorted(overrides):
+            if ts > t:
+                net.step(ts - t)
+                t = ts
+            V = net.read("V")
+            V[i] = v
+            net.write("V", V)
+        while t < n_steps:
+            k = n_steps - t if chunk is None else min(chunk, n_steps - t)
+            net.step(k)
+            t += k
+        net.sync()
+        steps, ids = net.spikes()
+        out = {f: net.read(f) for f in _fields(prob)}
+        out.update(steps=steps, ids=ids, counters=net.counters())
+        return out
+    finally:
+        net.close()
+
+
+def assert_parity(g, o, prob):
+    assert len(g["ids"]) == len(o["ids"]), (len(g["ids"]), len(o["ids"]))
+    assert np.array_equal(g["steps"], o["steps"])
+    assert np.array_equal(g["ids"], o["ids"])
+    for f in _fields(prob):
+        a, b = np.asarray(g[f]), np.asarray(o[f])
+        if a.dtype == np.float32:
+            a, b = a.view(np.uint32), b.astype(np.float32).view(np.uint32)
+        assert np.array_equal(a, b), f"field {f} differs at {np.flatnonzero(a != b)[:8]}"
+    assert g["counters"]["events"] == o["events"]
+    assert g["counters"]["spikes"] == len(o["ids"])
+
+
+_cache = {}
+
+
+def oracle_run(key, prob, **kw):
+    if key not in _cache:
+        _cache[key] = oracle.run(prob, **kw)
+    return _cache[key]
+
+
+# ------------------------------------------------------------------ the configs
+@pytest.mark.parametrize("w16", [True, False])
+@pytest.mark.parametrize("receive", ["global", "tiled"])
+def test_vogels_4k_full(gpu, w16, receive):
+    """Vogels-Abbott, 4,000 neurons, 2 % connectivity, 1,000 steps."""
+    prob = si.vogels_4k(seed=1, n_steps=1000)
+    o = oracle_run("v4k", prob)
+    g = run_gpu(gpu, prob, w16=w16, receive=receive)
+    assert len(o["ids"]) > 1000
+    assert_parity(g, o, prob)
+
+
+@pytest.mark.parametrize("receive", ["global", "tiled"])
+def test_brunel_12k5_full(gpu, receive):
+    """Brunel, 12,500 neurons, C_E 1,000 / C_I 250, 15-step delay, 10,000 steps."""
+    prob = si.brunel_12k5(seed=1, n_steps=10000)
+    o = oracle_run("b12k5", prob)
+    g = run_gpu(gpu, prob, w16=True, receive=receive)
+    assert len(o["ids"]) > 100000
+    assert_parity(g, o, prob)
+
+
+@pytest.mark.parametrize("w16", [True, False])
+@pytest.mark.parametrize("receive", ["global", "tiled"])
+def test_brunel_stdp_small(gpu, w16, receive):
+    """Brunel+ at 4,000 neurons (in-degree 400), STDP, 15-step delay."""
+    prob = si.brunel_stdp_100k(seed=2, n_steps=3000, n=4000, k=400)
+    o = oracle_run("bstdp4k", prob)
+    g = run_gpu(gpu, prob, w16=w16, receive=receive)
+    assert len(o["ids"]) > 1000
+    assert not np.array_equal(o["w"], prob.w)  # plasticity did something
+    assert_parity(g, o, prob)
+
+
+@pytest.mark.parametrize("receive", ["global", "tiled"])
+def test_batched_uneven_parity(gpu, receive):
+    """A batch of uneven Brunel networks in one context equals the oracle
+    on the whole batch."""
+    prob = si.batched_sweep(n_nets=12, base_seed=3, n_steps=1500, n_lo=37, n_hi=6000)
+    o = oracle_run("batch12", prob)
+    g = run_gpu(gpu, prob, receive=receive, chunk=700)
+    assert_parity(g, o, prob)
+
+
+def test_batched_instance_equals_alone(gpu):
+    """Every instance of a batch behaves as if it ran alone (its Philox key
+    is its instance index)."""
+    prob = si.batched_sweep(n_nets=6, base_seed=5, n_steps=800, n_lo=300, n_hi=3000)
+    g = run_gpu(gpu, prob, receive="tiled")
+    for b in range(6):
+        sub = si.sub_problem(prob, b)
+        o = oracle.run(sub, inst_key0=b)
+        lo, hi = int(prob.inst_off[b]), int(prob.inst_off[b + 1])
+        m = (g["ids"] >= lo) & (g["ids"] < hi)
+        assert np.array_equal(g["steps"][m], o["steps"])
+        assert np.array_equal(g["ids"][m] - lo, o["ids"])
+
+
+# ------------------------------------------------------------------ timing of the pipeline
+@pytest.mark.parametrize("d", [1, 2, 15, 16])
+@pytest.mark.parametrize("model", [si.VOGELS, si.BRUNEL])
+def test_forced_spike_arrives_after_d_steps(gpu, d, model):
+    """A spike forced at step tau reaches its targets' update at tau + d."""
+    if model == si.VOGELS:
+        inst = si.vogels_instance(300)
+        w_e, w_i = 106168, -589824
+    else:
+        inst = si.brunel_instance(300, k=0)
+        inst.lam = 0.0
+        w_e, w_i = 6554, -32768
+    inst.n_exc = 240
+    edges = [(0, 5), (0, 77), (0, 299), (250, 5), (250, 6)]
+    w = [w_e, w_e, w_e, w_i, w_i]
+    prob = si.from_edges(model, inst, edges, w, delay=d, n_steps=40)
+    ov = [(7, 0, 1000.0), (9, 250, 1000.0)]
+    o = oracle.run(prob, overrides=ov)
+    for receive in ("global", "tiled"):
+        g = run_gpu(gpu, prob, overrides=ov, receive=receive)
+        assert_parity(g, o, prob)
+
+
+@pytest.mark.parametrize("d", [1, 3])
+def test_relay_network(gpu, d):
+    """Listing 1's ping-pong network: S_{t+d} = out-neighbours(S_t)."""
+    rng = np.random.Generator(np.random.PCG64(1))
+    edges = [(j, i) for j in range(100) for i in range(100, 200) if rng.random() < 0.05]
+    edges += [(j, i) for j in range(100, 200) for i in range(100) if rng.random() < 0.05]
+    inst = si.brunel_instance(200, k=0)
+    inst.n_exc, inst.tau_m, inst.v_th, inst.v_reset, inst.refractory_steps, inst.lam = 200, 1e-6, 0.05, 0.0, 0, 0.0
+    prob = si.from_edges(si.BRUNEL, inst, edges, [6554] * len(edges), delay=d, n_steps=60)
+    acc0 = np.zeros(200, np.int32)
+    acc0[:100] = 6554
+    state = {"V": np.zeros(200, np.float32), "acc0": acc0}
+    ostate = {"V": np.zeros(200, np.float32), "ge": np.zeros(200, np.float32), "gi": np.zeros(200, np.float32),
+              "r": np.zeros(200, np.int32), "x": np.zeros(200, np.float32), "y": np.zeros(200, np.float32),
+              "acc0": acc0, "acc1": np.zeros(200, np.int32), "w": prob.w.copy()}
+    o = oracle.run(prob, state=ostate)
+    g = run_gpu(gpu, prob, state=state, receive="tiled")
+    assert len(o["ids"]) > 500
+    assert_parity(g, o, prob)
+
+
+# ------------------------------------------------------------------ edge cases
+def test_empty_graph_and_ragged_instances(gpu):
+    """No edges at all, instances of 1, 7, 255, 257 and 1000 neurons."""
+    insts = [si.brunel_instance(n, k=0, nu_ratio=3.0) for n in (1, 7, 255, 257, 1000)]
+    prob = si.problem(si.BRUNEL, insts, delay=2, n_steps=700, seed=9)
+    assert prob.n_edges == 0
+    o = oracle.run(prob)
+    for receive in ("global", "tiled"):
+        assert_parity(run_gpu(gpu, prob, receive=receive), o, prob)
+
+
+def test_stdp_delay_one(gpu):
+    prob = si.brunel_stdp_100k(seed=4, n_steps=800, n=1500, k=150)
+    prob.delay = 1
+    o = oracle.run(prob)
+    assert_parity(run_gpu(gpu, prob, receive="tiled"), o, prob)
+
+
+def test_unsorted_rows(gpu):
+    """Rows need not be sorted: the global receive takes them; the tiled one
+    refuses them with an argument error."""
+    prob = si.brunel_12k5(seed=3, n_steps=300)
+    rng = np.random.Generator(np.random.PCG64(0))
+    tgt, w = prob.tgt.copy(), prob.w.copy()
+    for j in range(0, prob.n, 97):
+        a, b = int(prob.row_off[j]), int(prob.row_off[j + 1])
+        p = rng.permutation(b - a)
+        tgt[a:b], w[a:b] = tgt[a:b][p], w[a:b][p]
+    prob.tgt, prob.w = tgt, w
+    o = oracle.run(prob)
+    assert_parity(run_gpu(gpu, prob, receive="global"), o, prob)
+    with pytest.raises(gpu.SnnError) as ei:
+        run_gpu(gpu, prob, receive="tiled")
+    assert ei.value.status == -1
+
+
+def test_invalid_graphs_are_rejected(gpu):
+    base = si.brunel_12k5(seed=1, n_steps=10)
+    # a target outside the source's instance
+    two = si.batched_sweep(n_nets=2, base_seed=1, n_steps=10, n_lo=500, n_hi=600)
+    bad = two.tgt.copy()
+    bad[0] = int(two.inst_off[1]) + 3
+    with pytest.raises(gpu.SnnError) as ei:
+        gpu.Network(si.Problem(**{**two.__dict__, "tgt": bad}))
+    assert ei.value.status == -1
+    # a row whose weights are not one shift of int16 codes
+    w = base.w.copy()
+    w[int(base.row_off[5])] = 32769
+    with pytest.raises(gpu.SnnError) as ei:
+        gpu.Network(si.Problem(**{**base.__dict__, "w": w}), w16=True)
+    assert ei.value.status == -1
+    # the same weights are fine as binary32 lattice values
+    gpu.Network(si.Problem(**{**base.__dict__, "w": w}), w16=False).close()
+
+
+def test_log_overflow_is_reported(gpu):
+    prob = si.brunel_12k5(seed=1, n_steps=400)
+    net = gpu.Network(prob, log_capacity=1000)
+    net.step(400)
+    with pytest.raises(gpu.SnnError) as ei:
+        net.sync()
+    assert ei.value.status == -4
+    net.log_clear()
+    net.step(1)
+    net.sync()
+    net.close()
+
+
+def test_reset_repeats_the_run(gpu):
+    prob = si.brunel_stdp_100k(seed=5, n_steps=600, n=2000, k=200)
+    net = gpu.Network(prob, receive=RECV["tiled"], log_capacity=1 << 20)
+    net.step(600)
+    a = net.spikes()
+    wa = net.read("w")
+    net.reset()
+    net.step(600)
+    b = net.spikes()
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(wa, net.read("w"))
+    net.close()
+
+
+def test_stats_match_raster(gpu):
+    """The binary64 device reductions equal rate and ISI CV computed from
+    the raster."""
+    prob = si.brunel_12k5(seed=2, n_steps=2000)
+    net = gpu.Network(prob, stats=True, log_capacity=1 << 22)
+    net.step(200)
+    net.stats_clear()
+    net.step(1800)
+    rate, cv = net.stats(0)
+    steps, ids = net.spikes(200, 2000)
+    net.close()
+    assert abs(rate - len(ids) / prob.n / 0.18) < 1e-9 * rate
+    order = np.lexsort((steps, ids))
+    s, i = steps[order].astype(np.float64), ids[order]
+    starts = np.flatnonzero(np.r_[True, i[1:] != i[:-1]])
+    ends = np.r_[starts[1:], len(i)]
+    cvs = [np.diff(s[a:b]).std() / np.diff(s[a:b]).mean() for a, b in zip(starts, ends) if b - a >= 3]
+    assert abs(cv - np.mean(cvs)) < 1e-9
