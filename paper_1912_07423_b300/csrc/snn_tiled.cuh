@@ -112,8 +112,7 @@ __global__ void __launch_bounds__(kTiledThreads) k_receive_tiled(Net n, const Ti
         const int4* s1 = reinterpret_cast<const int4*>(acc_s + T.len);
         for (uint32_t i = threadIdx.x; i < T.len / 4; i += blockDim.x) g1[i] = s1[i];
     }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    // every lane of a warp counted the same segments: lane 0 reports them
     if (lane == 0 && ev) atomicAdd(&n.ctl->events, ev);
     if (bad) atomicOr(&n.ctl->err, kErrBadTarget);
 }

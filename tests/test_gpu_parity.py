@@ -29,7 +29,8 @@ def run_gpu(snn, prob, n_steps=None, *, w16=True, receive="global", overrides=()
     """Simulate through the C ABI; overrides (step, id, V) are written
     between steps, before that step's update, like the oracle applies them."""
     n_steps = prob.n_steps if n_steps is None else n_steps
-    cap = prob.n * max(n_steps, 1) // 10 + 4096
+    total = prob.n * max(n_steps, 1)
+    cap = total + 4096 if total < 10_000_000 else total // 10 + 4096
     net = snn.Network(prob, w16=w16, receive=RECV[receive], log_capacity=cap)
     try:
         if state:
