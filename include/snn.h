@@ -196,6 +196,32 @@ snn_status snn_stats(snn_ctx* ctx, uint32_t inst, double* rate_hz, double* isi_c
 /* Start the statistics window at the current step. */
 snn_status snn_stats_clear(snn_ctx* ctx);
 
+/* Population rate and mean ISI CV computed without allocating any device
+ * memory.  The paper has no counterpart; this exists for callers that cannot
+ * call cudaMalloc when they want the numbers: applications that give the
+ * GPU's memory to their own fixed arena at start-up, and latency-critical
+ * loops where an allocation may synchronise the device.
+ *
+ * Inputs are device arrays of n neurons: count[i] spikes in the window,
+ * isi_sum[i] and isi_sq[i] the sum and the sum of squares of the neuron's
+ * inter-spike intervals in steps (the layout snn_stats keeps internally).
+ * window_steps * dt_ms is the window length.  Results go to *rate_hz and
+ * *isi_cv (host), with the same definitions as snn_stats; the partial sums
+ * are added in a fixed order, so repeated calls give identical results.
+ * Work is enqueued on `stream` (a cudaStream_t, NULL for the legacy default
+ * stream) and the call waits for it.
+ *
+ * Scratch: a static device array of 8192 * 3 + 3 doubles (192 KB) inside
+ * the library, held by every GPU that loads the library until exit, so n is
+ * limited to 16,777,216; larger n returns SNN_E_ARG.  The first call on a
+ * device looks the array's address up (cudaGetSymbolAddress); make that first
+ * call before any stream capture begins.  All calls share the array: calls
+ * that overlap on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller. */
+snn_status snn_rate_cv_static(const uint32_t* count, const unsigned long long* isi_sum,
+                              const unsigned long long* isi_sq, uint32_t n, uint64_t window_steps, double dt_ms,
+                              void* stream, double* rate_hz, double* isi_cv);
+
 /* What the context chose and holds. */
 typedef struct {
     uint32_t receive;      /* SNN_RECV_GLOBAL or SNN_RECV_TILED (after snn_build_graph) */

@@ -92,6 +92,8 @@ def load():
                                   ctypes.POINTER(ctypes.c_double)]),
                 "snn_stats_clear": (S, [_vp]),
                 "snn_get_info": (S, [_vp, ctypes.POINTER(Info)]),
+                "snn_rate_cv_static": (S, [_vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double, _vp,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
                 "snn_last_error": (ctypes.c_char_p, [_vp]),
                 "snn_status_string": (ctypes.c_char_p, [ctypes.c_int]),
                 "snn_destroy": (None, [_vp]),
@@ -108,7 +110,7 @@ def exported_symbols() -> list:
     return ["snn_create", "snn_build_graph", "snn_reset", "snn_step", "snn_step_profiled", "snn_sync",
             "snn_read_spikes",
             "snn_log_clear", "snn_read_state", "snn_write_state", "snn_counters", "snn_stats", "snn_stats_clear",
-            "snn_get_info", "snn_last_error", "snn_status_string", "snn_destroy"]
+            "snn_get_info", "snn_rate_cv_static", "snn_last_error", "snn_status_string", "snn_destroy"]
 
 
 def _params_array(instances) -> ctypes.Array:
