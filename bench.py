@@ -55,6 +55,8 @@ def peaks():
 def workload(name: str, rank: int):
     if name == "batched_sweep_256":
         return si.batched_sweep(256, base_seed=1 + 1000 * rank, n_steps=0)
+    if name.startswith("batched_sweep_"):  # a smaller sweep of the same recipe (profiling)
+        return si.batched_sweep(int(name.rsplit("_", 1)[1]), base_seed=1 + 1000 * rank, n_steps=0)
     if name == "vogels_1m":
         return si.vogels_1m(seed=1 + rank, n_steps=0)
     if name == "brunel_12k5":

@@ -40,7 +40,8 @@ class SnnError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("model", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("delay", ctypes.c_uint32),
                 ("n_inst", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("log_capacity", ctypes.c_uint64),
-                ("receive", ctypes.c_uint32), ("steps_per_graph", ctypes.c_uint32)]
+                ("receive", ctypes.c_uint32), ("steps_per_graph", ctypes.c_uint32), ("tune_steps", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 class Params(ctypes.Structure):
@@ -157,8 +158,8 @@ class Network:
     """
 
     def __init__(self, problem, *, w16: bool = True, receive: int = RECV_AUTO, log_capacity: int | None = None,
-                 stats: bool = False, steps_per_graph: int = 0, device: str = "cuda:0", stream=None,
-                 build_graph: bool = True):
+                 stats: bool = False, steps_per_graph: int = 0, tune_steps: int = 0, device: str = "cuda:0",
+                 stream=None, build_graph: bool = True):
         import torch
         if not torch.cuda.is_available():
             raise SnnError(-3, "no CUDA device: libsnn has no CPU fallback")
@@ -173,7 +174,7 @@ class Network:
         if log_capacity is None:
             log_capacity = max(1 << 16, int(problem.n) * 64)
         self.cfg = Config(problem.model, flags, problem.delay, len(problem.instances), problem.seed, log_capacity,
-                          receive, steps_per_graph)
+                          receive, steps_per_graph, tune_steps, 0)
         self.params = _params_array(problem.instances)
         ctx = _vp()
         st = self.lib.snn_create(ctypes.byref(self.cfg), ctypes.addressof(self.params), ctypes.byref(self.dev),

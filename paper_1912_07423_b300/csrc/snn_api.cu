@@ -65,6 +65,9 @@ struct snn_ctx {
     uint32_t* cpre = nullptr;
     TiledPlan tiled{};
     bool use_tiled = false;
+    bool tuned = false;                // tiles re-cut by measured work
+    std::vector<uint64_t> inst_edges;  // synapses of each instance
+    uint4* rinfo = nullptr;            // row records (start, length, meta)
 
     // CUDA graphs: one step, and steps_per_graph steps
     cudaGraphExec_t g1 = nullptr, gk = nullptr;
@@ -292,8 +295,45 @@ snn_status init_state(snn_ctx* c)
     CUDA_TRY(c, cudaMemsetAsync(c->net.count, 0, (size_t)c->cr * 4, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->net.icount, 0, (size_t)c->cr * c->cfg.n_inst * 4, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->net.lbase, 0, (size_t)c->cr * 8, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->net.inst_spikes, 0, (size_t)c->cfg.n_inst * 8, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->net.tile_ctr, 0, 2 * sizeof(unsigned int), c->stream));
     c->host_steps = 0;
     return SNN_OK;
+}
+
+// Cut the tiles of the tiled receive; work[b] = expected delivered edges of
+// instance b per step (null: proportional to its synapses).
+snn_status plan_tiles(snn_ctx* c, const double* work)
+{
+    const uint32_t max_len = c->vogels ? 28672u : 57344u;  // 224 KB of accumulators: one CTA per SM
+    return tiled_plan(c->tiled, c->net, c->params.data(), c->pbase.data(), c->cfg.n_inst, c->vogels ? 2 : 1, max_len,
+                      work, c->inst_edges.data(), sm_count(), [c](size_t b) { return dev_alloc(c, b); },
+                      [c](void* p) { dev_free(c, p); }, c->stream);
+}
+
+// Re-cut the tiles by the spikes measured so far (results do not depend on
+// the tiling, only the balance across SMs does), then re-capture the graphs.
+snn_status retune(snn_ctx* c)
+{
+    c->tuned = true;
+    std::vector<unsigned long long> spk(c->cfg.n_inst, 0);
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    CUDA_TRY(c, cudaMemcpy(spk.data(), c->net.inst_spikes, spk.size() * 8, cudaMemcpyDeviceToHost));
+    std::vector<double> work(c->cfg.n_inst, 0.0);
+    double total = 0.0;
+    for (uint32_t b = 0; b < c->cfg.n_inst; ++b) {
+        const double deg = c->params[b].n ? (double)c->inst_edges[b] / c->params[b].n : 0.0;
+        // delivered edges plus the fixed work per spike and tile (row record, splits)
+        work[b] = (double)spk[b] * (deg + 8.0);
+        total += work[b];
+    }
+    if (total <= 0.0) return SNN_OK;
+    snn_status st = plan_tiles(c, work.data());
+    if (st != SNN_OK) return fail(c, st, "re-cutting the tiles failed");
+    drop_graphs(c);
+    st = capture(c, 1, &c->g1);
+    if (st == SNN_OK && c->k_steps > 1) st = capture(c, c->k_steps, &c->gk);
+    return st;
 }
 
 }  // namespace
@@ -390,6 +430,8 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     n.count = alloc_n<unsigned int>(c, c->cr);
     n.icount = alloc_n<unsigned int>(c, (size_t)c->cr * cfg->n_inst);
     n.lbase = alloc_n<unsigned long long>(c, c->cr);
+    n.inst_spikes = alloc_n<unsigned long long>(c, cfg->n_inst);
+    n.tile_ctr = alloc_n<unsigned int>(c, 2);
     c->ctl = alloc_n<Ctl>(c, 1);
     c->inst = alloc_n<InstDev>(c, cfg->n_inst);
     c->inst_of_w32 = alloc_n<uint32_t>(c, Npz / 32);
@@ -398,7 +440,8 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     n.r = alloc_n<uint8_t>(c, Npz);
     n.acc0 = alloc_n<int32_t>(c, Npz);
     n.q = alloc_n<uint32_t>(c, (size_t)c->D * Npz);
-    bool ok = c->ctl && c->inst && c->inst_of_w32 && c->pois && n.V && n.r && n.acc0 && n.q && n.count && n.icount && n.lbase;
+    bool ok = c->ctl && c->inst && c->inst_of_w32 && c->pois && n.V && n.r && n.acc0 && n.q && n.count && n.icount && n.lbase &&
+              n.inst_spikes && n.tile_ctr;
     if (c->vogels) {
         n.ge = alloc_n<float>(c, Npz);
         n.gi = alloc_n<float>(c, Npz);
@@ -464,8 +507,9 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
     tiled_free(c->tiled, [c](void* p) { dev_free(c, p); });
     c->use_tiled = false;
     for (void* p : {(void*)c->roff, (void*)c->tgt, (void*)c->w16p, (void*)c->w32p, (void*)c->meta, (void*)c->coff,
-                    (void*)c->cedge, (void*)c->cpre, (void*)c->w_init})
+                    (void*)c->cedge, (void*)c->cpre, (void*)c->w_init, (void*)c->rinfo})
         dev_free(c, p);
+    c->rinfo = nullptr;
     c->roff = nullptr; c->tgt = nullptr; c->w16p = nullptr; c->w32p = nullptr; c->meta = nullptr;
     c->coff = nullptr; c->cedge = nullptr; c->cpre = nullptr; c->w_init = nullptr;
     c->graph_loaded = false;
@@ -594,7 +638,13 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
         CUDA_TRY(c, cudaStreamSynchronize(s));
     }
 
+    c->rinfo = alloc_n<uint4>(c, Np);
+    if (!c->rinfo) return fail(c, SNN_E_NOMEM, "row records");
+    k_row_info<<<(uint32_t)sm_count() * 8, 256, 0, s>>>(c->roff, c->meta, Np, c->rinfo);
+    CUDA_TRY(c, cudaGetLastError());
+
     Net& n = c->net;
+    n.rinfo = c->rinfo;
     n.roff = c->roff;
     n.tgt = c->tgt;
     n.w16 = c->w16p;
@@ -605,13 +655,13 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
     n.cpre = c->cpre;
 
     // receive strategy: the target-tiled form needs sorted rows
+    c->inst_edges.assign(c->cfg.n_inst, 0);
+    for (uint32_t b = 0; b < c->cfg.n_inst; ++b)
+        c->inst_edges[b] = row_off[c->g_off[b + 1]] - row_off[c->g_off[b]];
     c->use_tiled = false;
+    c->tuned = false;
     if (c->cfg.receive != SNN_RECV_GLOBAL) {
-        snn_status st = SNN_E_ARG;
-        if (c->rows_sorted)
-            st = tiled_plan(c->tiled, c->net, c->params.data(), c->pbase.data(), c->cfg.n_inst, c->vogels ? 2 : 1,
-                            c->vogels ? 7168u : 14336u, nullptr, [c](size_t b) { return dev_alloc(c, b); },
-                            [c](void* p) { dev_free(c, p); }, s);
+        snn_status st = c->rows_sorted ? plan_tiles(c, nullptr) : SNN_E_ARG;
         if (st == SNN_OK) {
             c->use_tiled = true;
         } else {
@@ -652,12 +702,26 @@ snn_status snn_step(snn_ctx* c, uint32_t n_steps)
     if (!c) return SNN_E_ARG;
     if (!c->graph_loaded) return fail(c, SNN_E_STATE, "snn_step before snn_build_graph");
     uint32_t left = n_steps;
+    const uint64_t tune_at = c->cfg.tune_steps ? c->cfg.tune_steps : 128;
+    if (c->use_tiled && !c->tuned && c->cfg.tune_steps != 0xffffffffu && c->host_steps + left >= tune_at) {
+        // run up to the tuning step, re-cut the tiles, go on
+        uint32_t first = (uint32_t)(tune_at > c->host_steps ? tune_at - c->host_steps : 0);
+        left -= first;
+        c->host_steps += first;
+        while (c->gk && first >= c->k_steps) {
+            CUDA_TRY(c, cudaGraphLaunch(c->gk, c->stream));
+            first -= c->k_steps;
+        }
+        while (first--) CUDA_TRY(c, cudaGraphLaunch(c->g1, c->stream));
+        snn_status st = retune(c);
+        if (st != SNN_OK) return st;
+    }
+    c->host_steps += left;
     while (c->gk && left >= c->k_steps) {
         CUDA_TRY(c, cudaGraphLaunch(c->gk, c->stream));
         left -= c->k_steps;
     }
     while (left--) CUDA_TRY(c, cudaGraphLaunch(c->g1, c->stream));
-    c->host_steps += n_steps;
     return SNN_OK;
 }
 

@@ -63,6 +63,8 @@ struct Net {
     unsigned int* count;       // |S_t| over all instances at [t % cr]
     unsigned int* icount;      // |S_t| of instance b at [(t % cr) * n_inst + b]
     unsigned long long* lbase; // log position of S_t's first spike at [t % cr]
+    unsigned long long* inst_spikes; // spikes of each instance since the last reset
+    unsigned int* tile_ctr;    // tiled receive: next tile to take, at [t & 1]
     const InstDev* inst;
     const uint32_t* inst_of_w32;  // instance of each 32-neuron word
     const uint32_t* pois;         // Poisson thresholds, kPoissonCap per instance
@@ -79,6 +81,7 @@ struct Net {
     int16_t* w16;
     float* w32;
     const uint8_t* meta;
+    const uint4* rinfo;     // per padded row: start (lo, hi), length, meta -- one load per spike
     const uint64_t* coff;   // STDP: plastic in-edges per padded post id
     const uint32_t* cedge;  // STDP: edge index of each plastic in-edge
     const uint32_t* cpre;   // STDP: padded presynaptic id of each plastic in-edge

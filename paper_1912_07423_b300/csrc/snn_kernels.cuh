@@ -228,8 +228,12 @@ __global__ void k_step_end(Net n)
 {
     const unsigned long long t = n.ctl->t;
     const uint32_t sc = (uint32_t)(t & (n.cr - 1)), sn = (uint32_t)((t + 1) & (n.cr - 1));
-    for (uint32_t b = threadIdx.x; b < n.n_inst; b += blockDim.x) n.icount[(size_t)sn * n.n_inst + b] = 0;
+    for (uint32_t b = threadIdx.x; b < n.n_inst; b += blockDim.x) {
+        n.inst_spikes[b] += n.icount[(size_t)sc * n.n_inst + b];
+        n.icount[(size_t)sn * n.n_inst + b] = 0;
+    }
     if (threadIdx.x == 0) {
+        n.tile_ctr[(t + 1) & 1ull] = 0;
         const uint32_t c = n.count[sc];
         n.ctl->spikes += c;
         n.lbase[sn] = n.lbase[sc] + c;
@@ -524,6 +528,15 @@ __global__ void k_weights_in(const uint64_t* roff, const uint8_t* meta, const in
                 w32[e] = (float)w;
             }
         }
+    }
+}
+
+// Row records for the receive: start, length and meta of every padded row.
+__global__ void k_row_info(const uint64_t* roff, const uint8_t* meta, uint32_t Np, uint4* rinfo)
+{
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < Np; j += gridDim.x * blockDim.x) {
+        const uint64_t a = roff[j], b = roff[j + 1];
+        rinfo[j] = make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)(b - a), meta[j]);
     }
 }
 

@@ -3,20 +3,34 @@
 // The paper delivers a spike with one CUDA block walking the spiker's
 // adjacency row and updating the recipients with atomics (Section III-A-2).
 // On a B300 the random 32-bit red.global.add that such a walk issues runs at
-// about 2e11 per second into L2, a fifth of what HBM can stream in edges, so
-// this form divides the work by TARGET instead: every network instance is cut
-// into tiles of consecutive neuron ids small enough for one CTA's shared
-// memory.  The CTA of a tile walks every spike of its instance, reads only the
-// segment of the spiker's (sorted) row that falls inside the tile, adds the
-// weights with shared-memory atomics, and finally stores the whole tile to
-// the global accumulators with coalesced writes.  Each edge is read once per
-// step; no global atomics are issued.  Segment bounds of rows that span
-// several tiles come from a split table built once with the graph.
+// about 2e11 per second into L2 (a fifth of what HBM can stream in edges),
+// while shared-memory atomics run about five times faster.  This form keeps
+// the walk over whole rows but adds into accumulators held in the CTA's
+// shared memory:
+//
+//   * a network instance is a TILE when its accumulators fit one CTA's shared
+//     memory; a larger instance is cut by target id into several tiles, and
+//     the segment of a (sorted) row inside each tile comes from a split table
+//     built once with the graph;
+//   * a tile whose expected work is large is split by SPIKES into P parts:
+//     part p delivers its share of the instance's spikes into a private copy
+//     of the tile's accumulators.  A part that is alone stores its copy to the
+//     global accumulators; otherwise it stores it to a partial buffer, and a
+//     second kernel adds the P partials up (coalesced, L2-resident).
+//
+// Every edge is read once per step, in whole coalesced rows; no global
+// atomics are issued.  The (tile, part) work items are listed heaviest first
+// and a persistent grid takes them one after the other from an atomic
+// counter.  Expected work comes from the edges at first and from the spike
+// counts measured on the first steps after the one-time re-plan; results do
+// not depend on the plan, only the balance across SMs does.
 #pragma once
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <functional>
+#include <numeric>
 #include <vector>
 
 #include "../../include/snn.h"
@@ -25,100 +39,169 @@
 namespace snn {
 
 struct TileDev {
-    uint32_t inst;            // instance
-    uint32_t lo, len;         // padded id range [lo, lo + len); len is a multiple of 256
-    uint32_t tau, ntiles;     // tile index inside the instance, tiles of the instance
-    uint32_t pad;
-    unsigned long long split; // base of the instance's split table: (ntiles-1) x n_b uint32
+    uint32_t inst;                  // instance
+    uint32_t lo, len;               // padded id range [lo, lo + len); len is a multiple of 256
+    uint32_t tau, ntiles;           // tile index inside the instance, tiles of the instance
+    uint32_t nparts;                // spike parts of this tile
+    unsigned long long split;       // base of the instance's split table: n_b rows x (ntiles-1) uint32
+    unsigned long long part_base;   // base of the tile's partials (nparts x len int32) if nparts > 1
+};
+
+struct MergeDev {  // one chunk of a multi-part tile to add up
+    uint32_t tile, off, len, pad;
 };
 
 struct TiledPlan {
     TileDev* tiles = nullptr;
+    uint32_t* items = nullptr;   // (tile << 8 | part), heaviest first
     uint32_t* split = nullptr;
-    uint32_t n_tiles = 0;
+    int32_t* partial = nullptr;
+    MergeDev* merges = nullptr;
+    uint32_t n_tiles = 0, n_items = 0, n_merges = 0;
     uint32_t max_len = 0;
+    uint32_t grid = 0;
     int channels = 1;
-    int threads = 512;
+    int threads = 1024;
     size_t smem = 0;
 };
 
-constexpr int kTiledThreads = 512;
+constexpr int kTiledThreads = 1024;
+constexpr int kUnroll = 8;         // edges in flight per lane
+constexpr uint32_t kMaxParts = 255;
+constexpr uint32_t kMergeChunk = 4096;
+
+template <bool W16>
+__device__ __forceinline__ int32_t weight_at(const Net& n, uint64_t e, uint32_t shift)
+{
+    return W16 ? ((int32_t)__ldg(n.w16 + e) << shift) : __float2int_rz(__ldg(n.w32 + e));
+}
 
 template <bool W16, int CH>
-__global__ void __launch_bounds__(kTiledThreads) k_receive_tiled(Net n, const TileDev* __restrict__ tiles,
-                                                                 const uint32_t* __restrict__ split)
+__global__ void __launch_bounds__(kTiledThreads, 1) k_receive_tiled(Net n, const TileDev* __restrict__ tiles,
+                                                                    const uint32_t* __restrict__ items,
+                                                                    const uint32_t* __restrict__ split,
+                                                                    int32_t* __restrict__ partial, uint32_t n_items)
 {
-    extern __shared__ int32_t acc_s[];  // CH * len
-    const TileDev T = tiles[blockIdx.x];
-    for (uint32_t i = threadIdx.x; i < CH * T.len; i += blockDim.x) acc_s[i] = 0;
-    __syncthreads();
+    extern __shared__ __align__(16) int32_t acc_s[];  // CH * len of the current tile
+    __shared__ uint32_t s_item;
     const unsigned long long t = n.ctl->t;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    unsigned long long ev = 0;
-    bool bad = false;  // a target outside the tile: the split table does not match the rows
-    if (t + 1 >= n.d) {
-        const unsigned long long ts = t + 1 - n.d;
-        const uint32_t cnt = n.icount[(size_t)(ts & (n.cr - 1)) * n.n_inst + T.inst];
-        const InstDev* I = n.inst + T.inst;
-        const uint32_t pbase = __ldg(&I->pbase), nb = __ldg(&I->n);
+    unsigned int* ctr = n.tile_ctr + (t & 1ull);
+    const bool deliver = t + 1 >= n.d;
+    const unsigned long long ts = deliver ? t + 1 - n.d : 0ull;
+    unsigned long long ev = 0;  // every lane of a warp counts the warp's segments; lane 0 reports
+    bool bad = false;           // a target outside the tile: the split table does not match the rows
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= n_items) break;
+        const uint32_t code = __ldg(items + item);
+        const TileDev T = tiles[code >> 8];
+        const uint32_t part = code & 0xffu;
+        const uint32_t cnt = deliver ? n.icount[(size_t)(ts & (n.cr - 1)) * n.n_inst + T.inst] : 0u;
+        if (cnt == 0) {  // nothing arrives: the update already cleared these accumulators
+            __syncthreads();
+            continue;
+        }
+        for (uint32_t i = threadIdx.x; i < CH * T.len; i += blockDim.x) acc_s[i] = 0;
+        __syncthreads();
+        const uint32_t pbase = __ldg(&n.inst[T.inst].pbase);
         const uint32_t* q = n.q + (size_t)(ts % n.D) * n.Np + pbase;
-        const uint32_t* s_lo = T.tau > 0 ? split + T.split + (size_t)(T.tau - 1) * nb : nullptr;
-        const uint32_t* s_hi = T.tau + 1 < T.ntiles ? split + T.split + (size_t)T.tau * nb : nullptr;
-        for (uint32_t s = warp; s < cnt; s += nwarps) {
+        const uint32_t nsplit = T.ntiles - 1;
+        const uint32_t* sp = split + T.split;
+        const uint32_t s_beg = (uint32_t)((unsigned long long)cnt * part / T.nparts);
+        const uint32_t s_end = (uint32_t)((unsigned long long)cnt * (part + 1) / T.nparts);
+        for (uint32_t s = s_beg + warp; s < s_end; s += nwarps) {
             const uint32_t j = q[s];
-            const uint64_t beg = __ldg(n.roff + j), end = __ldg(n.roff + j + 1);
-            uint64_t sb = beg, se = end;
-            if (s_lo) sb = beg + __ldg(s_lo + (j - pbase));
-            if (s_hi) se = beg + __ldg(s_hi + (j - pbase));
-            const uint32_t meta = __ldg(n.meta + j);
-            const uint32_t shift = meta & 31u;
-            int32_t* a = acc_s + ((CH == 2 && (meta & 0x80u)) ? T.len : 0u) - T.lo;
+            const uint4 r = __ldg(n.rinfo + j);
+            uint64_t sb = ((unsigned long long)r.y << 32) | r.x;
+            uint64_t se = sb + r.z;
+            if (nsplit) {
+                const uint32_t* sj = sp + (size_t)(j - pbase) * nsplit;
+                const uint64_t beg = sb;
+                if (T.tau > 0) sb = beg + __ldg(sj + T.tau - 1);
+                if (T.tau < nsplit) se = beg + __ldg(sj + T.tau);
+            }
+            const uint32_t shift = r.w & 31u;
+            int32_t* a = acc_s + ((CH == 2 && (r.w & 0x80u)) ? T.len : 0u);
             ev += se - sb;
-            uint64_t e = sb + lane;
-            for (; e + 96 < se; e += 128) {
-                uint32_t tg[4];
-                int32_t wv[4];
+            for (uint64_t e0 = sb; e0 < se; e0 += 32 * kUnroll) {
+                uint32_t tg[kUnroll];
+                int32_t wv[kUnroll];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    tg[u] = __ldg(n.tgt + e + 32 * u);
-                    wv[u] = W16 ? ((int32_t)__ldg(n.w16 + e + 32 * u) << shift)
-                                : __float2int_rz(__ldg(n.w32 + e + 32 * u));
+                for (int u = 0; u < kUnroll; ++u) {
+                    const uint64_t e = e0 + 32 * u + lane;
+                    tg[u] = e < se ? __ldg(n.tgt + e) - T.lo : 0xffffffffu;
+                    wv[u] = e < se ? weight_at<W16>(n, e, shift) : 0;
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (tg[u] - T.lo < T.len)
+                for (int u = 0; u < kUnroll; ++u) {
+                    if (e0 + 32 * u + lane >= se) continue;
+                    if (tg[u] < T.len)
                         atomicAdd(a + tg[u], wv[u]);
                     else
                         bad = true;
                 }
             }
-            for (; e < se; e += 32) {
-                const uint32_t tg = __ldg(n.tgt + e);
-                const int32_t wv = W16 ? ((int32_t)__ldg(n.w16 + e) << shift) : __float2int_rz(__ldg(n.w32 + e));
-                if (tg - T.lo < T.len)
-                    atomicAdd(a + tg, wv);
-                else
-                    bad = true;
-            }
         }
+        __syncthreads();
+        // the tile's pending input for the next update, or this part's share of it
+        int4* g0;
+        int4* g1 = nullptr;
+        if (T.nparts == 1) {
+            g0 = reinterpret_cast<int4*>(n.acc0 + T.lo);
+            if (CH == 2) g1 = reinterpret_cast<int4*>(n.acc1 + T.lo);
+        } else {
+            int32_t* base = partial + T.part_base + (size_t)part * CH * T.len;
+            g0 = reinterpret_cast<int4*>(base);
+            if (CH == 2) g1 = reinterpret_cast<int4*>(base + T.len);
+        }
+        const int4* s0 = reinterpret_cast<const int4*>(acc_s);
+        for (uint32_t i = threadIdx.x; i < T.len / 4; i += blockDim.x) g0[i] = s0[i];
+        if (CH == 2) {
+            const int4* s1 = reinterpret_cast<const int4*>(acc_s + T.len);
+            for (uint32_t i = threadIdx.x; i < T.len / 4; i += blockDim.x) g1[i] = s1[i];
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    // the tile's pending input for the next update (whole tile, every step)
-    int4* g0 = reinterpret_cast<int4*>(n.acc0 + T.lo);
-    const int4* s0 = reinterpret_cast<const int4*>(acc_s);
-    for (uint32_t i = threadIdx.x; i < T.len / 4; i += blockDim.x) g0[i] = s0[i];
-    if (CH == 2) {
-        int4* g1 = reinterpret_cast<int4*>(n.acc1 + T.lo);
-        const int4* s1 = reinterpret_cast<const int4*>(acc_s + T.len);
-        for (uint32_t i = threadIdx.x; i < T.len / 4; i += blockDim.x) g1[i] = s1[i];
-    }
-    // every lane of a warp counted the same segments: lane 0 reports them
     if (lane == 0 && ev) atomicAdd(&n.ctl->events, ev);
     if (bad) atomicOr(&n.ctl->err, kErrBadTarget);
 }
 
-// Split table: for row j of a multi-tile instance and inner boundary tau,
-// the offset inside the row of the first target >= the boundary's padded id.
+// Adds the parts of the multi-part tiles into the global accumulators, one
+// chunk of kMergeChunk neurons per block.
+template <int CH>
+__global__ void __launch_bounds__(256) k_merge_parts(Net n, const TileDev* __restrict__ tiles,
+                                                     const MergeDev* __restrict__ merges,
+                                                     const int32_t* __restrict__ partial)
+{
+    const MergeDev M = merges[blockIdx.x];
+    const TileDev T = tiles[M.tile];
+    const unsigned long long t = n.ctl->t;
+    if (t + 1 < n.d) return;
+    const unsigned long long ts = t + 1 - n.d;
+    if (n.icount[(size_t)(ts & (n.cr - 1)) * n.n_inst + T.inst] == 0) return;  // no part wrote anything
+    const int32_t* base = partial + T.part_base;
+    for (uint32_t c = 0; c < CH; ++c) {
+        int32_t* acc = c ? n.acc1 : n.acc0;
+        for (uint32_t i = M.off + threadIdx.x * 4; i < M.off + M.len; i += blockDim.x * 4) {
+            int4 s = make_int4(0, 0, 0, 0);
+            for (uint32_t p = 0; p < T.nparts; ++p) {
+                const int4 v = *reinterpret_cast<const int4*>(base + ((size_t)p * CH + c) * T.len + i);
+                s.x += v.x;
+                s.y += v.y;
+                s.z += v.z;
+                s.w += v.w;
+            }
+            *reinterpret_cast<int4*>(acc + T.lo + i) = s;
+        }
+    }
+}
+
+// Split table of one multi-tile instance: for local row l and inner boundary
+// tau (1..ntiles-1), the offset inside the row of the first target >= the
+// boundary's padded id, stored at [l * (ntiles-1) + tau - 1].
 __global__ void k_split_rows(const uint64_t* roff, const uint32_t* tgt, uint32_t pbase, uint32_t nb,
                              const uint32_t* bounds /* ntiles+1 padded ids */, uint32_t ntiles, uint32_t* split)
 {
@@ -137,7 +220,7 @@ __global__ void k_split_rows(const uint64_t* roff, const uint32_t* tgt, uint32_t
                 else
                     hi = mid;
             }
-            split[(size_t)(tau - 1) * nb + l] = (uint32_t)(lo - beg);
+            split[(size_t)l * (ntiles - 1) + (tau - 1)] = (uint32_t)(lo - beg);
         }
     }
 }
@@ -153,29 +236,47 @@ inline cudaError_t tiled_set_smem(size_t smem)
     return e;
 }
 
-// Cut every instance into tiles of at most max_len padded ids (multiples of
-// 256) and build the split tables of the instances with several tiles.
-// tiles_per_inst, if given, asks for at least that many tiles per instance
-// (load balancing by expected work).  Needs sorted rows.
+inline void tiled_free(TiledPlan& P, const std::function<void(void*)>& release)
+{
+    release(P.tiles);
+    release(P.items);
+    release(P.split);
+    release(P.partial);
+    release(P.merges);
+    P = TiledPlan{};
+}
+
+// Build the plan.  work[b] is the expected delivered edges of instance b per
+// step (any positive scale; null: proportional to its synapses).  An
+// instance is cut by target into tiles of at most max_len padded ids (the
+// shared-memory limit); a tile is split by spikes into parts so that no work
+// item carries more than about total / (items_per_cta * CTAs).  Needs sorted
+// rows when an instance has several tiles.
 inline snn_status tiled_plan(TiledPlan& P, const Net& n, const snn_params* params, const uint32_t* pbase,
-                             uint32_t n_inst, int channels, uint32_t max_len, const uint32_t* tiles_per_inst,
-                             const std::function<void*(size_t)>& alloc, const std::function<void(void*)>& release,
-                             cudaStream_t s)
+                             uint32_t n_inst, int channels, uint32_t max_len, const double* work,
+                             const uint64_t* inst_edges, int sms, const std::function<void*(size_t)>& alloc,
+                             const std::function<void(void*)>& release, cudaStream_t s)
 {
     max_len = std::max<uint32_t>(256, max_len / 256 * 256);
+    std::vector<double> wk(n_inst, 0.0);
+    for (uint32_t b = 0; b < n_inst; ++b) wk[b] = work ? work[b] : (double)inst_edges[b];
+    const double total = std::accumulate(wk.begin(), wk.end(), 0.0);
+
     std::vector<TileDev> tiles;
+    std::vector<double> tile_work;
     std::vector<std::vector<uint32_t>> bounds(n_inst);
+    std::vector<unsigned long long> split_base(n_inst, 0);
     unsigned long long split_total = 0;
+    uint32_t longest = 0;
     for (uint32_t b = 0; b < n_inst; ++b) {
         const uint32_t npad = pbase[b + 1] - pbase[b];
         if (npad == 0) continue;
         const uint32_t m = npad / 256;
-        uint32_t T = (npad + max_len - 1) / max_len;
-        if (tiles_per_inst) T = std::max(T, tiles_per_inst[b]);
-        T = std::min(T, m);
+        const uint32_t T = std::min<uint32_t>((npad + max_len - 1) / max_len, m);
         auto& B = bounds[b];
         B.resize(T + 1);
         for (uint32_t tau = 0; tau <= T; ++tau) B[tau] = pbase[b] + 256u * (uint32_t)((unsigned long long)tau * m / T);
+        split_base[b] = split_total;
         for (uint32_t tau = 0; tau < T; ++tau) {
             TileDev d{};
             d.inst = b;
@@ -183,50 +284,102 @@ inline snn_status tiled_plan(TiledPlan& P, const Net& n, const snn_params* param
             d.len = B[tau + 1] - B[tau];
             d.tau = tau;
             d.ntiles = T;
-            d.split = split_total;
+            d.nparts = 1;
+            d.split = split_base[b];
             tiles.push_back(d);
+            tile_work.push_back(wk[b] * d.len / npad);
+            longest = std::max(longest, d.len);
         }
         if (T > 1) split_total += (unsigned long long)(T - 1) * params[b].n;
     }
-    uint32_t longest = 0;
-    for (const TileDev& d : tiles) longest = std::max(longest, d.len);
-    P.n_tiles = (uint32_t)tiles.size();
-    P.max_len = longest;
-    P.channels = channels;
-    P.threads = kTiledThreads;
-    P.smem = (size_t)longest * channels * 4;
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (P.smem > (size_t)optin || P.n_tiles == 0) return SNN_E_ARG;
-    if (tiled_set_smem(P.smem) != cudaSuccess) return SNN_E_CUDA;
-    P.tiles = static_cast<TileDev*>(alloc(tiles.size() * sizeof(TileDev)));
-    P.split = static_cast<uint32_t*>(alloc(std::max<unsigned long long>(split_total, 1) * 4));
-    if (!P.tiles || !P.split) return SNN_E_NOMEM;
-    struct Tmp {
-        uint32_t* p;
-        const std::function<void(void*)>& f;
-        ~Tmp() { f(p); }
-    } dbounds{static_cast<uint32_t*>(alloc(65536 * 4)), release};
-    if (!dbounds.p) return SNN_E_NOMEM;
-    if (cudaMemcpyAsync(P.tiles, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return SNN_E_CUDA;
-    for (uint32_t b = 0; b < n_inst; ++b) {
+    const size_t smem = (size_t)longest * channels * 4;
+    if (tiles.empty() || smem > (size_t)optin) return SNN_E_ARG;
+    if (tiled_set_smem(smem) != cudaSuccess) return SNN_E_CUDA;
+    int ctas = 0;
+    cudaError_t oe = channels == 2
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_receive_tiled<true, 2>, kTiledThreads, smem)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_receive_tiled<true, 1>, kTiledThreads, smem);
+    if (oe != cudaSuccess || ctas < 1) {
+        cudaGetLastError();
+        ctas = 1;
+    }
+    const uint32_t n_ctas = (uint32_t)(sms * ctas);
+    const double items_per_cta = 3.0;
+    const double target = total > 0 ? total / (items_per_cta * n_ctas) : 1.0;
+    // parts, partial buffer and the merge chunks
+    struct Item {
+        uint32_t code;
+        double w;
+    };
+    std::vector<Item> items;
+    std::vector<MergeDev> merges;
+    unsigned long long part_total = 0;
+    for (uint32_t k = 0; k < tiles.size(); ++k) {
+        TileDev& d = tiles[k];
+        uint32_t parts = total > 0 ? (uint32_t)std::ceil(tile_work[k] / target) : 1u;
+        parts = std::max<uint32_t>(1, std::min<uint32_t>({parts, kMaxParts, n_ctas}));
+        d.nparts = parts;
+        if (parts > 1) {
+            d.part_base = part_total;
+            part_total += (unsigned long long)parts * channels * d.len;
+            for (uint32_t off = 0; off < d.len; off += kMergeChunk)
+                merges.push_back(MergeDev{k, off, std::min(kMergeChunk, d.len - off), 0});
+        }
+        for (uint32_t p = 0; p < parts; ++p) items.push_back(Item{(k << 8) | p, tile_work[k] / parts});
+    }
+    if (tiles.size() >= (1u << 24)) return SNN_E_ARG;
+    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.w > b.w; });
+    std::vector<uint32_t> codes(items.size());
+    for (size_t i = 0; i < items.size(); ++i) codes[i] = items[i].code;
+
+    TiledPlan Q;
+    Q.n_tiles = (uint32_t)tiles.size();
+    Q.n_items = (uint32_t)codes.size();
+    Q.n_merges = (uint32_t)merges.size();
+    Q.max_len = longest;
+    Q.channels = channels;
+    Q.threads = kTiledThreads;
+    Q.smem = smem;
+    Q.grid = std::min<uint32_t>(Q.n_items, n_ctas);
+    Q.tiles = static_cast<TileDev*>(alloc(tiles.size() * sizeof(TileDev)));
+    Q.items = static_cast<uint32_t*>(alloc(codes.size() * 4));
+    Q.split = static_cast<uint32_t*>(alloc(std::max<unsigned long long>(split_total, 1) * 4));
+    Q.partial = static_cast<int32_t*>(alloc(std::max<unsigned long long>(part_total, 4) * 4));
+    Q.merges = static_cast<MergeDev*>(alloc(std::max<size_t>(merges.size(), 1) * sizeof(MergeDev)));
+    uint32_t* dbounds = static_cast<uint32_t*>(alloc(65536 * 4));
+    snn_status st = (Q.tiles && Q.items && Q.split && Q.partial && Q.merges && dbounds) ? SNN_OK : SNN_E_NOMEM;
+    if (st == SNN_OK &&
+        (cudaMemcpyAsync(Q.tiles, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+         cudaMemcpyAsync(Q.items, codes.data(), codes.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+         (merges.size() && cudaMemcpyAsync(Q.merges, merges.data(), merges.size() * sizeof(MergeDev),
+                                           cudaMemcpyHostToDevice, s) != cudaSuccess)))
+        st = SNN_E_CUDA;
+    for (uint32_t b = 0; b < n_inst && st == SNN_OK; ++b) {
         const auto& B = bounds[b];
         if (B.size() <= 2) continue;
         const uint32_t T = (uint32_t)B.size() - 1;
-        if (T + 1 > 65536) return SNN_E_ARG;
-        unsigned long long base = 0;
-        for (const TileDev& d : tiles)
-            if (d.inst == b) {
-                base = d.split;
-                break;
-            }
-        if (cudaMemcpyAsync(dbounds.p, B.data(), B.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) return SNN_E_CUDA;
-        k_split_rows<<<1184, 256, 0, s>>>(n.roff, n.tgt, pbase[b], params[b].n, dbounds.p, T, P.split + base);
-        if (cudaGetLastError() != cudaSuccess) return SNN_E_CUDA;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return SNN_E_CUDA;
+        if (T + 1 > 65536) {
+            st = SNN_E_ARG;
+            break;
+        }
+        if (cudaMemcpyAsync(dbounds, B.data(), B.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            st = SNN_E_CUDA;
+            break;
+        }
+        k_split_rows<<<1184, 256, 0, s>>>(n.roff, n.tgt, pbase[b], params[b].n, dbounds, T, Q.split + split_base[b]);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) st = SNN_E_CUDA;
     }
+    cudaStreamSynchronize(s);
+    release(dbounds);
+    if (st != SNN_OK) {
+        tiled_free(Q, release);
+        return st;
+    }
+    tiled_free(P, release);
+    P = Q;
     return SNN_OK;
 }
 
@@ -234,25 +387,18 @@ inline cudaError_t enqueue_tiled_receive(const TiledPlan& P, const Net& n, bool 
 {
     if (P.channels == 2) {
         if (w16)
-            k_receive_tiled<true, 2><<<P.n_tiles, P.threads, P.smem, s>>>(n, P.tiles, P.split);
+            k_receive_tiled<true, 2><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items);
         else
-            k_receive_tiled<false, 2><<<P.n_tiles, P.threads, P.smem, s>>>(n, P.tiles, P.split);
+            k_receive_tiled<false, 2><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items);
+        if (P.n_merges) k_merge_parts<2><<<P.n_merges, 256, 0, s>>>(n, P.tiles, P.merges, P.partial);
     } else {
         if (w16)
-            k_receive_tiled<true, 1><<<P.n_tiles, P.threads, P.smem, s>>>(n, P.tiles, P.split);
+            k_receive_tiled<true, 1><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items);
         else
-            k_receive_tiled<false, 1><<<P.n_tiles, P.threads, P.smem, s>>>(n, P.tiles, P.split);
+            k_receive_tiled<false, 1><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items);
+        if (P.n_merges) k_merge_parts<1><<<P.n_merges, 256, 0, s>>>(n, P.tiles, P.merges, P.partial);
     }
     return cudaGetLastError();
 }
 
-}  // namespace snn
-
-namespace snn {
-inline void tiled_free(TiledPlan& P, const std::function<void(void*)>& release)
-{
-    release(P.tiles);
-    release(P.split);
-    P = TiledPlan{};
-}
 }  // namespace snn

@@ -38,14 +38,14 @@ def test_library_exports_every_declared_function():
 def test_argument_errors_without_device():
     lib = snn.load()
     ctx = ctypes.c_void_p()
-    cfg = snn.Config(0, 0, 0, 1, 1, 0, 0, 0)  # delay 0 is invalid
+    cfg = snn.Config(0, 0, 0, 1, 1, 0, 0, 0, 0, 0)  # delay 0 is invalid
     p = (snn.Params * 1)()
     p[0].n, p[0].n_exc, p[0].dt, p[0].tau_m, p[0].tau_e, p[0].tau_i = 10, 8, 0.1, 20.0, 5.0, 10.0
     assert lib.snn_create(ctypes.byref(cfg), ctypes.addressof(p), None, ctypes.byref(ctx)) == -1
     assert ctx.value is None
-    cfg = snn.Config(0, snn.F_STDP, 1, 1, 1, 0, 0, 0)  # STDP needs the Brunel model
+    cfg = snn.Config(0, snn.F_STDP, 1, 1, 1, 0, 0, 0, 0, 0)  # STDP needs the Brunel model
     assert lib.snn_create(ctypes.byref(cfg), ctypes.addressof(p), None, ctypes.byref(ctx)) == -1
-    cfg = snn.Config(1, 0, 1, 1, 1, 0, 0, 0)
+    cfg = snn.Config(1, 0, 1, 1, 1, 0, 0, 0, 0, 0)
     p[0].lam = 500.0  # Poisson table would exceed 64 entries
     assert lib.snn_create(ctypes.byref(cfg), ctypes.addressof(p), None, ctypes.byref(ctx)) == -1
     p[0].lam = 2.0

@@ -281,3 +281,43 @@ def test_stats_match_raster(gpu):
     ends = np.r_[starts[1:], len(i)]
     cvs = [np.diff(s[a:b]).std() / np.diff(s[a:b]).mean() for a, b in zip(starts, ends) if b - a >= 3]
     assert abs(cv - np.mean(cvs)) < 1e-9
+
+
+@pytest.mark.parametrize("tune_steps", [1, 37])
+def test_retuned_tiles_keep_parity(gpu, tune_steps):
+    """Re-cutting the tiles by measured work mid-run changes nothing."""
+    prob = si.batched_sweep(n_nets=9, base_seed=8, n_steps=400, n_lo=200, n_hi=20000)
+    o = oracle_run("batch9", prob)
+    net = gpu.Network(prob, receive=RECV["tiled"], log_capacity=prob.n * 400, tune_steps=tune_steps)
+    before = net.info()["n_tiles"]
+    for k in (10, 50, 340):
+        net.step(k)
+    after = net.info()["n_tiles"]
+    g = {f: net.read(f) for f in _fields(prob)}
+    g["steps"], g["ids"] = net.spikes()
+    g["counters"] = net.counters()
+    net.close()
+    assert before > 0 and after > 0
+    assert_parity(g, o, prob)
+
+
+@pytest.mark.parametrize("model", [si.BRUNEL, si.VOGELS])
+def test_instances_larger_than_one_tile(gpu, model):
+    """Instances whose accumulators exceed one CTA's shared memory are cut
+    into target tiles; row segments come from the split table."""
+    if model == si.BRUNEL:
+        prob = si.problem(si.BRUNEL, [si.brunel_instance(70000, k=60, nu_ratio=3.0),
+                                      si.brunel_instance(3000, k=300)], delay=3, n_steps=300, seed=4)
+    else:
+        prob = si.problem(si.VOGELS, [si.vogels_instance(31000, k=80, c=1.0)], delay=1, n_steps=300, seed=4)
+    o = oracle.run(prob)
+    net = gpu.Network(prob, receive=RECV["tiled"], log_capacity=prob.n * 300, tune_steps=100)
+    net.step(300)
+    info = net.info()
+    g = {f: net.read(f) for f in _fields(prob)}
+    g["steps"], g["ids"] = net.spikes()
+    g["counters"] = net.counters()
+    net.close()
+    assert info["n_tiles"] >= 2
+    assert len(o["ids"]) > 1000
+    assert_parity(g, o, prob)
