@@ -80,9 +80,10 @@ typedef struct {
     uint64_t log_capacity; /* spikes the raster log keeps (0: no log) */
     uint32_t receive;      /* SNN_RECV_* */
     uint32_t steps_per_graph; /* steps captured per CUDA graph (0: library default) */
-    uint32_t tune_steps;   /* tiled receive: after this many steps of the first run the
-                              tiles are re-cut by the measured spike counts (0: 128,
-                              0xffffffff: never); results do not depend on the tiling */
+    uint32_t tune_steps;   /* tiled receive: at this step and at 8x this step of the first
+                              run the work items are re-cut by the spike counts measured
+                              since the previous cut (0: 256, 0xffffffff: never); results
+                              do not depend on the plan */
     uint32_t reserved;
 } snn_config;
 
@@ -143,9 +144,10 @@ snn_status snn_reset(snn_ctx* ctx);
 
 /* Enqueue n_steps timesteps on the context's stream and return without
  * waiting.  Device-side errors surface at the next call that synchronises.
- * With the tiled receive, the call that crosses step cfg.tune_steps (once per
- * context) waits for the device, re-cuts the tiles by the measured work and
- * re-captures its CUDA graphs before going on. */
+ * With the tiled receive, a call that crosses a re-plan step (see
+ * cfg.tune_steps; twice per graph load) waits for the device, re-cuts the
+ * work items by the measured work and re-captures its CUDA graphs before
+ * going on. */
 snn_status snn_step(snn_ctx* ctx, uint32_t n_steps);
 
 /* Run n_steps timesteps without the CUDA graph, with CUDA events around

@@ -65,7 +65,9 @@ struct snn_ctx {
     uint32_t* cpre = nullptr;
     TiledPlan tiled{};
     bool use_tiled = false;
-    bool tuned = false;                // tiles re-cut by measured work
+    uint32_t tune_count = 0;           // re-plans done (at most 2)
+    uint64_t tune_next = 0;            // step of the next re-plan
+    std::vector<unsigned long long> spk_seen;  // instance spike counts at the last re-plan
     std::vector<uint64_t> inst_edges;  // synapses of each instance
     uint4* rinfo = nullptr;            // row records (start, length, meta)
 
@@ -195,7 +197,7 @@ snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr)
 {
     const Net& n = c->net;
     if (ev) cudaEventRecord(ev[0], s);
-    const uint32_t ublocks = grid_for(c->Np / 8, 256);
+    const uint32_t ublocks = grid_for(c->Np / kUpdateNeurons, 256);
     const uint32_t wblocks = (uint32_t)sm_count() * 8;
     if (c->stdp) {
         if (c->w16)
@@ -281,7 +283,7 @@ snn_status check_device_errors(snn_ctx* c)
 
 snn_status init_state(snn_ctx* c)
 {
-    k_init_state<<<grid_for(c->Np / 8, 256), 256, 0, c->stream>>>(c->net, c->vogels ? 1 : 0, c->stdp ? 1 : 0);
+    k_init_state<<<grid_for(c->Np / 4, 256), 256, 0, c->stream>>>(c->net, c->vogels ? 1 : 0, c->stdp ? 1 : 0);
     CUDA_TRY(c, cudaGetLastError());
     // control block: step 0, empty queues and log
     CUDA_TRY(c, cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), c->stream));
@@ -315,7 +317,7 @@ snn_status plan_tiles(snn_ctx* c, const double* work)
 // the tiling, only the balance across SMs does), then re-capture the graphs.
 snn_status retune(snn_ctx* c)
 {
-    c->tuned = true;
+    c->tune_count++;
     std::vector<unsigned long long> spk(c->cfg.n_inst, 0);
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     CUDA_TRY(c, cudaMemcpy(spk.data(), c->net.inst_spikes, spk.size() * 8, cudaMemcpyDeviceToHost));
@@ -323,10 +325,13 @@ snn_status retune(snn_ctx* c)
     double total = 0.0;
     for (uint32_t b = 0; b < c->cfg.n_inst; ++b) {
         const double deg = c->params[b].n ? (double)c->inst_edges[b] / c->params[b].n : 0.0;
-        // delivered edges plus the fixed work per spike and tile (row record, splits)
-        work[b] = (double)spk[b] * (deg + 8.0);
+        // delivered edges plus the fixed work per spike (row record, splits),
+        // from the spikes since the previous re-plan
+        const unsigned long long d = spk[b] >= c->spk_seen[b] ? spk[b] - c->spk_seen[b] : spk[b];
+        work[b] = (double)d * (deg + 8.0);
         total += work[b];
     }
+    c->spk_seen = spk;
     if (total <= 0.0) return SNN_OK;
     snn_status st = plan_tiles(c, work.data());
     if (st != SNN_OK) return fail(c, st, "re-cutting the tiles failed");
@@ -407,7 +412,8 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
 
     // per-instance constants and Poisson tables
     std::vector<InstDev> hinst(cfg->n_inst);
-    std::vector<uint32_t> hpois((size_t)cfg->n_inst * kPoissonCap, 0);
+    // thresholds padded with 0xffffffff: the device sampler searches all 64
+    std::vector<uint32_t> hpois((size_t)cfg->n_inst * kPoissonCap, 0xffffffffu);
     for (uint32_t b = 0; b < cfg->n_inst; ++b) {
         int np = 0;
         if (cfg->model == SNN_BRUNEL) np = poisson_table(params[b].lambda, &hpois[(size_t)b * kPoissonCap], kPoissonCap);
@@ -659,7 +665,9 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
     for (uint32_t b = 0; b < c->cfg.n_inst; ++b)
         c->inst_edges[b] = row_off[c->g_off[b + 1]] - row_off[c->g_off[b]];
     c->use_tiled = false;
-    c->tuned = false;
+    c->tune_count = 0;
+    c->tune_next = c->cfg.tune_steps ? c->cfg.tune_steps : 256;
+    c->spk_seen.assign(c->cfg.n_inst, 0);
     if (c->cfg.receive != SNN_RECV_GLOBAL) {
         snn_status st = c->rows_sorted ? plan_tiles(c, nullptr) : SNN_E_ARG;
         if (st == SNN_OK) {
@@ -702,10 +710,10 @@ snn_status snn_step(snn_ctx* c, uint32_t n_steps)
     if (!c) return SNN_E_ARG;
     if (!c->graph_loaded) return fail(c, SNN_E_STATE, "snn_step before snn_build_graph");
     uint32_t left = n_steps;
-    const uint64_t tune_at = c->cfg.tune_steps ? c->cfg.tune_steps : 128;
-    if (c->use_tiled && !c->tuned && c->cfg.tune_steps != 0xffffffffu && c->host_steps + left >= tune_at) {
-        // run up to the tuning step, re-cut the tiles, go on
-        uint32_t first = (uint32_t)(tune_at > c->host_steps ? tune_at - c->host_steps : 0);
+    // re-plan the tiled receive twice, at tune_steps and 8 x tune_steps
+    while (c->use_tiled && c->tune_count < 2 && c->cfg.tune_steps != 0xffffffffu &&
+           c->host_steps + left >= c->tune_next) {
+        uint32_t first = (uint32_t)(c->tune_next > c->host_steps ? c->tune_next - c->host_steps : 0);
         left -= first;
         c->host_steps += first;
         while (c->gk && first >= c->k_steps) {
@@ -715,6 +723,7 @@ snn_status snn_step(snn_ctx* c, uint32_t n_steps)
         while (first--) CUDA_TRY(c, cudaGraphLaunch(c->g1, c->stream));
         snn_status st = retune(c);
         if (st != SNN_OK) return st;
+        c->tune_next *= 8;
     }
     c->host_steps += left;
     while (c->gk && left >= c->k_steps) {

@@ -15,21 +15,38 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // ---------------------------------------------------------------------------
 // Update Neurons (Section III-A-1): N_t -> N'_{t+1}, spikers -> S_t.
-// One thread advances 8 consecutive neurons (two 128-bit loads per float
-// field, one Philox block for the 8 Poisson words).  Spiking ids are
+// One thread advances kUpdateNeurons consecutive neurons (128-bit loads per
+// float field) and computes one Philox block, whose 8 words are the Poisson
+// draws of an aligned group of 8 neurons.  Spiking ids are
 // compacted per warp with a shuffle scan and one atomicAdd on the queue
 // index (Section III-A-2: queues are arrays with an atomic index).
 // ---------------------------------------------------------------------------
+
+constexpr int kUpdateNeurons = 8;  // neurons per thread of the update (4 or 8)
+
+// Number of Poisson thresholds <= u: branch-free binary search over the
+// instance's 64-entry table (entries past the real length are 0xffffffff;
+// the count is capped at the real length nT).
+__device__ __forceinline__ uint32_t poisson_count(const uint32_t* __restrict__ T, uint32_t nT, uint32_t u)
+{
+    uint32_t k = 0;
+#pragma unroll
+    for (uint32_t step = 32; step; step >>= 1)
+        if (__ldg(T + k + step - 1) <= u) k += step;
+    return min(k, nT);
+}
+
 template <int MODEL, bool STDP, bool STATS>
 __global__ void __launch_bounds__(256) k_update(Net n)
 {
+    constexpr int NPT = kUpdateNeurons;  // neurons per thread
     const unsigned long long t = n.ctl->t;
-    const uint32_t G = n.Np >> 3;
+    const uint32_t G = n.Np / NPT;
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = g < G;  // whole warps: Np is a multiple of 256
-    const uint32_t id0 = g * 8u;
+    const uint32_t id0 = g * NPT;
     uint32_t spk = 0;  // bit k: neuron id0 + k spiked
-    const uint32_t b = active ? __ldg(n.inst_of_w32 + (g >> 2)) : 0u;  // uniform across the warp
+    const uint32_t b = active ? __ldg(n.inst_of_w32 + (id0 >> 5)) : 0u;  // uniform across the warp
     const InstDev* I = n.inst + b;
     const uint32_t pbase = active ? __ldg(&I->pbase) : 0u;
 
@@ -39,28 +56,28 @@ __global__ void __launch_bounds__(256) k_update(Net n)
         if (local0 < nloc) {
             const float v_th = __ldg(&I->v_th), v_reset = __ldg(&I->v_reset), Pm = __ldg(&I->Pm);
             const uint32_t R = __ldg(&I->R);
-            float V[8];
-            *reinterpret_cast<float4*>(V) = *reinterpret_cast<const float4*>(n.V + id0);
-            *reinterpret_cast<float4*>(V + 4) = *reinterpret_cast<const float4*>(n.V + id0 + 4);
-            uint2 rr = *reinterpret_cast<const uint2*>(n.r + id0);
-            uint8_t r[8];
-            *reinterpret_cast<uint2*>(r) = rr;
-            int32_t a0[8];
-            *reinterpret_cast<int4*>(a0) = *reinterpret_cast<const int4*>(n.acc0 + id0);
-            *reinterpret_cast<int4*>(a0 + 4) = *reinterpret_cast<const int4*>(n.acc0 + id0 + 4);
+            float V[NPT];
+            uint8_t r[NPT];
+            int32_t a0[NPT];
+#pragma unroll
+            for (int h = 0; h < NPT / 4; ++h) {
+                *reinterpret_cast<float4*>(V + 4 * h) = *reinterpret_cast<const float4*>(n.V + id0 + 4 * h);
+                *reinterpret_cast<uint32_t*>(r + 4 * h) = *reinterpret_cast<const uint32_t*>(n.r + id0 + 4 * h);
+                *reinterpret_cast<int4*>(a0 + 4 * h) = *reinterpret_cast<const int4*>(n.acc0 + id0 + 4 * h);
+            }
 
             if (MODEL == 0) {  // Vogels-Abbott CUBA
                 const float Pe = __ldg(&I->Pe), Pi = __ldg(&I->Pi), e_l = __ldg(&I->e_l);
-                float ge[8], gi[8];
-                int32_t a1[8];
-                *reinterpret_cast<float4*>(ge) = *reinterpret_cast<const float4*>(n.ge + id0);
-                *reinterpret_cast<float4*>(ge + 4) = *reinterpret_cast<const float4*>(n.ge + id0 + 4);
-                *reinterpret_cast<float4*>(gi) = *reinterpret_cast<const float4*>(n.gi + id0);
-                *reinterpret_cast<float4*>(gi + 4) = *reinterpret_cast<const float4*>(n.gi + id0 + 4);
-                *reinterpret_cast<int4*>(a1) = *reinterpret_cast<const int4*>(n.acc1 + id0);
-                *reinterpret_cast<int4*>(a1 + 4) = *reinterpret_cast<const int4*>(n.acc1 + id0 + 4);
+                float ge[NPT], gi[NPT];
+                int32_t a1[NPT];
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
+                for (int h = 0; h < NPT / 4; ++h) {
+                    *reinterpret_cast<float4*>(ge + 4 * h) = *reinterpret_cast<const float4*>(n.ge + id0 + 4 * h);
+                    *reinterpret_cast<float4*>(gi + 4 * h) = *reinterpret_cast<const float4*>(n.gi + id0 + 4 * h);
+                    *reinterpret_cast<int4*>(a1 + 4 * h) = *reinterpret_cast<const int4*>(n.acc1 + id0 + 4 * h);
+                }
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) {
                     if (local0 + k >= nloc) continue;
                     float e = __fadd_rn(ge[k], __fmul_rn(__int2float_rn(a0[k]), kLattice));
                     float i = __fadd_rn(gi[k], __fmul_rn(__int2float_rn(a1[k]), kLattice));
@@ -85,20 +102,21 @@ __global__ void __launch_bounds__(256) k_update(Net n)
                     gi[k] = i;
                     r[k] = (uint8_t)rk;
                 }
-                *reinterpret_cast<float4*>(n.ge + id0) = *reinterpret_cast<float4*>(ge);
-                *reinterpret_cast<float4*>(n.ge + id0 + 4) = *reinterpret_cast<float4*>(ge + 4);
-                *reinterpret_cast<float4*>(n.gi + id0) = *reinterpret_cast<float4*>(gi);
-                *reinterpret_cast<float4*>(n.gi + id0 + 4) = *reinterpret_cast<float4*>(gi + 4);
-                *reinterpret_cast<int4*>(n.acc1 + id0) = make_int4(0, 0, 0, 0);
-                *reinterpret_cast<int4*>(n.acc1 + id0 + 4) = make_int4(0, 0, 0, 0);
+#pragma unroll
+                for (int h = 0; h < NPT / 4; ++h) {
+                    *reinterpret_cast<float4*>(n.ge + id0 + 4 * h) = *reinterpret_cast<float4*>(ge + 4 * h);
+                    *reinterpret_cast<float4*>(n.gi + id0 + 4 * h) = *reinterpret_cast<float4*>(gi + 4 * h);
+                    *reinterpret_cast<int4*>(n.acc1 + id0 + 4 * h) = make_int4(0, 0, 0, 0);
+                }
             } else {  // Brunel with Poisson drive
                 const int32_t jext = __ldg(&I->jext);
                 const uint32_t* T = n.pois + __ldg(&I->pois_off);
                 const uint32_t nT = __ldg(&I->pois_n);
                 uint32_t words[8];
                 philox_words8(n.seed, b, local0 >> 3, t, 1, words);
+                const uint32_t wofs = local0 & 7u & ~(uint32_t)(NPT - 1);  // 0 for 8 per thread
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
+                for (int k = 0; k < NPT; ++k) {
                     if (local0 + k >= nloc) continue;
                     float v = V[k];
                     uint32_t rk = r[k];
@@ -106,8 +124,7 @@ __global__ void __launch_bounds__(256) k_update(Net n)
                         rk -= 1;
                         v = v_reset;
                     } else {
-                        uint32_t next = 0;
-                        while (next < nT && __ldg(T + next) <= words[k]) ++next;
+                        const uint32_t next = poisson_count(T, nT, words[(wofs + k) & 7u]);
                         const int32_t in = a0[k] + (int32_t)next * jext;
                         v = __fadd_rn(__fmul_rn(v, Pm), __fmul_rn(__int2float_rn(in), kLattice));
                         if (v >= v_th) {
@@ -127,15 +144,16 @@ __global__ void __launch_bounds__(256) k_update(Net n)
                     uint32_t arr = 0;
                     if (t >= n.d) {
                         const uint32_t slot = (uint32_t)((t - n.d) % n.D);
-                        arr = (n.bits[(size_t)slot * (n.Np >> 5) + (id0 >> 5)] >> (id0 & 31u)) & 0xffu;
+                        arr = (n.bits[(size_t)slot * (n.Np >> 5) + (id0 >> 5)] >> (id0 & 31u)) & ((1u << NPT) - 1u);
                     }
-                    float xs[8], ys[8];
-                    *reinterpret_cast<float4*>(xs) = *reinterpret_cast<const float4*>(n.x + id0);
-                    *reinterpret_cast<float4*>(xs + 4) = *reinterpret_cast<const float4*>(n.x + id0 + 4);
-                    *reinterpret_cast<float4*>(ys) = *reinterpret_cast<const float4*>(n.y + id0);
-                    *reinterpret_cast<float4*>(ys + 4) = *reinterpret_cast<const float4*>(n.y + id0 + 4);
+                    float xs[NPT], ys[NPT];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
+                    for (int h = 0; h < NPT / 4; ++h) {
+                        *reinterpret_cast<float4*>(xs + 4 * h) = *reinterpret_cast<const float4*>(n.x + id0 + 4 * h);
+                        *reinterpret_cast<float4*>(ys + 4 * h) = *reinterpret_cast<const float4*>(n.y + id0 + 4 * h);
+                    }
+#pragma unroll
+                    for (int k = 0; k < NPT; ++k) {
                         if (local0 + k >= n_exc) continue;
                         float xv = __fmul_rn(xs[k], Pp);
                         if (arr >> k & 1u) xv = __fadd_rn(xv, 1.0f);
@@ -144,20 +162,22 @@ __global__ void __launch_bounds__(256) k_update(Net n)
                         xs[k] = xv;
                         ys[k] = yv;
                     }
-                    *reinterpret_cast<float4*>(n.x + id0) = *reinterpret_cast<float4*>(xs);
-                    *reinterpret_cast<float4*>(n.x + id0 + 4) = *reinterpret_cast<float4*>(xs + 4);
-                    *reinterpret_cast<float4*>(n.y + id0) = *reinterpret_cast<float4*>(ys);
-                    *reinterpret_cast<float4*>(n.y + id0 + 4) = *reinterpret_cast<float4*>(ys + 4);
+#pragma unroll
+                    for (int h = 0; h < NPT / 4; ++h) {
+                        *reinterpret_cast<float4*>(n.x + id0 + 4 * h) = *reinterpret_cast<float4*>(xs + 4 * h);
+                        *reinterpret_cast<float4*>(n.y + id0 + 4 * h) = *reinterpret_cast<float4*>(ys + 4 * h);
+                    }
                 }
             }
-            *reinterpret_cast<float4*>(n.V + id0) = *reinterpret_cast<float4*>(V);
-            *reinterpret_cast<float4*>(n.V + id0 + 4) = *reinterpret_cast<float4*>(V + 4);
-            *reinterpret_cast<uint2*>(n.r + id0) = *reinterpret_cast<uint2*>(r);
-            *reinterpret_cast<int4*>(n.acc0 + id0) = make_int4(0, 0, 0, 0);
-            *reinterpret_cast<int4*>(n.acc0 + id0 + 4) = make_int4(0, 0, 0, 0);
+#pragma unroll
+            for (int h = 0; h < NPT / 4; ++h) {
+                *reinterpret_cast<float4*>(n.V + id0 + 4 * h) = *reinterpret_cast<float4*>(V + 4 * h);
+                *reinterpret_cast<uint32_t*>(n.r + id0 + 4 * h) = *reinterpret_cast<uint32_t*>(r + 4 * h);
+                *reinterpret_cast<int4*>(n.acc0 + id0 + 4 * h) = make_int4(0, 0, 0, 0);
+            }
             if (STATS && spk) {
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
+                for (int k = 0; k < NPT; ++k)
                     if (spk >> k & 1u) {
                         const uint32_t c = n.st_cnt[id0 + k];
                         if (c > 0) {
@@ -176,11 +196,12 @@ __global__ void __launch_bounds__(256) k_update(Net n)
     const uint32_t slot_q = (uint32_t)(t % n.D);
     const uint32_t slot_c = (uint32_t)(t & (n.cr - 1));
     if (STDP) {
-        // the warp's 256 neurons = 8 bitmask words; lanes 4m..4m+3 form word m
-        uint32_t word = spk << (8u * (lane & 3u));
-        word |= __shfl_xor_sync(kFull, word, 1);
-        word |= __shfl_xor_sync(kFull, word, 2);
-        if (active && (lane & 3u) == 0) n.bits[(size_t)slot_q * (n.Np >> 5) + (id0 >> 5)] = word;
+        // 32 / NPT lanes cover one 32-neuron bitmask word
+        constexpr uint32_t L = 32 / kUpdateNeurons;
+        uint32_t word = spk << (kUpdateNeurons * (lane & (L - 1u)));
+#pragma unroll
+        for (uint32_t o = 1; o < L; o <<= 1) word |= __shfl_xor_sync(kFull, word, o);
+        if (active && (lane & (L - 1u)) == 0) n.bits[(size_t)slot_q * (n.Np >> 5) + (id0 >> 5)] = word;
     }
     // warp compaction: exclusive scan of the per-thread spike counts, one
     // atomicAdd on the instance's queue index and one on the step's total
