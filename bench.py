@@ -213,7 +213,9 @@ def run_ours(args, rank, world, dist):
         return e0.elapsed_time(e1) / 1e3, c1["events"] - c0["events"], c1["spikes"] - c0["spikes"]
 
     # ---- headline: batched + int16, timed on the device
-    net = snn.Network(prob, w16=True, receive=snn.RECV_AUTO, log_capacity=cap)
+    recv_mode = {"auto": snn.RECV_AUTO, "global": snn.RECV_GLOBAL, "tiled": snn.RECV_TILED,
+                 "bulk": snn.RECV_BULK}[args.receive]
+    net = snn.Network(prob, w16=True, receive=recv_mode, log_capacity=cap)
     info = net.info()
     recv_kind = info["receive"]
     net.step(args.warmup)
@@ -288,7 +290,7 @@ def run_ours(args, rank, world, dist):
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        net = snn.Network(prob, w16=True, receive=snn.RECV_AUTO, log_capacity=cap)  # h2d of the graph
+        net = snn.Network(prob, w16=True, receive=recv_mode, log_capacity=cap)  # h2d of the graph
         net.step(args.steps)
         steps_h, ids_h = net.spikes()  # d2h of the raster
         t_e2e = time.perf_counter() - t0
@@ -336,6 +338,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="batched_sweep_256")
     ap.add_argument("--profile-steps", type=int, default=500)
+    ap.add_argument("--receive", choices=["auto", "global", "tiled", "bulk"], default="auto")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

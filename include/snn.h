@@ -70,6 +70,7 @@ typedef enum {
 #define SNN_RECV_AUTO 0u   /* the library picks: tiled when the rows are sorted, else global */
 #define SNN_RECV_GLOBAL 1u /* warp per spike, red.global.add into L2-resident accumulators */
 #define SNN_RECV_TILED 2u  /* target-tiled, accumulators in shared memory; needs sorted rows */
+#define SNN_RECV_BULK 3u   /* as TILED, rows staged into shared memory by bulk async copies */
 
 typedef struct {
     uint32_t model;        /* snn_model */

@@ -16,12 +16,12 @@ import numpy as np
 
 from .build import LIB, build as _build
 
-__all__ = ["Network", "SnnError", "load", "VOGELS", "BRUNEL", "RECV_AUTO", "RECV_GLOBAL", "RECV_TILED",
+__all__ = ["Network", "SnnError", "load", "VOGELS", "BRUNEL", "RECV_AUTO", "RECV_GLOBAL", "RECV_TILED", "RECV_BULK",
            "F_STDP", "F_W16", "F_STATS", "FIELDS"]
 
 VOGELS, BRUNEL = 0, 1
 F_STDP, F_W16, F_STATS = 1, 2, 4
-RECV_AUTO, RECV_GLOBAL, RECV_TILED = 0, 1, 2
+RECV_AUTO, RECV_GLOBAL, RECV_TILED, RECV_BULK = 0, 1, 2, 3
 FIELDS = {"V": 0, "ge": 1, "gi": 2, "r": 3, "x": 4, "y": 5, "acc0": 6, "acc1": 7, "w": 8}
 _FIELD_DTYPE = {"V": np.float32, "ge": np.float32, "gi": np.float32, "r": np.int32, "x": np.float32,
                 "y": np.float32, "acc0": np.int32, "acc1": np.int32, "w": np.int32}
@@ -278,6 +278,6 @@ class Network:
     def info(self) -> dict:
         i = Info()
         self._check(self.lib.snn_get_info(self.ctx, ctypes.byref(i)), "snn_get_info")
-        return {"receive": {RECV_GLOBAL: "global", RECV_TILED: "tiled"}.get(i.receive, "?"), "n_tiles": i.n_tiles,
+        return {"receive": {RECV_GLOBAL: "global", RECV_TILED: "tiled", RECV_BULK: "bulk"}.get(i.receive, "?"), "n_tiles": i.n_tiles,
                 "n_padded": i.n_padded, "rows_sorted": bool(i.rows_sorted), "edges": i.edges,
                 "device_bytes": i.device_bytes}

@@ -19,6 +19,7 @@
 #include "snn_device.cuh"
 #include "snn_kernels.cuh"
 #include "snn_tiled.cuh"
+#include "snn_bulk.cuh"
 
 using namespace snn;
 
@@ -65,6 +66,7 @@ struct snn_ctx {
     uint32_t* cpre = nullptr;
     TiledPlan tiled{};
     bool use_tiled = false;
+    bool use_bulk = false;             // tiled plan, bulk-copy kernel
     uint32_t tune_count = 0;           // re-plans done (at most 2)
     uint64_t tune_next = 0;            // step of the next re-plan
     std::vector<unsigned long long> spk_seen;  // instance spike counts at the last re-plan
@@ -230,7 +232,9 @@ snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr)
             k_stdp_potentiate<false><<<wblocks, 256, 0, s>>>(n);
     }
     if (ev) cudaEventRecord(ev[3], s);
-    if (c->use_tiled) {
+    if (c->use_tiled && c->use_bulk) {
+        CUDA_TRY(c, enqueue_bulk_receive(c->tiled, n, c->w16, s));
+    } else if (c->use_tiled) {
         CUDA_TRY(c, enqueue_tiled_receive(c->tiled, n, c->w16, s));
     } else if (c->w16) {
         k_receive_global<true><<<wblocks, 256, 0, s>>>(n);
@@ -307,10 +311,23 @@ snn_status init_state(snn_ctx* c)
 // instance b per step (null: proportional to its synapses).
 snn_status plan_tiles(snn_ctx* c, const double* work)
 {
-    const uint32_t max_len = c->vogels ? 28672u : 57344u;  // 224 KB of accumulators: one CTA per SM
-    return tiled_plan(c->tiled, c->net, c->params.data(), c->pbase.data(), c->cfg.n_inst, c->vogels ? 2 : 1, max_len,
-                      work, c->inst_edges.data(), sm_count(), [c](size_t b) { return dev_alloc(c, b); },
-                      [c](void* p) { dev_free(c, p); }, c->stream);
+    // accumulators of one tile: 224 KB (tiled), or what the copy ring leaves
+    // of the 227 KB (bulk); one CTA per SM either way
+    const uint32_t ch = c->vogels ? 2u : 1u;
+    const uint32_t bulk_len = (uint32_t)((227u * 1024u - 1024u - kBulkSlots * bulk_slot_bytes(c->w16)) / 4u / 256u * 256u);
+    const uint32_t max_len = (c->use_bulk ? bulk_len : 57344u) / ch / 256u * 256u;
+    snn_status st = tiled_plan(c->tiled, c->net, c->params.data(), c->pbase.data(), c->cfg.n_inst, (int)ch, max_len,
+                               work, c->inst_edges.data(), sm_count(), [c](size_t b) { return dev_alloc(c, b); },
+                               [c](void* p) { dev_free(c, p); }, c->stream);
+    if (st == SNN_OK && c->use_bulk) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const size_t smem = bulk_smem(c->tiled.max_len, (int)ch, c->w16);
+        if (smem > (size_t)optin) return SNN_E_ARG;
+        if (bulk_set_smem(smem) != cudaSuccess) return SNN_E_CUDA;
+    }
+    return st;
 }
 
 // Re-cut the tiles by the spikes measured so far (results do not depend on
@@ -368,7 +385,7 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     if (!cfg || !params || cfg->n_inst == 0) return SNN_E_ARG;
     if (cfg->model > SNN_BRUNEL || cfg->delay < 1 || cfg->delay > 1000) return SNN_E_ARG;
     if ((cfg->flags & SNN_F_STDP) && cfg->model != SNN_BRUNEL) return SNN_E_ARG;
-    if (cfg->receive > SNN_RECV_TILED) return SNN_E_ARG;
+    if (cfg->receive > SNN_RECV_BULK) return SNN_E_ARG;
     uint64_t N = 0, Np = 0;
     for (uint32_t b = 0; b < cfg->n_inst; ++b) {
         const snn_params& p = params[b];
@@ -547,12 +564,12 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
 
     c->E = E;
     c->roff = alloc_n<uint64_t>(c, (size_t)Np + 1);
-    c->tgt = alloc_n<uint32_t>(c, E);
+    c->tgt = alloc_n<uint32_t>(c, E + 16);  // tail padding: bulk copies round their end up
     c->meta = alloc_n<uint8_t>(c, Np);
     if (c->w16)
-        c->w16p = alloc_n<int16_t>(c, E);
+        c->w16p = alloc_n<int16_t>(c, E + 16);
     else
-        c->w32p = alloc_n<float>(c, E);
+        c->w32p = alloc_n<float>(c, E + 16);
     if (c->stdp) c->w_init = alloc_n<int32_t>(c, E);
     int32_t* wtmp = c->stdp ? c->w_init : alloc_n<int32_t>(c, E);
     uint32_t* dsrc = alloc_n<uint32_t>(c, Np);
@@ -665,6 +682,7 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
     for (uint32_t b = 0; b < c->cfg.n_inst; ++b)
         c->inst_edges[b] = row_off[c->g_off[b + 1]] - row_off[c->g_off[b]];
     c->use_tiled = false;
+    c->use_bulk = c->cfg.receive == SNN_RECV_BULK;
     c->tune_count = 0;
     c->tune_next = c->cfg.tune_steps ? c->cfg.tune_steps : 256;
     c->spk_seen.assign(c->cfg.n_inst, 0);
@@ -674,7 +692,7 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
             c->use_tiled = true;
         } else {
             tiled_free(c->tiled, [c](void* p) { dev_free(c, p); });
-            if (c->cfg.receive == SNN_RECV_TILED)
+            if (c->cfg.receive == SNN_RECV_TILED || c->cfg.receive == SNN_RECV_BULK)
                 return fail(c, st, c->rows_sorted ? "the tiled receive does not fit this graph"
                                                   : "the tiled receive needs rows sorted by target");
         }
@@ -980,7 +998,7 @@ snn_status snn_stats_clear(snn_ctx* c)
 snn_status snn_get_info(snn_ctx* c, snn_info* info)
 {
     if (!c || !info) return SNN_E_ARG;
-    info->receive = c->use_tiled ? SNN_RECV_TILED : SNN_RECV_GLOBAL;
+    info->receive = c->use_tiled ? (c->use_bulk ? SNN_RECV_BULK : SNN_RECV_TILED) : SNN_RECV_GLOBAL;
     info->n_tiles = c->use_tiled ? c->tiled.n_tiles : 0;
     info->n_padded = c->Np;
     info->rows_sorted = c->rows_sorted ? 1 : 0;

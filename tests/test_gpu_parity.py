@@ -13,7 +13,7 @@ import snn_inputs as si
 
 pytestmark = pytest.mark.gpu
 
-RECV = {"global": 1, "tiled": 2}
+RECV = {"global": 1, "tiled": 2, "bulk": 3}
 
 
 def _fields(prob):
@@ -81,7 +81,7 @@ def oracle_run(key, prob, **kw):
 
 # ------------------------------------------------------------------ the configs
 @pytest.mark.parametrize("w16", [True, False])
-@pytest.mark.parametrize("receive", ["global", "tiled"])
+@pytest.mark.parametrize("receive", ["global", "tiled", "bulk"])
 def test_vogels_4k_full(gpu, w16, receive):
     """Vogels-Abbott, 4,000 neurons, 2 % connectivity, 1,000 steps."""
     prob = si.vogels_4k(seed=1, n_steps=1000)
@@ -91,7 +91,7 @@ def test_vogels_4k_full(gpu, w16, receive):
     assert_parity(g, o, prob)
 
 
-@pytest.mark.parametrize("receive", ["global", "tiled"])
+@pytest.mark.parametrize("receive", ["global", "tiled", "bulk"])
 def test_brunel_12k5_full(gpu, receive):
     """Brunel, 12,500 neurons, C_E 1,000 / C_I 250, 15-step delay, 10,000 steps."""
     prob = si.brunel_12k5(seed=1, n_steps=10000)
@@ -102,7 +102,7 @@ def test_brunel_12k5_full(gpu, receive):
 
 
 @pytest.mark.parametrize("w16", [True, False])
-@pytest.mark.parametrize("receive", ["global", "tiled"])
+@pytest.mark.parametrize("receive", ["global", "tiled", "bulk"])
 def test_brunel_stdp_small(gpu, w16, receive):
     """Brunel+ at 4,000 neurons (in-degree 400), STDP, 15-step delay."""
     prob = si.brunel_stdp_100k(seed=2, n_steps=3000, n=4000, k=400)
@@ -113,7 +113,7 @@ def test_brunel_stdp_small(gpu, w16, receive):
     assert_parity(g, o, prob)
 
 
-@pytest.mark.parametrize("receive", ["global", "tiled"])
+@pytest.mark.parametrize("receive", ["global", "tiled", "bulk"])
 def test_batched_uneven_parity(gpu, receive):
     """A batch of uneven Brunel networks in one context equals the oracle
     on the whole batch."""
@@ -155,7 +155,7 @@ def test_forced_spike_arrives_after_d_steps(gpu, d, model):
     prob = si.from_edges(model, inst, edges, w, delay=d, n_steps=40)
     ov = [(7, 0, 1000.0), (9, 250, 1000.0)]
     o = oracle.run(prob, overrides=ov)
-    for receive in ("global", "tiled"):
+    for receive in ("global", "tiled", "bulk"):
         g = run_gpu(gpu, prob, overrides=ov, receive=receive)
         assert_parity(g, o, prob)
 
@@ -176,7 +176,9 @@ def test_relay_network(gpu, d):
               "r": np.zeros(200, np.int32), "x": np.zeros(200, np.float32), "y": np.zeros(200, np.float32),
               "acc0": acc0, "acc1": np.zeros(200, np.int32), "w": prob.w.copy()}
     o = oracle.run(prob, state=ostate)
-    g = run_gpu(gpu, prob, state=state, receive="tiled")
+    for receive in ("tiled", "bulk"):
+        g = run_gpu(gpu, prob, state=state, receive=receive)
+        assert_parity(g, o, prob)
     assert len(o["ids"]) > 500
     assert_parity(g, o, prob)
 
@@ -188,7 +190,7 @@ def test_empty_graph_and_ragged_instances(gpu):
     prob = si.problem(si.BRUNEL, insts, delay=2, n_steps=700, seed=9)
     assert prob.n_edges == 0
     o = oracle.run(prob)
-    for receive in ("global", "tiled"):
+    for receive in ("global", "tiled", "bulk"):
         assert_parity(run_gpu(gpu, prob, receive=receive), o, prob)
 
 
@@ -283,12 +285,13 @@ def test_stats_match_raster(gpu):
     assert abs(cv - np.mean(cvs)) < 1e-9
 
 
+@pytest.mark.parametrize("receive", ["tiled", "bulk"])
 @pytest.mark.parametrize("tune_steps", [1, 37])
-def test_retuned_tiles_keep_parity(gpu, tune_steps):
+def test_retuned_tiles_keep_parity(gpu, tune_steps, receive):
     """Re-cutting the tiles by measured work mid-run changes nothing."""
     prob = si.batched_sweep(n_nets=9, base_seed=8, n_steps=400, n_lo=200, n_hi=20000)
     o = oracle_run("batch9", prob)
-    net = gpu.Network(prob, receive=RECV["tiled"], log_capacity=prob.n * 400, tune_steps=tune_steps)
+    net = gpu.Network(prob, receive=RECV[receive], log_capacity=prob.n * 400, tune_steps=tune_steps)
     before = net.info()["n_tiles"]
     for k in (10, 50, 340):
         net.step(k)
@@ -301,8 +304,9 @@ def test_retuned_tiles_keep_parity(gpu, tune_steps):
     assert_parity(g, o, prob)
 
 
+@pytest.mark.parametrize("receive", ["tiled", "bulk"])
 @pytest.mark.parametrize("model", [si.BRUNEL, si.VOGELS])
-def test_instances_larger_than_one_tile(gpu, model):
+def test_instances_larger_than_one_tile(gpu, model, receive):
     """Instances whose accumulators exceed one CTA's shared memory are cut
     into target tiles; row segments come from the split table."""
     if model == si.BRUNEL:
@@ -311,7 +315,7 @@ def test_instances_larger_than_one_tile(gpu, model):
     else:
         prob = si.problem(si.VOGELS, [si.vogels_instance(31000, k=80, c=1.0)], delay=1, n_steps=300, seed=4)
     o = oracle.run(prob)
-    net = gpu.Network(prob, receive=RECV["tiled"], log_capacity=prob.n * 300, tune_steps=100)
+    net = gpu.Network(prob, receive=RECV[receive], log_capacity=prob.n * 300, tune_steps=100)
     net.step(300)
     info = net.info()
     g = {f: net.read(f) for f in _fields(prob)}
