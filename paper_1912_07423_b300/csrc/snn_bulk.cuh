@@ -325,13 +325,13 @@ inline cudaError_t enqueue_bulk_receive(const TiledPlan& P, const Net& n, bool w
             k_receive_bulk<true, 2><<<P.grid, kBulkThreads, smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
         else
             k_receive_bulk<false, 2><<<P.grid, kBulkThreads, smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
-        if (P.n_merges) k_merge_parts<2><<<P.n_merges, 256, 0, s>>>(n, P.tiles, P.merges, P.partial);
+        if (P.n_merges) k_merge_parts<2><<<P.n_merges, kMergeChunk / 4, 0, s>>>(n, P.tiles, P.merges, P.partial);
     } else {
         if (w16)
             k_receive_bulk<true, 1><<<P.grid, kBulkThreads, smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
         else
             k_receive_bulk<false, 1><<<P.grid, kBulkThreads, smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
-        if (P.n_merges) k_merge_parts<1><<<P.n_merges, 256, 0, s>>>(n, P.tiles, P.merges, P.partial);
+        if (P.n_merges) k_merge_parts<1><<<P.n_merges, kMergeChunk / 4, 0, s>>>(n, P.tiles, P.merges, P.partial);
     }
     return cudaGetLastError();
 }

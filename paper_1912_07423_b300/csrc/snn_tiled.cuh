@@ -227,11 +227,12 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_receive_tiled(Net n, const
 }
 
 // Adds the parts of the multi-part tiles into the global accumulators, one
-// chunk of kMergeChunk neurons per block.
+// chunk of kMergeChunk neurons per block, one int4 per thread, eight parts'
+// loads in flight per thread.
 template <int CH>
-__global__ void __launch_bounds__(256) k_merge_parts(Net n, const TileDev* __restrict__ tiles,
-                                                     const MergeDev* __restrict__ merges,
-                                                     const int32_t* __restrict__ partial)
+__global__ void __launch_bounds__(kMergeChunk / 4) k_merge_parts(Net n, const TileDev* __restrict__ tiles,
+                                                                const MergeDev* __restrict__ merges,
+                                                                const int32_t* __restrict__ partial)
 {
     const MergeDev M = merges[blockIdx.x];
     const TileDev T = tiles[M.tile];
@@ -239,20 +240,34 @@ __global__ void __launch_bounds__(256) k_merge_parts(Net n, const TileDev* __res
     if (t + 1 < n.d) return;
     const unsigned long long ts = t + 1 - n.d;
     if (n.icount[(size_t)(ts & (n.cr - 1)) * n.n_inst + T.inst] == 0) return;  // no part wrote anything
+    const uint32_t i = M.off + threadIdx.x * 4;
+    if (i >= M.off + M.len) return;
     const int32_t* base = partial + T.part_base;
     for (uint32_t c = 0; c < CH; ++c) {
-        int32_t* acc = c ? n.acc1 : n.acc0;
-        for (uint32_t i = M.off + threadIdx.x * 4; i < M.off + M.len; i += blockDim.x * 4) {
-            int4 s = make_int4(0, 0, 0, 0);
-            for (uint32_t p = 0; p < T.nparts; ++p) {
-                const int4 v = *reinterpret_cast<const int4*>(base + ((size_t)p * CH + c) * T.len + i);
-                s.x += v.x;
-                s.y += v.y;
-                s.z += v.z;
-                s.w += v.w;
+        const int32_t* src = base + (size_t)c * T.len + i;
+        const size_t stride = (size_t)CH * T.len;  // between parts
+        int4 s = make_int4(0, 0, 0, 0);
+        uint32_t p = 0;
+        for (; p + 8 <= T.nparts; p += 8) {
+            int4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldg(reinterpret_cast<const int4*>(src + (p + u) * stride));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                s.x += v[u].x;
+                s.y += v[u].y;
+                s.z += v[u].z;
+                s.w += v[u].w;
             }
-            *reinterpret_cast<int4*>(acc + T.lo + i) = s;
         }
+        for (; p < T.nparts; ++p) {
+            const int4 v = __ldg(reinterpret_cast<const int4*>(src + p * stride));
+            s.x += v.x;
+            s.y += v.y;
+            s.z += v.z;
+            s.w += v.w;
+        }
+        *reinterpret_cast<int4*>((c ? n.acc1 : n.acc0) + T.lo + i) = s;
     }
 }
 
@@ -447,13 +462,13 @@ inline cudaError_t enqueue_tiled_receive(const TiledPlan& P, const Net& n, bool 
             k_receive_tiled<true, 2><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items);
         else
             k_receive_tiled<false, 2><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items);
-        if (P.n_merges) k_merge_parts<2><<<P.n_merges, 256, 0, s>>>(n, P.tiles, P.merges, P.partial);
+        if (P.n_merges) k_merge_parts<2><<<P.n_merges, kMergeChunk / 4, 0, s>>>(n, P.tiles, P.merges, P.partial);
     } else {
         if (w16)
             k_receive_tiled<true, 1><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items);
         else
             k_receive_tiled<false, 1><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items);
-        if (P.n_merges) k_merge_parts<1><<<P.n_merges, 256, 0, s>>>(n, P.tiles, P.merges, P.partial);
+        if (P.n_merges) k_merge_parts<1><<<P.n_merges, kMergeChunk / 4, 0, s>>>(n, P.tiles, P.merges, P.partial);
     }
     return cudaGetLastError();
 }
