@@ -1,0 +1,74 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py
+times (default receive, 16-bit weights, CUDA-graph steps, re-planned tiles).
+
+The batched sweep of 256 networks is too large for the oracle to run whole,
+but its networks are independent and each one's random draws depend only on
+(seed, instance, neuron, step): sampled networks are re-run alone by the
+oracle and must match bit for bit.  The 1M-neuron Vogels network and the
+100k-neuron Brunel+ network are compared whole over a window of steps.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import snn_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_run(gpu, prob, steps, chunks=(100,)):
+    net = gpu.Network(prob, log_capacity=prob.n * steps // 5 + (1 << 20))
+    t = 0
+    for c in chunks:
+        net.step(c)
+        t += c
+    if t < steps:
+        net.step(steps - t)
+    net.sync()
+    out = {"steps_ids": net.spikes(), "V": net.read("V"), "info": net.info(), "counters": net.counters()}
+    if prob.stdp:
+        out["w"] = net.read("w")
+    net.close()
+    return out
+
+
+def test_batched_sweep_256_sampled_networks(gpu):
+    prob = si.batched_sweep(256, base_seed=1, n_steps=0)
+    steps = 400  # crosses the first re-plan of the work items (step 256)
+    g = _gpu_run(gpu, prob, steps, chunks=(100, 200))
+    assert g["info"]["receive"] == "tiled"
+    gs, gi = g["steps_ids"]
+    sizes = np.array([inst.n for inst in prob.instances])
+    sample = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 37, 200})
+    for b in sample:
+        sub = si.sub_problem(prob, b, n_steps=steps)
+        o = oracle.run(sub, inst_key0=b)
+        lo, hi = int(prob.inst_off[b]), int(prob.inst_off[b + 1])
+        m = (gi >= lo) & (gi < hi)
+        assert len(o["ids"]) > 0
+        assert np.array_equal(gs[m], o["steps"]), b
+        assert np.array_equal(gi[m] - lo, o["ids"]), b
+        assert np.array_equal(g["V"][lo:hi].view(np.uint32), o["V"].view(np.uint32)), b
+
+
+def test_vogels_1m_whole_network(gpu):
+    prob = si.vogels_1m(seed=1, n_steps=120)
+    g = _gpu_run(gpu, prob, 120)
+    o = oracle.run(prob)
+    gs, gi = g["steps_ids"]
+    assert len(o["ids"]) > 1000
+    assert np.array_equal(gs, o["steps"]) and np.array_equal(gi, o["ids"])
+    assert np.array_equal(g["V"].view(np.uint32), o["V"].view(np.uint32))
+    assert g["counters"]["events"] == o["events"]
+
+
+def test_brunel_stdp_100k_whole_network(gpu):
+    prob = si.brunel_stdp_100k(seed=1, n_steps=300)
+    g = _gpu_run(gpu, prob, 300)
+    o = oracle.run(prob)
+    gs, gi = g["steps_ids"]
+    assert len(o["ids"]) > 1000
+    assert np.array_equal(gs, o["steps"]) and np.array_equal(gi, o["ids"])
+    assert np.array_equal(g["V"].view(np.uint32), o["V"].view(np.uint32))
+    assert np.array_equal(g["w"], o["w"])
+    assert not np.array_equal(o["w"], prob.w)
