@@ -195,9 +195,10 @@ int sm_count()
 
 // The kernels of one timestep, in pipeline order (Fig. 1).  ev, if given,
 // holds 6 events recorded between the phases.
-snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr)
+snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr, uint32_t k = 0)
 {
-    const Net& n = c->net;
+    Net n = c->net;
+    n.k = k;  // step = ctl->t + k
     if (ev) cudaEventRecord(ev[0], s);
     const uint32_t ublocks = grid_for(c->Np / kUpdateNeurons, 256);
     const uint32_t wblocks = (uint32_t)sm_count() * 8;
@@ -242,8 +243,10 @@ snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr)
         k_receive_global<false><<<wblocks, 256, 0, s>>>(n);
     }
     if (ev) cudaEventRecord(ev[4], s);
-    k_step_end<<<1, 256, 0, s>>>(n);
-    if (ev) cudaEventRecord(ev[5], s);
+    if (ev) {  // profiled steps run one at a time
+        k_advance<<<1, 1, 0, s>>>(c->ctl, 1);
+        cudaEventRecord(ev[5], s);
+    }
     CUDA_TRY(c, cudaGetLastError());
     return SNN_OK;
 }
@@ -253,7 +256,11 @@ snn_status capture(snn_ctx* c, uint32_t steps, cudaGraphExec_t* out)
     cudaGraph_t g = nullptr;
     CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     snn_status st = SNN_OK;
-    for (uint32_t i = 0; i < steps && st == SNN_OK; ++i) st = enqueue_step(c, c->cap_stream);
+    for (uint32_t i = 0; i < steps && st == SNN_OK; ++i) st = enqueue_step(c, c->cap_stream, nullptr, i);
+    if (st == SNN_OK) {
+        k_advance<<<1, 1, 0, c->cap_stream>>>(c->ctl, steps);
+        if (cudaGetLastError() != cudaSuccess) st = fail(c, SNN_E_CUDA, "graph capture: k_advance launch");
+    }
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
     if (st != SNN_OK) {
         if (g) cudaGraphDestroy(g);
@@ -338,6 +345,16 @@ snn_status retune(snn_ctx* c)
     std::vector<unsigned long long> spk(c->cfg.n_inst, 0);
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     CUDA_TRY(c, cudaMemcpy(spk.data(), c->net.inst_spikes, spk.size() * 8, cudaMemcpyDeviceToHost));
+    {  // the last step's counts are folded in by the next update
+        unsigned long long t = 0;
+        CUDA_TRY(c, cudaMemcpy(&t, &c->ctl->t, 8, cudaMemcpyDeviceToHost));
+        if (t > 0) {
+            std::vector<unsigned int> last(c->cfg.n_inst, 0);
+            CUDA_TRY(c, cudaMemcpy(last.data(), c->net.icount + (size_t)((t - 1) & (c->cr - 1)) * c->cfg.n_inst,
+                                   last.size() * 4, cudaMemcpyDeviceToHost));
+            for (uint32_t b = 0; b < c->cfg.n_inst; ++b) spk[b] += last[b];
+        }
+    }
     std::vector<double> work(c->cfg.n_inst, 0.0);
     double total = 0.0;
     for (uint32_t b = 0; b < c->cfg.n_inst; ++b) {
@@ -799,8 +816,16 @@ snn_status snn_read_spikes(snn_ctx* c, uint32_t t0, uint32_t t1, uint32_t* steps
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     Ctl h;
     CUDA_TRY(c, cudaMemcpy(&h, c->ctl, sizeof h, cudaMemcpyDeviceToHost));
+    // logged spikes: the last step's base plus its count (the next step's
+    // update would compute the same)
     unsigned long long total = 0;
-    CUDA_TRY(c, cudaMemcpy(&total, c->net.lbase + (h.t & (c->cr - 1)), 8, cudaMemcpyDeviceToHost));
+    if (h.t > h.t_log0) {
+        unsigned long long lb = 0;
+        unsigned int cnt = 0;
+        CUDA_TRY(c, cudaMemcpy(&lb, c->net.lbase + ((h.t - 1) & (c->cr - 1)), 8, cudaMemcpyDeviceToHost));
+        CUDA_TRY(c, cudaMemcpy(&cnt, c->net.count + ((h.t - 1) & (c->cr - 1)), 4, cudaMemcpyDeviceToHost));
+        total = lb + cnt;
+    }
     const uint64_t avail = std::min<uint64_t>(total, c->cfg.log_capacity);
     std::vector<unsigned long long> L(avail);
     if (avail) CUDA_TRY(c, cudaMemcpy(L.data(), c->net.log, avail * 8, cudaMemcpyDeviceToHost));
@@ -950,8 +975,10 @@ snn_status snn_counters(snn_ctx* c, uint64_t* steps, uint64_t* spikes, uint64_t*
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     Ctl h;
     CUDA_TRY(c, cudaMemcpy(&h, c->ctl, sizeof h, cudaMemcpyDeviceToHost));
+    unsigned int last = 0;  // the last step's spikes are folded in by the next update
+    if (h.t > 0) CUDA_TRY(c, cudaMemcpy(&last, c->net.count + ((h.t - 1) & (c->cr - 1)), 4, cudaMemcpyDeviceToHost));
     if (steps) *steps = h.t;
-    if (spikes) *spikes = h.spikes;
+    if (spikes) *spikes = h.spikes + last;
     if (events) *events = h.events;
     return SNN_OK;
 }

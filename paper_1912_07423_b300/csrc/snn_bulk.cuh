@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kBulkThreads, 1) k_receive_bulk(Net n, const T
     }
     __syncthreads();
 
-    const unsigned long long t = n.ctl->t;
+    const unsigned long long t = n.ctl->t + n.k;
     unsigned int* ctr = n.tile_ctr + (t & 1ull);
     const bool deliver = t + 1 >= n.d;
     const unsigned long long ts = deliver ? t + 1 - n.d : 0ull;

@@ -58,7 +58,7 @@ struct Ctl {
 struct Net {
     uint32_t Np, D, d, n_inst;
     uint32_t cr;               // count-ring length, a power of two >= D + 2
-    uint32_t pad0;
+    uint32_t k;                // this launch's step offset: step = ctl->t + k
     uint64_t seed;
     unsigned int* count;       // |S_t| over all instances at [t % cr]
     unsigned int* icount;      // |S_t| of instance b at [(t % cr) * n_inst + b]

@@ -40,7 +40,23 @@ template <int MODEL, bool STDP, bool STATS>
 __global__ void __launch_bounds__(256) k_update(Net n)
 {
     constexpr int NPT = kUpdateNeurons;  // neurons per thread
-    const unsigned long long t = n.ctl->t;
+    const unsigned long long t = n.ctl->t + n.k;
+    // per-step bookkeeping of the previous step (its kernels have finished):
+    // fold its queue indices into the counters, clear the next step's indices
+    // and the tile counter of the next receive
+    {
+        const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
+        const uint32_t sn = (uint32_t)((t + 1) & (n.cr - 1));
+        if (gt < n.n_inst) {
+            if (t > 0) n.inst_spikes[gt] += n.icount[(size_t)((t - 1) & (n.cr - 1)) * n.n_inst + gt];
+            n.icount[(size_t)sn * n.n_inst + gt] = 0;
+        }
+        if (gt == 0) {
+            if (t > 0) n.ctl->spikes += n.count[(t - 1) & (n.cr - 1)];
+            n.count[sn] = 0;
+            n.tile_ctr[(t + 1) & 1ull] = 0;
+        }
+    }
     const uint32_t G = n.Np / NPT;
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = g < G;  // whole warps: Np is a multiple of 256
@@ -195,6 +211,10 @@ __global__ void __launch_bounds__(256) k_update(Net n)
     const uint32_t lane = lane_id();
     const uint32_t slot_q = (uint32_t)(t % n.D);
     const uint32_t slot_c = (uint32_t)(t & (n.cr - 1));
+    if (blockIdx.x == 0 && threadIdx.x == 0 && n.log_cap) {
+        const unsigned long long tp = t - 1;
+        n.lbase[slot_c] = (t > n.ctl->t_log0) ? n.lbase[tp & (n.cr - 1)] + n.count[tp & (n.cr - 1)] : 0ull;
+    }
     if (STDP) {
         // 32 / NPT lanes cover one 32-neuron bitmask word
         constexpr uint32_t L = 32 / kUpdateNeurons;
@@ -222,8 +242,14 @@ __global__ void __launch_bounds__(256) k_update(Net n)
     wbase = __shfl_sync(kFull, wbase, 31);
     lpos = __shfl_sync(kFull, lpos, 31);
     if (!spk) return;
-    // log position of this step's first spike (written by the previous step's end)
-    const unsigned long long lb = n.log_cap ? n.lbase[slot_c] + lpos : 0ull;
+    // log position of this step's first spike: the previous step's base plus
+    // its count (0 at the first step of the log)
+    unsigned long long lb = 0;
+    if (n.log_cap) {
+        const unsigned long long tp = t - 1;
+        lb = (t > n.ctl->t_log0) ? n.lbase[tp & (n.cr - 1)] + n.count[tp & (n.cr - 1)] : 0ull;
+        lb += lpos;
+    }
     const uint32_t off = incl - c;
     uint32_t* q = n.q + (size_t)slot_q * n.Np + pbase + wbase + off;
     uint32_t m = spk, k = 0;
@@ -243,25 +269,10 @@ __global__ void __launch_bounds__(256) k_update(Net n)
     }
 }
 
-// End of a step: the log position of the next step's first spike follows
-// this step's; the queue indices of the next step start at zero; t += 1.
-__global__ void k_step_end(Net n)
-{
-    const unsigned long long t = n.ctl->t;
-    const uint32_t sc = (uint32_t)(t & (n.cr - 1)), sn = (uint32_t)((t + 1) & (n.cr - 1));
-    for (uint32_t b = threadIdx.x; b < n.n_inst; b += blockDim.x) {
-        n.inst_spikes[b] += n.icount[(size_t)sc * n.n_inst + b];
-        n.icount[(size_t)sn * n.n_inst + b] = 0;
-    }
-    if (threadIdx.x == 0) {
-        n.tile_ctr[(t + 1) & 1ull] = 0;
-        const uint32_t c = n.count[sc];
-        n.ctl->spikes += c;
-        n.lbase[sn] = n.lbase[sc] + c;
-        n.count[sn] = 0;
-        n.ctl->t = t + 1;
-    }
-}
+// The step counter advances once per captured graph (the kernels of a graph
+// carry their offset inside it); the per-step bookkeeping is done by the
+// next step's update kernel.
+__global__ void k_advance(Ctl* ctl, uint32_t steps) { ctl->t += steps; }
 
 // Visit the spikes of one queue slot, instance by instance, spreading them
 // over all warps of the grid: f(j) for every spiking padded id j.
@@ -293,7 +304,7 @@ __device__ __forceinline__ void for_each_spike(const Net& n, unsigned long long 
 template <bool W16>
 __global__ void __launch_bounds__(256) k_receive_global(Net n)
 {
-    const unsigned long long t = n.ctl->t;
+    const unsigned long long t = n.ctl->t + n.k;
     if (t + 1 < n.d) return;
     const uint32_t lane = lane_id();
     unsigned long long ev = 0;
@@ -333,7 +344,7 @@ __global__ void __launch_bounds__(256) k_receive_global(Net n)
 template <bool W16>
 __global__ void __launch_bounds__(256) k_stdp_depress(Net n)
 {
-    const unsigned long long t = n.ctl->t;
+    const unsigned long long t = n.ctl->t + n.k;
     if (t < n.d) return;
     const uint32_t lane = lane_id();
     for_each_spike(n, t - n.d, [&](uint32_t j) {
@@ -366,7 +377,7 @@ __global__ void __launch_bounds__(256) k_stdp_depress(Net n)
 template <bool W16>
 __global__ void __launch_bounds__(256) k_stdp_potentiate(Net n)
 {
-    const unsigned long long t = n.ctl->t;
+    const unsigned long long t = n.ctl->t + n.k;
     const uint32_t lane = lane_id();
     for_each_spike(n, t, [&](uint32_t i) {
         const InstDev* I = n.inst + __ldg(n.inst_of_w32 + (i >> 5));

@@ -80,17 +80,21 @@ template <bool W16, int CH>
 __global__ void __launch_bounds__(kTiledThreads, 1) k_receive_tiled(Net n, const TileDev* __restrict__ tiles,
                                                                     const uint32_t* __restrict__ items,
                                                                     const uint32_t* __restrict__ split,
-                                                                    int32_t* __restrict__ partial, uint32_t n_items)
+                                                                    int32_t* __restrict__ partial, uint32_t n_items,
+                                                                    uint32_t max_len)
 {
-    extern __shared__ __align__(16) int32_t acc_s[];  // CH * len of the current tile
+    extern __shared__ __align__(16) int32_t acc_s[];  // CH * max_len (the current tile uses CH * len)
     __shared__ uint32_t s_item;
-    const unsigned long long t = n.ctl->t;
+    const unsigned long long t = n.ctl->t + n.k;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     unsigned int* ctr = n.tile_ctr + (t & 1ull);
     const bool deliver = t + 1 >= n.d;
     const unsigned long long ts = deliver ? t + 1 - n.d : 0ull;
     unsigned long long ev = 0;  // every lane of a warp counts the warp's segments; lane 0 reports
     bool bad = false;           // a target outside the tile: the split table does not match the rows
+    // the accumulators start at zero, and every write-out leaves them at zero
+    for (uint32_t i = threadIdx.x; i < CH * max_len / 4; i += blockDim.x)
+        reinterpret_cast<int4*>(acc_s)[i] = make_int4(0, 0, 0, 0);
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1u);
         __syncthreads();
@@ -104,8 +108,6 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_receive_tiled(Net n, const
             __syncthreads();
             continue;
         }
-        for (uint32_t i = threadIdx.x; i < CH * T.len; i += blockDim.x) acc_s[i] = 0;
-        __syncthreads();
         const uint32_t pbase = __ldg(&n.inst[T.inst].pbase);
         const uint32_t* q = n.q + (size_t)(ts % n.D) * n.Np + pbase;
         const uint32_t nsplit = T.ntiles - 1;
@@ -214,11 +216,17 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_receive_tiled(Net n, const
             g0 = reinterpret_cast<int4*>(base);
             if (CH == 2) g1 = reinterpret_cast<int4*>(base + T.len);
         }
-        const int4* s0 = reinterpret_cast<const int4*>(acc_s);
-        for (uint32_t i = threadIdx.x; i < T.len / 4; i += blockDim.x) g0[i] = s0[i];
+        int4* s0 = reinterpret_cast<int4*>(acc_s);
+        for (uint32_t i = threadIdx.x; i < T.len / 4; i += blockDim.x) {
+            g0[i] = s0[i];
+            s0[i] = make_int4(0, 0, 0, 0);
+        }
         if (CH == 2) {
-            const int4* s1 = reinterpret_cast<const int4*>(acc_s + T.len);
-            for (uint32_t i = threadIdx.x; i < T.len / 4; i += blockDim.x) g1[i] = s1[i];
+            int4* s1 = reinterpret_cast<int4*>(acc_s + T.len);
+            for (uint32_t i = threadIdx.x; i < T.len / 4; i += blockDim.x) {
+                g1[i] = s1[i];
+                s1[i] = make_int4(0, 0, 0, 0);
+            }
         }
         __syncthreads();
     }
@@ -236,7 +244,7 @@ __global__ void __launch_bounds__(kMergeChunk / 4) k_merge_parts(Net n, const Ti
 {
     const MergeDev M = merges[blockIdx.x];
     const TileDev T = tiles[M.tile];
-    const unsigned long long t = n.ctl->t;
+    const unsigned long long t = n.ctl->t + n.k;
     if (t + 1 < n.d) return;
     const unsigned long long ts = t + 1 - n.d;
     if (n.icount[(size_t)(ts & (n.cr - 1)) * n.n_inst + T.inst] == 0) return;  // no part wrote anything
@@ -459,15 +467,15 @@ inline cudaError_t enqueue_tiled_receive(const TiledPlan& P, const Net& n, bool 
 {
     if (P.channels == 2) {
         if (w16)
-            k_receive_tiled<true, 2><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items);
+            k_receive_tiled<true, 2><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
         else
-            k_receive_tiled<false, 2><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items);
+            k_receive_tiled<false, 2><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
         if (P.n_merges) k_merge_parts<2><<<P.n_merges, kMergeChunk / 4, 0, s>>>(n, P.tiles, P.merges, P.partial);
     } else {
         if (w16)
-            k_receive_tiled<true, 1><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items);
+            k_receive_tiled<true, 1><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
         else
-            k_receive_tiled<false, 1><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items);
+            k_receive_tiled<false, 1><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
         if (P.n_merges) k_merge_parts<1><<<P.n_merges, kMergeChunk / 4, 0, s>>>(n, P.tiles, P.merges, P.partial);
     }
     return cudaGetLastError();
