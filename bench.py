@@ -43,6 +43,14 @@ B_NEURON = {si.BRUNEL: 18, si.VOGELS: 44}
 B_NEURON_STDP = 16
 
 
+def gpu_launches(steps: int, recv_kind: str, stdp: bool, per_graph: int = 16) -> int:
+    """Kernels of this library launched by `steps` steps of snn_step: the
+    update, the two STDP passes, the receive (tiled: per-step plan and
+    receive; bulk: receive, merge; global: receive), and one step-counter
+    advance per captured graph (per_graph steps, the rest one by one)."""
+    per_step = 1 + (2 if stdp else 0) + {"tiled": 2, "bulk": 2, "global": 1}[recv_kind]
+    return steps * per_step + steps // per_graph + steps % per_graph
+
 def kernel_source_hash() -> str:
     """Hash of the sources of the tiled receive (its ncu traffic figure is
     only reported while these are unchanged)."""
@@ -296,7 +304,7 @@ def run_ours(args, rank, world, dist):
            "step_roofline": {"bytes_per_step": step_b / args.steps, "frac": step_frac, "peak": hbm,
                              "unit": "GB/s", "achieved": step_b / t_main / 1e9},
            "phase_ms_per_step": {k: v / n_prof for k, v in phases.items()},
-           "gpu_launches": int(args.steps * (3 if not prob.stdp else 5)),
+           "gpu_launches": gpu_launches(args.steps, recv_kind, prob.stdp),
            "clocks": clk}
 
     # ---- plain single-precision weights + global-atomic receive, same networks

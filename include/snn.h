@@ -81,10 +81,11 @@ typedef struct {
     uint64_t log_capacity; /* spikes the raster log keeps (0: no log) */
     uint32_t receive;      /* SNN_RECV_* */
     uint32_t steps_per_graph; /* steps captured per CUDA graph (0: library default) */
-    uint32_t tune_steps;   /* tiled receive: at this step and at 8x this step of the first
-                              run the work items are re-cut by the spike counts measured
-                              since the previous cut (0: 256, 0xffffffff: never); results
-                              do not depend on the plan */
+    uint32_t tune_steps;   /* bulk-copy receive: at this step and at 8x this step of the
+                              first run its static work items are re-cut by the spike
+                              counts measured since the previous cut (0: 256, 0xffffffff:
+                              never); the tiled receive cuts its items on the device every
+                              step.  Results do not depend on the plan */
     uint32_t reserved;
 } snn_config;
 
@@ -145,18 +146,21 @@ snn_status snn_reset(snn_ctx* ctx);
 
 /* Enqueue n_steps timesteps on the context's stream and return without
  * waiting.  Device-side errors surface at the next call that synchronises.
- * With the tiled receive, a call that crosses a re-plan step (see
+ * With the bulk-copy receive, a call that crosses a re-plan step (see
  * cfg.tune_steps; twice per graph load) waits for the device, re-cuts the
  * work items by the measured work and re-captures its CUDA graphs before
  * going on. */
 snn_status snn_step(snn_ctx* ctx, uint32_t n_steps);
 
 /* Run n_steps timesteps without the CUDA graph, with CUDA events around
- * every kernel of the step, and wait for them.  phase_ms[5] receives the
+ * every kernel of the step, and wait for them.  phase_ms[6] receives the
  * summed device time of each phase: [0] Update Synapses (depression),
  * [1] Update Neurons, [2] Update Synapses (potentiation), [3] Receive
- * Spikes, [4] end-of-step bookkeeping.  Used to measure one kernel's share
- * of the step; the simulation advances exactly as with snn_step. */
+ * Spikes (the receive kernel; with the tiled receive also any wait for its
+ * per-step plan, which runs beside [0]-[2] when the delay is 2 or more and
+ * before [3] otherwise), [4] the merge of the receive's partial
+ * accumulators, [5] end-of-step bookkeeping.  Used to measure one kernel's
+ * share of the step; the simulation advances exactly as with snn_step. */
 snn_status snn_step_profiled(snn_ctx* ctx, uint32_t n_steps, double* phase_ms);
 
 /* Wait for the enqueued work; returns the first pending device-side error. */

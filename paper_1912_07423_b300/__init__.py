@@ -226,9 +226,9 @@ class Network:
 
     def step_profiled(self, n_steps: int) -> dict:
         """Steps with per-kernel CUDA events; summed device ms per phase."""
-        ms = (ctypes.c_double * 5)()
+        ms = (ctypes.c_double * 6)()
         self._check(self.lib.snn_step_profiled(self.ctx, int(n_steps), ms), "snn_step_profiled")
-        return dict(zip(["depress", "update", "potentiate", "receive", "step_end"], list(ms)))
+        return dict(zip(["depress", "update", "potentiate", "receive", "merge", "step_end"], list(ms)))
 
     def sync(self):
         self._check(self.lib.snn_sync(self.ctx), "snn_sync")

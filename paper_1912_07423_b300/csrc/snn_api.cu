@@ -29,6 +29,8 @@ struct snn_ctx {
     snn_device dev{};
     cudaStream_t stream = nullptr;   // user stream (may be the legacy default)
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t side = nullptr;       // the per-step plan, beside the update when the delay allows
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
 
     // sizes and host mirrors of the layout
@@ -194,7 +196,9 @@ int sm_count()
 }
 
 // The kernels of one timestep, in pipeline order (Fig. 1).  ev, if given,
-// holds 6 events recorded between the phases.
+// holds kPhases + 1 events recorded between the phases.
+constexpr int kPhases = 6;
+
 snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr, uint32_t k = 0)
 {
     Net n = c->net;
@@ -202,6 +206,17 @@ snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr, u
     if (ev) cudaEventRecord(ev[0], s);
     const uint32_t ublocks = grid_for(c->Np / kUpdateNeurons, 256);
     const uint32_t wblocks = (uint32_t)sm_count() * 8;
+    // the tiled receive's plan reads the spike counts of step t + 1 - d: with
+    // d >= 2 they are final before this step's update, and the plan runs
+    // beside it (after the previous step's merge, which read the last plan)
+    const bool planned = c->use_tiled && !c->use_bulk;
+    const bool fork = planned && c->cfg.delay >= 2;
+    if (fork) {
+        CUDA_TRY(c, cudaEventRecord(c->ev_fork, s));
+        CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        CUDA_TRY(c, enqueue_tiled_plan(c->tiled, n, c->side));
+        CUDA_TRY(c, cudaEventRecord(c->ev_join, c->side));
+    }
     if (c->stdp) {
         if (c->w16)
             k_stdp_depress<true><<<wblocks, 256, 0, s>>>(n);
@@ -233,19 +248,27 @@ snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr, u
             k_stdp_potentiate<false><<<wblocks, 256, 0, s>>>(n);
     }
     if (ev) cudaEventRecord(ev[3], s);
+    cudaEvent_t mid = ev ? ev[4] : nullptr;  // between the receive and the merge
     if (c->use_tiled && c->use_bulk) {
-        CUDA_TRY(c, enqueue_bulk_receive(c->tiled, n, c->w16, s));
+        CUDA_TRY(c, enqueue_bulk_receive(c->tiled, n, c->w16, s, mid));
     } else if (c->use_tiled) {
+        if (fork)
+            CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_join, 0));
+        else
+            CUDA_TRY(c, enqueue_tiled_plan(c->tiled, n, s));
         CUDA_TRY(c, enqueue_tiled_receive(c->tiled, n, c->w16, s));
-    } else if (c->w16) {
-        k_receive_global<true><<<wblocks, 256, 0, s>>>(n);
+        if (mid) cudaEventRecord(mid, s);  // no merge: the parts add into the accumulators
     } else {
-        k_receive_global<false><<<wblocks, 256, 0, s>>>(n);
+        if (c->w16)
+            k_receive_global<true><<<wblocks, 256, 0, s>>>(n);
+        else
+            k_receive_global<false><<<wblocks, 256, 0, s>>>(n);
+        if (mid) cudaEventRecord(mid, s);
     }
-    if (ev) cudaEventRecord(ev[4], s);
+    if (ev) cudaEventRecord(ev[5], s);
     if (ev) {  // profiled steps run one at a time
         k_advance<<<1, 1, 0, s>>>(c->ctl, 1);
-        cudaEventRecord(ev[5], s);
+        cudaEventRecord(ev[6], s);
     }
     CUDA_TRY(c, cudaGetLastError());
     return SNN_OK;
@@ -286,6 +309,7 @@ snn_status check_device_errors(snn_ctx* c)
     CUDA_TRY(c, cudaMemcpyAsync(&err, &c->ctl->err, sizeof err, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     if (err & kErrTimeout) return fail(c, SNN_E_TIMEOUT, "a bounded device-side wait gave up");
+    if (err & kErrPlan) return fail(c, SNN_E_OVERFLOW, "the receive plan of a step did not fit its buffer");
     if (err & kErrLogOverflow)
         return fail(c, SNN_E_OVERFLOW, "the spike log is full (log_capacity = %llu)",
                     (unsigned long long)c->cfg.log_capacity);
@@ -325,7 +349,7 @@ snn_status plan_tiles(snn_ctx* c, const double* work)
     const uint32_t max_len = (c->use_bulk ? bulk_len : 57344u) / ch / 256u * 256u;
     snn_status st = tiled_plan(c->tiled, c->net, c->params.data(), c->pbase.data(), c->cfg.n_inst, (int)ch, max_len,
                                work, c->inst_edges.data(), sm_count(), [c](size_t b) { return dev_alloc(c, b); },
-                               [c](void* p) { dev_free(c, p); }, c->stream);
+                               [c](void* p) { dev_free(c, p); }, c->stream, !c->use_bulk);
     if (st == SNN_OK && c->use_bulk) {
         int dev = 0, optin = 0;
         cudaGetDevice(&dev);
@@ -438,8 +462,15 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
         c->g_off[b + 1] = c->g_off[b] + params[b].n;
         c->pbase[b + 1] = c->pbase[b] + (params[b].n + kPad - 1) / kPad * kPad;
     }
-    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
+        if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+        if (c->side) cudaStreamDestroy(c->side);
+        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        if (c->ev_join) cudaEventDestroy(c->ev_join);
         delete c;
         return SNN_E_CUDA;
     }
@@ -745,8 +776,9 @@ snn_status snn_step(snn_ctx* c, uint32_t n_steps)
     if (!c) return SNN_E_ARG;
     if (!c->graph_loaded) return fail(c, SNN_E_STATE, "snn_step before snn_build_graph");
     uint32_t left = n_steps;
-    // re-plan the tiled receive twice, at tune_steps and 8 x tune_steps
-    while (c->use_tiled && c->tune_count < 2 && c->cfg.tune_steps != 0xffffffffu &&
+    // re-plan the static plan of the bulk-copy receive twice, at tune_steps
+    // and 8 x tune_steps (the tiled receive plans every step on the device)
+    while (c->use_tiled && c->use_bulk && c->tune_count < 2 && c->cfg.tune_steps != 0xffffffffu &&
            c->host_steps + left >= c->tune_next) {
         uint32_t first = (uint32_t)(c->tune_next > c->host_steps ? c->tune_next - c->host_steps : 0);
         left -= first;
@@ -773,8 +805,8 @@ snn_status snn_step_profiled(snn_ctx* c, uint32_t n_steps, double* phase_ms)
 {
     if (!c || !phase_ms) return SNN_E_ARG;
     if (!c->graph_loaded) return fail(c, SNN_E_STATE, "snn_step_profiled before snn_build_graph");
-    for (int k = 0; k < 5; ++k) phase_ms[k] = 0.0;
-    std::vector<cudaEvent_t> ev((size_t)n_steps * 6);
+    for (int k = 0; k < kPhases; ++k) phase_ms[k] = 0.0;
+    std::vector<cudaEvent_t> ev((size_t)n_steps * (kPhases + 1));
     for (auto& e : ev)
         if (cudaEventCreate(&e) != cudaSuccess) {
             cudaGetLastError();
@@ -782,16 +814,17 @@ snn_status snn_step_profiled(snn_ctx* c, uint32_t n_steps, double* phase_ms)
         }
     snn_status st = SNN_OK;
     for (uint32_t i = 0; i < n_steps && st == SNN_OK; ++i) {
-        for (int k = 0; k < 6; ++k)
-            if (!ev[(size_t)i * 6 + k]) st = fail(c, SNN_E_CUDA, "cudaEventCreate failed");
-        if (st == SNN_OK) st = enqueue_step(c, c->stream, &ev[(size_t)i * 6]);
+        for (int k = 0; k <= kPhases; ++k)
+            if (!ev[(size_t)i * (kPhases + 1) + k]) st = fail(c, SNN_E_CUDA, "cudaEventCreate failed");
+        if (st == SNN_OK) st = enqueue_step(c, c->stream, &ev[(size_t)i * (kPhases + 1)]);
     }
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (st == SNN_OK && e != cudaSuccess) st = fail(c, SNN_E_CUDA, "profiled steps: %s", cudaGetErrorString(e));
     for (uint32_t i = 0; i < n_steps && st == SNN_OK; ++i)
-        for (int k = 0; k < 5; ++k) {
+        for (int k = 0; k < kPhases; ++k) {
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, ev[(size_t)i * 6 + k], ev[(size_t)i * 6 + k + 1]) == cudaSuccess)
+            const size_t b = (size_t)i * (kPhases + 1) + k;
+            if (cudaEventElapsedTime(&ms, ev[b], ev[b + 1]) == cudaSuccess)
                 phase_ms[k] += ms;
         }
     for (auto& x : ev)
@@ -1041,6 +1074,9 @@ void snn_destroy(snn_ctx* c)
     drop_graphs(c);
     while (!c->allocs.empty()) dev_free(c, c->allocs.back().p);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     cudaGetLastError();
     delete c;
 }

@@ -317,7 +317,8 @@ inline cudaError_t bulk_set_smem(size_t smem)
     return e;
 }
 
-inline cudaError_t enqueue_bulk_receive(const TiledPlan& P, const Net& n, bool w16, cudaStream_t s)
+inline cudaError_t enqueue_bulk_receive(const TiledPlan& P, const Net& n, bool w16, cudaStream_t s,
+                                        cudaEvent_t mid = nullptr /* recorded between the receive and the merge */)
 {
     const size_t smem = bulk_smem(P.max_len, P.channels, w16);
     if (P.channels == 2) {
@@ -325,12 +326,14 @@ inline cudaError_t enqueue_bulk_receive(const TiledPlan& P, const Net& n, bool w
             k_receive_bulk<true, 2><<<P.grid, kBulkThreads, smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
         else
             k_receive_bulk<false, 2><<<P.grid, kBulkThreads, smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
+        if (mid) cudaEventRecord(mid, s);
         if (P.n_merges) k_merge_parts<2><<<P.n_merges, kMergeChunk / 4, 0, s>>>(n, P.tiles, P.merges, P.partial);
     } else {
         if (w16)
             k_receive_bulk<true, 1><<<P.grid, kBulkThreads, smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
         else
             k_receive_bulk<false, 1><<<P.grid, kBulkThreads, smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
+        if (mid) cudaEventRecord(mid, s);
         if (P.n_merges) k_merge_parts<1><<<P.n_merges, kMergeChunk / 4, 0, s>>>(n, P.tiles, P.merges, P.partial);
     }
     return cudaGetLastError();

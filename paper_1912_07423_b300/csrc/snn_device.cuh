@@ -31,6 +31,7 @@ enum : uint32_t {
     kErrBadWeight = 4u,
     kErrPlasticShift = 8u,
     kErrTimeout = 16u,
+    kErrPlan = 32u,  // the per-step receive plan did not fit its buffer (not reached: the buffer is sized for the bound)
 };
 
 // Per-instance constants, each binary32 value the binary64 expression

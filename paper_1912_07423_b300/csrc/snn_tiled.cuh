@@ -12,18 +12,28 @@
 //     memory; a larger instance is cut by target id into several tiles, and
 //     the segment of a (sorted) row inside each tile comes from a split table
 //     built once with the graph;
-//   * a tile whose expected work is large is split by SPIKES into P parts:
-//     part p delivers its share of the instance's spikes into a private copy
-//     of the tile's accumulators.  A part that is alone stores its copy to the
-//     global accumulators; otherwise it stores it to a partial buffer, and a
-//     second kernel adds the P partials up (coalesced, L2-resident).
+//   * every step a one-block kernel (k_plan) cuts the work of that step from
+//     the spike counts of the step being delivered: tile k, with c_k arriving
+//     spikes and w_k = c_k s_k expected work (s_k: mean row segment plus a
+//     fixed cost per spike), gets P_k = ceil(w_k / target) spike parts,
+//     target = sum(w) / (kItemsPerCta * CTAs); part p delivers spikes
+//     [c_k p / P_k, c_k (p+1) / P_k).  The (tile, part) items are listed
+//     heaviest first, and a persistent grid takes them one after the other
+//     from an atomic counter;
+//   * a part's copy of the accumulators leaves shared memory by one bulk
+//     asynchronous copy (the TMA engine): a tile's only part copies it over
+//     the global accumulators, the parts of a split tile add it into them
+//     with the copy's element-wise integer reduction in L2 (the update left
+//     them at zero).  Integer sums do not depend on the order of the adds.
 //
 // Every edge is read once per step, in whole coalesced rows; no global
-// atomics are issued.  The (tile, part) work items are listed heaviest first
-// and a persistent grid takes them one after the other from an atomic
-// counter.  Expected work comes from the edges at first and from the spike
-// counts measured on the first steps after the one-time re-plan; results do
-// not depend on the plan, only the balance across SMs does.
+// atomics are issued by the threads.  The plan follows each step's spikes,
+// so a burst in one network is cut as finely as it needs; results do not
+// depend on the plan, only the balance across SMs does.
+//
+// The bulk-copy kernel (snn_bulk.cuh) uses the same tiles with a static plan
+// cut on the host from the expected or measured spike rates
+// (TileDev::nparts, part_base; re-cut on the first steps).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -42,24 +52,40 @@ struct TileDev {
     uint32_t inst;                  // instance
     uint32_t lo, len;               // padded id range [lo, lo + len); len is a multiple of 256
     uint32_t tau, ntiles;           // tile index inside the instance, tiles of the instance
-    uint32_t nparts;                // spike parts of this tile
+    uint32_t nparts;                // static plan: spike parts of this tile
+    uint32_t pad;
+    float seg;                      // per-step plan: expected work per arriving spike (edges)
     unsigned long long split;       // base of the instance's split table: n_b rows x (ntiles-1) uint32
-    unsigned long long part_base;   // base of the tile's partials (nparts x len int32) if nparts > 1
+    unsigned long long part_base;   // static plan: base of the partials (nparts x CH x len int32) if nparts > 1
 };
 
 struct MergeDev {  // one chunk of a multi-part tile to add up
     uint32_t tile, off, len, pad;
 };
 
+// The plan of one step, written by k_plan and read by the receive.
+struct StepPlan {
+    uint32_t* hdr = nullptr;    // [0] items
+    uint32_t* items = nullptr;  // (tile << 8 | part), heaviest first
+    uint32_t* parts = nullptr;  // P_k (0: no spike arrives)
+};
+
 struct TiledPlan {
     TileDev* tiles = nullptr;
-    uint32_t* items = nullptr;   // (tile << 8 | part), heaviest first
     uint32_t* split = nullptr;
     int32_t* partial = nullptr;
+    // static plan (bulk-copy receive)
+    uint32_t* items = nullptr;   // (tile << 8 | part), heaviest first
     MergeDev* merges = nullptr;
-    uint32_t n_tiles = 0, n_items = 0, n_merges = 0;
+    uint32_t n_items = 0, n_merges = 0;
+    // per-step plan (tiled receive)
+    StepPlan step;
+    bool dynamic = false;
+    uint32_t n_tiles = 0;
     uint32_t max_len = 0;
     uint32_t grid = 0;
+    uint32_t cap = 1;            // most parts of a tile in one step
+    uint32_t items_cap = 0;      // per-step plan: room for items
     int channels = 1;
     int threads = 1024;
     size_t smem = 0;
@@ -69,30 +95,359 @@ constexpr int kTiledThreads = 1024;
 constexpr int kVec = 4;            // 4-edge vectors in flight per lane
 constexpr uint32_t kMaxParts = 255;
 constexpr uint32_t kMergeChunk = 4096;
+constexpr int kPlanThreads = 1024;
+constexpr uint32_t kPlanMaxTiles = 4096;
+constexpr uint32_t kRankSortMax = 1024;  // up to this many tiles the plan sorts by rank, above by a bitonic network
+constexpr float kItemsPerCta = 1.5f;     // per-step plan: items per CTA at the target size
+constexpr float kSpikeCost = 8.0f;     // fixed work of one arriving spike, in edges
 
-template <bool W16>
-__device__ __forceinline__ int32_t weight_at(const Net& n, uint64_t e, uint32_t shift)
+// Edges are read once per step and never again before the rest of the
+// (larger than L2) graph has streamed by, so their loads carry an L2
+// evict-first policy: L2 keeps the partials, accumulators, queues and row
+// records instead.
+__device__ __forceinline__ unsigned long long evict_first_policy()
 {
-    return W16 ? ((int32_t)__ldg(n.w16 + e) << shift) : __float2int_rz(__ldg(n.w32 + e));
+    unsigned long long p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
 
+__device__ __forceinline__ uint4 ld_edges4(const void* ptr, unsigned long long pol)
+{
+    uint4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(ptr), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ uint2 ld_edges2(const void* ptr, unsigned long long pol)
+{
+    uint2 v;
+    asm("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(ptr), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_edge(const uint32_t* ptr, unsigned long long pol)
+{
+    uint32_t v;
+    asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ uint16_t ld_edge16(const int16_t* ptr, unsigned long long pol)
+{
+    uint16_t v;
+    asm("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
+
+template <bool W16>
+__device__ __forceinline__ int32_t weight_at(const Net& n, uint64_t e, uint32_t shift, unsigned long long pol)
+{
+    if (W16) return (int32_t)(int16_t)ld_edge16(n.w16 + e, pol) << shift;
+    return __float2int_rz(__uint_as_float(ld_edge(reinterpret_cast<const uint32_t*>(n.w32 + e), pol)));
+}
+
+// Adds the edges [sb, se) of one row into the tile's accumulators a (one
+// warp, all lanes; targets are padded ids, lo the tile's first).  Edges
+// [a4, b4) are read 4 at a time (16-byte target, 8- or 16-byte weight
+// loads); the unaligned head and tail, one edge per lane, are loaded with
+// the first vectors so that they cost no round trip of their own.
+template <bool W16>
+__device__ __forceinline__ void add_segment(const Net& n, int32_t* a, uint64_t sb, uint64_t se, uint32_t shift,
+                                            uint32_t lo, uint32_t len, uint32_t lane, unsigned long long pol,
+                                            bool& bad)
+{
+    const uint64_t up4 = (sb + 3) & ~3ull, dn4 = se & ~3ull;
+    const uint64_t a4 = up4 < se ? up4 : se;
+    const uint64_t b4 = dn4 > a4 ? dn4 : a4;
+    uint32_t hx = 0;
+    int32_t hw = 0;
+    bool head = false;
+    {
+        uint64_t e = ~0ull;
+        if (lane < a4 - sb)
+            e = sb + lane;
+        else if (lane >= 4 && lane - 4 < se - b4)
+            e = b4 + (lane - 4);
+        if (e != ~0ull) {
+            hx = ld_edge(n.tgt + e, pol) - lo;
+            hw = weight_at<W16>(n, e, shift, pol);
+            head = true;
+        }
+    }
+    for (uint64_t base = a4; base < b4; base += 128 * kVec) {
+        uint4 tv[kVec];
+        int32_t wv[kVec][4];
+#pragma unroll
+        for (int u = 0; u < kVec; ++u) {
+            const uint64_t e = base + 128 * u + 4 * lane;
+            tv[u] = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+            wv[u][0] = wv[u][1] = wv[u][2] = wv[u][3] = 0;
+            if (e < b4) {
+                tv[u] = ld_edges4(n.tgt + e, pol);
+                if (W16) {
+                    const uint2 h = ld_edges2(n.w16 + e, pol);
+                    wv[u][0] = (int32_t)(int16_t)(h.x & 0xffffu) << shift;
+                    wv[u][1] = (int32_t)(int16_t)(h.x >> 16) << shift;
+                    wv[u][2] = (int32_t)(int16_t)(h.y & 0xffffu) << shift;
+                    wv[u][3] = (int32_t)(int16_t)(h.y >> 16) << shift;
+                } else {
+                    const uint4 f = ld_edges4(n.w32 + e, pol);
+                    wv[u][0] = __float2int_rz(__uint_as_float(f.x));
+                    wv[u][1] = __float2int_rz(__uint_as_float(f.y));
+                    wv[u][2] = __float2int_rz(__uint_as_float(f.z));
+                    wv[u][3] = __float2int_rz(__uint_as_float(f.w));
+                }
+            }
+        }
+        if (head) {
+            if (hx < len)
+                atomicAdd(a + hx, hw);
+            else
+                bad = true;
+            head = false;
+        }
+#pragma unroll
+        for (int u = 0; u < kVec; ++u) {
+            if (base + 128 * u + 4 * lane >= b4) continue;
+            const uint32_t xs[4] = {tv[u].x - lo, tv[u].y - lo, tv[u].z - lo, tv[u].w - lo};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (xs[k] < len)
+                    atomicAdd(a + xs[k], wv[u][k]);
+                else
+                    bad = true;
+            }
+        }
+    }
+    if (head) {  // a row with no whole vector
+        if (hx < len)
+            atomicAdd(a + hx, hw);
+        else
+            bad = true;
+    }
+}
+
+// Delivers the spikes [s_beg, s_end) of the instance's queue q (local ids
+// from pbase) to tile T: one spike per warp, warps strided; the next spike's
+// row record is fetched while the current row is delivered.
+template <bool W16, int CH>
+__device__ __forceinline__ void deliver_part(const Net& n, const TileDev& T, const uint32_t* q, uint32_t pbase,
+                                             const uint32_t* sp, int32_t* acc_s, uint32_t s_beg, uint32_t s_end,
+                                             unsigned long long pol, unsigned long long& ev, bool& bad)
+{
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t nsplit = T.ntiles - 1;
+    uint32_t s = s_beg + warp;
+    uint32_t j = 0;
+    uint4 r = make_uint4(0, 0, 0, 0);
+    if (s < s_end) {
+        j = q[s];
+        r = __ldg(n.rinfo + j);
+    }
+    while (s < s_end) {
+        const uint32_t s_next = s + nwarps;
+        uint32_t j_next = 0;
+        uint4 r_next = make_uint4(0, 0, 0, 0);
+        if (s_next < s_end) {
+            j_next = q[s_next];
+            r_next = __ldg(n.rinfo + j_next);
+        }
+        uint64_t sb = ((unsigned long long)r.y << 32) | r.x;
+        uint64_t se = sb + r.z;
+        if (nsplit) {
+            const uint32_t* sj = sp + (size_t)(j - pbase) * nsplit;
+            const uint64_t beg = sb;
+            if (T.tau > 0) sb = beg + __ldg(sj + T.tau - 1);
+            if (T.tau < nsplit) se = beg + __ldg(sj + T.tau);
+        }
+        ev += se - sb;
+        int32_t* a = acc_s + ((CH == 2 && (r.w & 0x80u)) ? T.len : 0u);
+        add_segment<W16>(n, a, sb, se, r.w & 31u, T.lo, T.len, lane, pol, bad);
+        s = s_next;
+        j = j_next;
+        r = r_next;
+    }
+}
+
+// Shared memory of k_plan for n_pad (a power of two >= the tiles) entries.
+__host__ __device__ inline size_t plan_smem(uint32_t n_pad) { return (size_t)n_pad * 16; }
+
+// The plan of step t's receive (one block).  Tile k gets P_k parts as the
+// header of this file states; the items are ordered by work per part,
+// heaviest first, ties by tile index: 64-bit keys sorted by rank (each key
+// counts the smaller ones) or, for many tiles, by a bitonic network.
+__global__ void __launch_bounds__(kPlanThreads, 1) k_plan(Net n, const TileDev* __restrict__ tiles, uint32_t n_tiles,
+                                                          StepPlan sp, uint32_t n_ctas, uint32_t cap, uint32_t items_cap)
+{
+    extern __shared__ __align__(16) unsigned char plan_s[];
+    __shared__ float red[32];
+    __shared__ uint32_t s_act, s_items;
+    const unsigned long long t = n.ctl->t + n.k;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    if (t + 1 < n.d) {
+        if (threadIdx.x == 0) sp.hdr[0] = 0;
+        return;
+    }
+    uint32_t n_pad = 1;
+    while (n_pad < n_tiles) n_pad <<= 1;
+    unsigned long long* key = reinterpret_cast<unsigned long long*>(plan_s);  // later: item offset by position
+    uint32_t* pk = reinterpret_cast<uint32_t*>(key + n_pad);                 // spikes, then P_k
+    float* wk = reinterpret_cast<float*>(pk + n_pad);                        // later: rank, then tile by position
+    uint32_t* at = reinterpret_cast<uint32_t*>(wk);
+    uint32_t* off = reinterpret_cast<uint32_t*>(key);
+    if (threadIdx.x == 0) s_act = 0;
+    const unsigned long long ts = t + 1 - n.d;
+    const uint32_t* cnt = n.icount + (size_t)(ts & (n.cr - 1)) * n.n_inst;
+    float wsum = 0.f;
+    for (uint32_t k = threadIdx.x; k < n_tiles; k += blockDim.x) {
+        const uint32_t c = cnt[__ldg(&tiles[k].inst)];
+        const float w = (float)c * __ldg(&tiles[k].seg);
+        pk[k] = c;
+        wk[k] = w;
+        wsum += w;
+    }
+    for (int o = 16; o; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    if (lane == 0) red[warp] = wsum;
+    __syncthreads();
+    float W = 0.f;
+    for (uint32_t i = 0; i < blockDim.x / 32; ++i) W += red[i];
+    const float target = W / (kItemsPerCta * (float)n_ctas);
+    for (uint32_t k = threadIdx.x; k < n_pad; k += blockDim.x) {
+        unsigned long long kk = ~0ull;
+        if (k < n_tiles) {
+            const uint32_t c = pk[k];
+            uint32_t P = 0;
+            if (c) {
+                P = 1;
+                if (target > 0.f) {
+                    const float x = ceilf(wk[k] / target);
+                    P = x < (float)cap ? (x > 1.f ? (uint32_t)x : 1u) : cap;
+                }
+                P = P < c ? P : c;
+                kk = ((unsigned long long)(~__float_as_uint(wk[k] / (float)P)) << 32) | k;
+                atomicAdd(&s_act, 1u);
+            }
+            pk[k] = P;
+            sp.parts[k] = P;
+        }
+        key[k] = kk;
+    }
+    __syncthreads();
+    const uint32_t n_act = s_act;  // the active keys sort first
+    if (n_pad <= kRankSortMax) {
+        // rank of key k = keys below it; g threads per key, each over n_pad / g keys
+        uint32_t* rank = at;
+        for (uint32_t k = threadIdx.x; k < n_pad; k += blockDim.x) rank[k] = 0;
+        __syncthreads();
+        uint32_t g = n_pad >= blockDim.x ? 1u : blockDim.x / n_pad;  // a power of two
+        g = g < n_pad ? g : n_pad;  // at least one key per thread
+        const uint32_t span = n_pad / g;
+        for (uint32_t idx = threadIdx.x; idx < n_pad * g; idx += blockDim.x) {
+            const uint32_t k = idx / g, j0 = (idx % g) * span;
+            const unsigned long long kk = key[k];
+            if (kk == ~0ull) continue;
+            uint32_t c = 0;
+            for (uint32_t j = j0; j < j0 + span; ++j) c += key[j] < kk ? 1u : 0u;
+            if (c) atomicAdd(&rank[k], c);
+        }
+        __syncthreads();
+        uint32_t r[kRankSortMax / kPlanThreads];
+        for (uint32_t i = 0, k = threadIdx.x; i < kRankSortMax / kPlanThreads; ++i, k += blockDim.x)
+            r[i] = (k < n_pad && key[k] != ~0ull) ? rank[k] : ~0u;
+        __syncthreads();
+        for (uint32_t i = 0, k = threadIdx.x; i < kRankSortMax / kPlanThreads; ++i, k += blockDim.x)
+            if (r[i] != ~0u) at[r[i]] = k;
+    } else {
+        for (uint32_t size = 2; size <= n_pad; size <<= 1) {
+            for (uint32_t stride = size >> 1; stride; stride >>= 1) {
+                for (uint32_t i = threadIdx.x; i < n_pad / 2; i += blockDim.x) {
+                    const uint32_t lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+                    const unsigned long long a = key[lo], b = key[hi];
+                    if ((a > b) == ((lo & size) == 0)) {
+                        key[lo] = b;
+                        key[hi] = a;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (uint32_t pos = threadIdx.x; pos < n_act; pos += blockDim.x) at[pos] = (uint32_t)key[pos];
+    }
+    __syncthreads();
+    // warp 0: item offsets by position; lane l takes positions [l m, (l+1) m)
+    if (warp == 0) {
+        const uint32_t m = (n_act + 31) / 32;
+        const uint32_t beg = lane * m < n_act ? lane * m : n_act, end = beg + m < n_act ? beg + m : n_act;
+        uint32_t ni = 0;
+        for (uint32_t pos = beg; pos < end; ++pos) ni += pk[at[pos]];
+        uint32_t x = ni;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= (uint32_t)o) x += y;
+        }
+        uint32_t o = x - ni;
+        for (uint32_t pos = beg; pos < end; ++pos) {
+            off[pos] = o;
+            o += pk[at[pos]];
+        }
+        if (lane == 31) {
+            const bool fits = x <= items_cap;
+            if (!fits) atomicOr(&n.ctl->err, kErrPlan);
+            s_items = fits ? x : 0u;
+            sp.hdr[0] = fits ? x : 0u;
+        }
+    }
+    __syncthreads();
+    // every thread: item i belongs to the last position whose offset is <= i
+    const uint32_t n_items = s_items;
+    for (uint32_t i = threadIdx.x; i < n_items; i += blockDim.x) {
+        uint32_t lo = 0, hi = n_act;  // off[lo] <= i < off[hi] (off[n_act] = n_items)
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (off[mid] <= i)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        sp.items[i] = (at[lo] << 8) | (i - off[lo]);
+    }
+}
+
+// Issues the bulk copy of bytes of shared memory s to global memory g, as a
+// plain copy or an element-wise int32 add into g.  Both addresses 16-byte
+// aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_out(int32_t* g, const int32_t* s, uint32_t bytes, bool add)
+{
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(s);
+    if (add)
+        asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.s32 [%0], [%1], %2;"
+                     ::"l"(g), "r"(sa), "r"(bytes) : "memory");
+    else
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(g), "r"(sa), "r"(bytes)
+                     : "memory");
+}
+
+// The receive of one step under the per-step plan.
 template <bool W16, int CH>
 __global__ void __launch_bounds__(kTiledThreads, 1) k_receive_tiled(Net n, const TileDev* __restrict__ tiles,
-                                                                    const uint32_t* __restrict__ items,
-                                                                    const uint32_t* __restrict__ split,
-                                                                    int32_t* __restrict__ partial, uint32_t n_items,
-                                                                    uint32_t max_len)
+                                                                    uint32_t n_tiles, StepPlan sp,
+                                                                    const uint32_t* __restrict__ split, uint32_t max_len)
 {
     extern __shared__ __align__(16) int32_t acc_s[];  // CH * max_len (the current tile uses CH * len)
     __shared__ uint32_t s_item;
     const unsigned long long t = n.ctl->t + n.k;
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t lane = threadIdx.x & 31u;
     unsigned int* ctr = n.tile_ctr + (t & 1ull);
-    const bool deliver = t + 1 >= n.d;
-    const unsigned long long ts = deliver ? t + 1 - n.d : 0ull;
+    const uint32_t n_items = sp.hdr[0];
+    const unsigned long long ts = t + 1 >= n.d ? t + 1 - n.d : 0ull;
     unsigned long long ev = 0;  // every lane of a warp counts the warp's segments; lane 0 reports
     bool bad = false;           // a target outside the tile: the split table does not match the rows
-    // the accumulators start at zero, and every write-out leaves them at zero
+    if (n_items == 0) return;
+    const unsigned long long pol = evict_first_policy();
+    // the accumulators start at zero, and every item leaves them at zero
     for (uint32_t i = threadIdx.x; i < CH * max_len / 4; i += blockDim.x)
         reinterpret_cast<int4*>(acc_s)[i] = make_int4(0, 0, 0, 0);
     for (;;) {
@@ -100,163 +455,55 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_receive_tiled(Net n, const
         __syncthreads();
         const uint32_t item = s_item;
         if (item >= n_items) break;
-        const uint32_t code = __ldg(items + item);
-        const TileDev T = tiles[code >> 8];
-        const uint32_t part = code & 0xffu;
-        const uint32_t cnt = deliver ? n.icount[(size_t)(ts & (n.cr - 1)) * n.n_inst + T.inst] : 0u;
-        if (cnt == 0) {  // nothing arrives: the update already cleared these accumulators
+        const uint32_t code = sp.items[item];
+        const uint32_t k = code >> 8, part = code & 0xffu;
+        const uint32_t P = k < n_tiles ? sp.parts[k] : 0u;
+        if (part >= P) {  // not produced by a correct plan: report, touch nothing
+            if (threadIdx.x == 0) atomicOr(&n.ctl->err, kErrPlan);
             __syncthreads();
             continue;
         }
+        const TileDev T = tiles[k];
+        const uint32_t cnt = n.icount[(size_t)(ts & (n.cr - 1)) * n.n_inst + T.inst];
         const uint32_t pbase = __ldg(&n.inst[T.inst].pbase);
         const uint32_t* q = n.q + (size_t)(ts % n.D) * n.Np + pbase;
-        const uint32_t nsplit = T.ntiles - 1;
-        const uint32_t* sp = split + T.split;
-        const uint32_t s_beg = (uint32_t)((unsigned long long)cnt * part / T.nparts);
-        const uint32_t s_end = (uint32_t)((unsigned long long)cnt * (part + 1) / T.nparts);
-        // one spike per warp; the next spike's row record is fetched while
-        // the current row is delivered
-        uint32_t s = s_beg + warp;
-        uint32_t j = 0;
-        uint4 r = make_uint4(0, 0, 0, 0);
-        if (s < s_end) {
-            j = q[s];
-            r = __ldg(n.rinfo + j);
-        }
-        while (s < s_end) {
-            const uint32_t s_next = s + nwarps;
-            uint32_t j_next = 0;
-            uint4 r_next = make_uint4(0, 0, 0, 0);
-            if (s_next < s_end) {
-                j_next = q[s_next];
-                r_next = __ldg(n.rinfo + j_next);
-            }
-            uint64_t sb = ((unsigned long long)r.y << 32) | r.x;
-            uint64_t se = sb + r.z;
-            if (nsplit) {
-                const uint32_t* sj = sp + (size_t)(j - pbase) * nsplit;
-                const uint64_t beg = sb;
-                if (T.tau > 0) sb = beg + __ldg(sj + T.tau - 1);
-                if (T.tau < nsplit) se = beg + __ldg(sj + T.tau);
-            }
-            const uint32_t shift = r.w & 31u;
-            int32_t* a = acc_s + ((CH == 2 && (r.w & 0x80u)) ? T.len : 0u);
-            ev += se - sb;
-            // edges [a4, b4) are read 4 at a time (16-byte target, 8- or 16-byte
-            // weight loads); the unaligned head and tail go one edge per lane
-            const uint64_t up4 = (sb + 3) & ~3ull, dn4 = se & ~3ull;
-            const uint64_t a4 = up4 < se ? up4 : se;
-            const uint64_t b4 = dn4 > a4 ? dn4 : a4;
-            {
-                uint64_t e = ~0ull;
-                if (lane < a4 - sb)
-                    e = sb + lane;
-                else if (lane >= 4 && lane - 4 < se - b4)
-                    e = b4 + (lane - 4);
-                if (e != ~0ull) {
-                    const uint32_t x = __ldg(n.tgt + e) - T.lo;
-                    const int32_t w = weight_at<W16>(n, e, shift);
-                    if (x < T.len)
-                        atomicAdd(a + x, w);
-                    else
-                        bad = true;
-                }
-            }
-            for (uint64_t base = a4; base < b4; base += 128 * kVec) {
-                uint4 tv[kVec];
-                int32_t wv[kVec][4];
-#pragma unroll
-                for (int u = 0; u < kVec; ++u) {
-                    const uint64_t e = base + 128 * u + 4 * lane;
-                    tv[u] = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
-                    wv[u][0] = wv[u][1] = wv[u][2] = wv[u][3] = 0;
-                    if (e < b4) {
-                        tv[u] = __ldg(reinterpret_cast<const uint4*>(n.tgt + e));
-                        if (W16) {
-                            const uint2 h = __ldg(reinterpret_cast<const uint2*>(n.w16 + e));
-                            wv[u][0] = (int32_t)(int16_t)(h.x & 0xffffu) << shift;
-                            wv[u][1] = (int32_t)(int16_t)(h.x >> 16) << shift;
-                            wv[u][2] = (int32_t)(int16_t)(h.y & 0xffffu) << shift;
-                            wv[u][3] = (int32_t)(int16_t)(h.y >> 16) << shift;
-                        } else {
-                            const float4 f = __ldg(reinterpret_cast<const float4*>(n.w32 + e));
-                            wv[u][0] = __float2int_rz(f.x);
-                            wv[u][1] = __float2int_rz(f.y);
-                            wv[u][2] = __float2int_rz(f.z);
-                            wv[u][3] = __float2int_rz(f.w);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < kVec; ++u) {
-                    if (base + 128 * u + 4 * lane >= b4) continue;
-                    const uint32_t xs[4] = {tv[u].x - T.lo, tv[u].y - T.lo, tv[u].z - T.lo, tv[u].w - T.lo};
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        if (xs[k] < T.len)
-                            atomicAdd(a + xs[k], wv[u][k]);
-                        else
-                            bad = true;
-                    }
-                }
-            }
-            s = s_next;
-            j = j_next;
-            r = r_next;
+        deliver_part<W16, CH>(n, T, q, pbase, split + T.split, acc_s,
+                              (uint32_t)((unsigned long long)cnt * part / P),
+                              (uint32_t)((unsigned long long)cnt * (part + 1) / P), pol, ev, bad);
+        // the tile's pending input for the next update, or this part's share
+        // of it: the shared-memory adds are made visible to the copy engine,
+        // which reads them out before they are cleared
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            bulk_out(n.acc0 + T.lo, acc_s, T.len * 4u, P > 1);
+            if (CH == 2) bulk_out(n.acc1 + T.lo, acc_s + T.len, T.len * 4u, P > 1);
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
         }
         __syncthreads();
-        // the tile's pending input for the next update, or this part's share of it
-        int4* g0;
-        int4* g1 = nullptr;
-        if (T.nparts == 1) {
-            g0 = reinterpret_cast<int4*>(n.acc0 + T.lo);
-            if (CH == 2) g1 = reinterpret_cast<int4*>(n.acc1 + T.lo);
-        } else {
-            int32_t* base = partial + T.part_base + (size_t)part * CH * T.len;
-            g0 = reinterpret_cast<int4*>(base);
-            if (CH == 2) g1 = reinterpret_cast<int4*>(base + T.len);
-        }
-        int4* s0 = reinterpret_cast<int4*>(acc_s);
-        for (uint32_t i = threadIdx.x; i < T.len / 4; i += blockDim.x) {
-            g0[i] = s0[i];
-            s0[i] = make_int4(0, 0, 0, 0);
-        }
-        if (CH == 2) {
-            int4* s1 = reinterpret_cast<int4*>(acc_s + T.len);
-            for (uint32_t i = threadIdx.x; i < T.len / 4; i += blockDim.x) {
-                g1[i] = s1[i];
-                s1[i] = make_int4(0, 0, 0, 0);
-            }
-        }
-        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < CH * T.len / 4; i += blockDim.x)
+            reinterpret_cast<int4*>(acc_s)[i] = make_int4(0, 0, 0, 0);
     }
+    if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     if (lane == 0 && ev) atomicAdd(&n.ctl->events, ev);
     if (bad) atomicOr(&n.ctl->err, kErrBadTarget);
 }
 
-// Adds the parts of the multi-part tiles into the global accumulators, one
-// chunk of kMergeChunk neurons per block, one int4 per thread, eight parts'
-// loads in flight per thread.
+// Adds up the partials of chunk of a multi-part tile: one int4 per thread,
+// eight partials' loads in flight.
 template <int CH>
-__global__ void __launch_bounds__(kMergeChunk / 4) k_merge_parts(Net n, const TileDev* __restrict__ tiles,
-                                                                const MergeDev* __restrict__ merges,
-                                                                const int32_t* __restrict__ partial)
+__device__ __forceinline__ void merge_chunk(const Net& n, const TileDev& T, const MergeDev& M, const int32_t* base,
+                                            uint32_t nparts)
 {
-    const MergeDev M = merges[blockIdx.x];
-    const TileDev T = tiles[M.tile];
-    const unsigned long long t = n.ctl->t + n.k;
-    if (t + 1 < n.d) return;
-    const unsigned long long ts = t + 1 - n.d;
-    if (n.icount[(size_t)(ts & (n.cr - 1)) * n.n_inst + T.inst] == 0) return;  // no part wrote anything
     const uint32_t i = M.off + threadIdx.x * 4;
     if (i >= M.off + M.len) return;
-    const int32_t* base = partial + T.part_base;
     for (uint32_t c = 0; c < CH; ++c) {
         const int32_t* src = base + (size_t)c * T.len + i;
         const size_t stride = (size_t)CH * T.len;  // between parts
         int4 s = make_int4(0, 0, 0, 0);
         uint32_t p = 0;
-        for (; p + 8 <= T.nparts; p += 8) {
+        for (; p + 8 <= nparts; p += 8) {
             int4 v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) v[u] = __ldg(reinterpret_cast<const int4*>(src + (p + u) * stride));
@@ -268,7 +515,7 @@ __global__ void __launch_bounds__(kMergeChunk / 4) k_merge_parts(Net n, const Ti
                 s.w += v[u].w;
             }
         }
-        for (; p < T.nparts; ++p) {
+        for (; p < nparts; ++p) {
             const int4 v = __ldg(reinterpret_cast<const int4*>(src + p * stride));
             s.x += v.x;
             s.y += v.y;
@@ -277,6 +524,21 @@ __global__ void __launch_bounds__(kMergeChunk / 4) k_merge_parts(Net n, const Ti
         }
         *reinterpret_cast<int4*>((c ? n.acc1 : n.acc0) + T.lo + i) = s;
     }
+}
+
+// Static plan: one chunk per block.
+template <int CH>
+__global__ void __launch_bounds__(kMergeChunk / 4) k_merge_parts(Net n, const TileDev* __restrict__ tiles,
+                                                                const MergeDev* __restrict__ merges,
+                                                                const int32_t* __restrict__ partial)
+{
+    const MergeDev M = merges[blockIdx.x];
+    const TileDev T = tiles[M.tile];
+    const unsigned long long t = n.ctl->t + n.k;
+    if (t + 1 < n.d) return;
+    const unsigned long long ts = t + 1 - n.d;
+    if (n.icount[(size_t)(ts & (n.cr - 1)) * n.n_inst + T.inst] == 0) return;  // no part wrote anything
+    merge_chunk<CH>(n, T, M, partial + T.part_base, T.nparts);
 }
 
 // Split table of one multi-tile instance: for local row l and inner boundary
@@ -319,23 +581,30 @@ inline cudaError_t tiled_set_smem(size_t smem)
 inline void tiled_free(TiledPlan& P, const std::function<void(void*)>& release)
 {
     release(P.tiles);
-    release(P.items);
     release(P.split);
     release(P.partial);
+    release(P.items);
     release(P.merges);
+    release(P.step.hdr);
+    release(P.step.items);
+    release(P.step.parts);
     P = TiledPlan{};
 }
 
-// Build the plan.  work[b] is the expected delivered edges of instance b per
-// step (any positive scale; null: proportional to its synapses).  An
-// instance is cut by target into tiles of at most max_len padded ids (the
-// shared-memory limit); a tile is split by spikes into parts so that no work
-// item carries more than about total / (items_per_cta * CTAs).  Needs sorted
-// rows when an instance has several tiles.
+// Build the tiles and, for the bulk-copy receive (dynamic false), its static
+// plan.  An instance is cut by target into tiles of at most max_len padded
+// ids (the shared-memory limit).  Static plan: work[b] is the expected
+// delivered edges of instance b per step (any positive scale; null:
+// proportional to its synapses); with target = total / (1.25 CTAs) a tile of
+// expected work w gets ceil(w / target) spike parts.  Per-step plan (dynamic
+// true): the buffers k_plan fills, sized for the most it can write --
+// sum_k P_k <= kItemsPerCta CTAs + tiles, since P_k <= w_k / target + 1, and
+// likewise for the partial words.  Needs sorted rows when an instance has
+// several tiles.
 inline snn_status tiled_plan(TiledPlan& P, const Net& n, const snn_params* params, const uint32_t* pbase,
                              uint32_t n_inst, int channels, uint32_t max_len, const double* work,
                              const uint64_t* inst_edges, int sms, const std::function<void*(size_t)>& alloc,
-                             const std::function<void(void*)>& release, cudaStream_t s)
+                             const std::function<void(void*)>& release, cudaStream_t s, bool dynamic)
 {
     max_len = std::max<uint32_t>(256, max_len / 256 * 256);
     std::vector<double> wk(n_inst, 0.0);
@@ -365,6 +634,8 @@ inline snn_status tiled_plan(TiledPlan& P, const Net& n, const snn_params* param
             d.tau = tau;
             d.ntiles = T;
             d.nparts = 1;
+            // mean segment of a row in this tile, plus the fixed cost of a spike
+            d.seg = (params[b].n ? (float)((double)inst_edges[b] / params[b].n * d.len / npad) : 0.0f) + kSpikeCost;
             d.split = split_base[b];
             tiles.push_back(d);
             tile_work.push_back(wk[b] * d.len / npad);
@@ -376,7 +647,8 @@ inline snn_status tiled_plan(TiledPlan& P, const Net& n, const snn_params* param
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t smem = (size_t)longest * channels * 4;
-    if (tiles.empty() || smem > (size_t)optin) return SNN_E_ARG;
+    if (tiles.empty() || smem > (size_t)optin || tiles.size() >= (1u << 24)) return SNN_E_ARG;
+    if (dynamic && tiles.size() > kPlanMaxTiles) return SNN_E_ARG;
     if (tiled_set_smem(smem) != cudaSuccess) return SNN_E_CUDA;
     int ctas = 0;
     cudaError_t oe = channels == 2
@@ -387,53 +659,69 @@ inline snn_status tiled_plan(TiledPlan& P, const Net& n, const snn_params* param
         ctas = 1;
     }
     const uint32_t n_ctas = (uint32_t)(sms * ctas);
-    const double items_per_cta = 1.25;  // measured: 1-1.5 best on the batched sweep
-    const double target = total > 0 ? total / (items_per_cta * n_ctas) : 1.0;
-    // parts, partial buffer and the merge chunks
-    struct Item {
-        uint32_t code;
-        double w;
-    };
-    std::vector<Item> items;
-    std::vector<MergeDev> merges;
-    unsigned long long part_total = 0;
-    for (uint32_t k = 0; k < tiles.size(); ++k) {
-        TileDev& d = tiles[k];
-        uint32_t parts = total > 0 ? (uint32_t)std::ceil(tile_work[k] / target) : 1u;
-        parts = std::max<uint32_t>(1, std::min<uint32_t>({parts, kMaxParts, n_ctas}));
-        d.nparts = parts;
-        if (parts > 1) {
-            d.part_base = part_total;
-            part_total += (unsigned long long)parts * channels * d.len;
-            for (uint32_t off = 0; off < d.len; off += kMergeChunk)
-                merges.push_back(MergeDev{k, off, std::min(kMergeChunk, d.len - off), 0});
-        }
-        for (uint32_t p = 0; p < parts; ++p) items.push_back(Item{(k << 8) | p, tile_work[k] / parts});
-    }
-    if (tiles.size() >= (1u << 24)) return SNN_E_ARG;
-    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.w > b.w; });
-    std::vector<uint32_t> codes(items.size());
-    for (size_t i = 0; i < items.size(); ++i) codes[i] = items[i].code;
+    const uint32_t cap = std::min<uint32_t>(kMaxParts, n_ctas);
 
     TiledPlan Q;
+    Q.dynamic = dynamic;
     Q.n_tiles = (uint32_t)tiles.size();
-    Q.n_items = (uint32_t)codes.size();
-    Q.n_merges = (uint32_t)merges.size();
     Q.max_len = longest;
     Q.channels = channels;
     Q.threads = kTiledThreads;
     Q.smem = smem;
-    Q.grid = std::min<uint32_t>(Q.n_items, n_ctas);
+    Q.cap = cap;
+    std::vector<uint32_t> codes;
+    std::vector<MergeDev> merges;
+    unsigned long long part_total = 0;
+    if (!dynamic) {  // static parts, heaviest first
+        const double target = total > 0 ? total / (1.25 * n_ctas) : 1.0;
+        struct Item {
+            uint32_t code;
+            double w;
+        };
+        std::vector<Item> items;
+        for (uint32_t k = 0; k < tiles.size(); ++k) {
+            TileDev& d = tiles[k];
+            uint32_t parts = total > 0 ? (uint32_t)std::ceil(tile_work[k] / target) : 1u;
+            parts = std::max<uint32_t>(1, std::min<uint32_t>(parts, cap));
+            d.nparts = parts;
+            if (parts > 1) {
+                d.part_base = part_total;
+                part_total += (unsigned long long)parts * channels * d.len;
+                for (uint32_t off = 0; off < d.len; off += kMergeChunk)
+                    merges.push_back(MergeDev{k, off, std::min(kMergeChunk, d.len - off), 0});
+            }
+            for (uint32_t p = 0; p < parts; ++p) items.push_back(Item{(k << 8) | p, tile_work[k] / parts});
+        }
+        std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.w > b.w; });
+        for (const Item& it : items) codes.push_back(it.code);
+        Q.n_items = (uint32_t)codes.size();
+        Q.n_merges = (uint32_t)merges.size();
+        Q.grid = std::min<uint32_t>(Q.n_items, n_ctas);
+        Q.items = static_cast<uint32_t*>(alloc(codes.size() * 4));
+        Q.merges = static_cast<MergeDev*>(alloc(std::max<size_t>(merges.size(), 1) * sizeof(MergeDev)));
+    } else {
+        // sum_k P_k <= sum_k (w_k / target + 1) = kItemsPerCta CTAs + tiles
+        Q.items_cap = (uint32_t)std::ceil(kItemsPerCta * n_ctas) + 16 + (uint32_t)tiles.size();
+        Q.grid = n_ctas;
+        Q.step.hdr = static_cast<uint32_t*>(alloc(4 * sizeof(uint32_t)));
+        Q.step.items = static_cast<uint32_t*>(alloc((size_t)Q.items_cap * 4));
+        Q.step.parts = static_cast<uint32_t*>(alloc(tiles.size() * 4));
+        uint32_t n_pad = 1;
+        while (n_pad < tiles.size()) n_pad <<= 1;
+        if (cudaFuncSetAttribute(k_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan_smem(n_pad)) !=
+            cudaSuccess)
+            return SNN_E_CUDA;
+    }
     Q.tiles = static_cast<TileDev*>(alloc(tiles.size() * sizeof(TileDev)));
-    Q.items = static_cast<uint32_t*>(alloc(codes.size() * 4));
     Q.split = static_cast<uint32_t*>(alloc(std::max<unsigned long long>(split_total, 1) * 4));
     Q.partial = static_cast<int32_t*>(alloc(std::max<unsigned long long>(part_total, 4) * 4));
-    Q.merges = static_cast<MergeDev*>(alloc(std::max<size_t>(merges.size(), 1) * sizeof(MergeDev)));
     uint32_t* dbounds = static_cast<uint32_t*>(alloc(65536 * 4));
-    snn_status st = (Q.tiles && Q.items && Q.split && Q.partial && Q.merges && dbounds) ? SNN_OK : SNN_E_NOMEM;
+    const bool have = dynamic ? (Q.step.hdr && Q.step.items && Q.step.parts) : (Q.items && Q.merges);
+    snn_status st = (have && Q.tiles && Q.split && Q.partial && dbounds) ? SNN_OK : SNN_E_NOMEM;
     if (st == SNN_OK &&
         (cudaMemcpyAsync(Q.tiles, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-         cudaMemcpyAsync(Q.items, codes.data(), codes.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+         (dynamic && cudaMemsetAsync(Q.step.hdr, 0, 4 * sizeof(uint32_t), s) != cudaSuccess) ||
+         (codes.size() && cudaMemcpyAsync(Q.items, codes.data(), codes.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) ||
          (merges.size() && cudaMemcpyAsync(Q.merges, merges.data(), merges.size() * sizeof(MergeDev),
                                            cudaMemcpyHostToDevice, s) != cudaSuccess)))
         st = SNN_E_CUDA;
@@ -463,20 +751,28 @@ inline snn_status tiled_plan(TiledPlan& P, const Net& n, const snn_params* param
     return SNN_OK;
 }
 
+// The per-step plan of one step.
+inline cudaError_t enqueue_tiled_plan(const TiledPlan& P, const Net& n, cudaStream_t s)
+{
+    uint32_t n_pad = 1;
+    while (n_pad < P.n_tiles) n_pad <<= 1;
+    k_plan<<<1, kPlanThreads, plan_smem(n_pad), s>>>(n, P.tiles, P.n_tiles, P.step, P.grid, P.cap, P.items_cap);
+    return cudaGetLastError();
+}
+
+// The receive of one step under its plan.
 inline cudaError_t enqueue_tiled_receive(const TiledPlan& P, const Net& n, bool w16, cudaStream_t s)
 {
     if (P.channels == 2) {
         if (w16)
-            k_receive_tiled<true, 2><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
+            k_receive_tiled<true, 2><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.n_tiles, P.step, P.split, P.max_len);
         else
-            k_receive_tiled<false, 2><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
-        if (P.n_merges) k_merge_parts<2><<<P.n_merges, kMergeChunk / 4, 0, s>>>(n, P.tiles, P.merges, P.partial);
+            k_receive_tiled<false, 2><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.n_tiles, P.step, P.split, P.max_len);
     } else {
         if (w16)
-            k_receive_tiled<true, 1><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
+            k_receive_tiled<true, 1><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.n_tiles, P.step, P.split, P.max_len);
         else
-            k_receive_tiled<false, 1><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
-        if (P.n_merges) k_merge_parts<1><<<P.n_merges, kMergeChunk / 4, 0, s>>>(n, P.tiles, P.merges, P.partial);
+            k_receive_tiled<false, 1><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.n_tiles, P.step, P.split, P.max_len);
     }
     return cudaGetLastError();
 }

@@ -304,6 +304,20 @@ def test_retuned_tiles_keep_parity(gpu, tune_steps, receive):
     assert_parity(g, o, prob)
 
 
+@pytest.mark.parametrize("n_inst,delay", [(1, 1), (2, 2), (3, 1), (33, 2), (1100, 2)])
+def test_per_step_plan_tile_counts(gpu, n_inst, delay):
+    """The tiled receive's per-step plan over 1 to 1,100 tiles (its rank sort
+    up to 1,024 tiles, its sorting network above), with the plan beside the
+    update (delay 2) and before the receive (delay 1)."""
+    insts = [si.brunel_instance(200 + 37 * (b % 7), k=20 + (b % 5), nu_ratio=3.0, graph_seed=b + 1)
+             for b in range(n_inst)]
+    prob = si.problem(si.BRUNEL, insts, delay=delay, n_steps=80, seed=7)
+    o = oracle.run(prob)
+    g = run_gpu(gpu, prob, w16=True, receive="tiled")
+    assert len(o["ids"]) > 10 * n_inst
+    assert_parity(g, o, prob)
+
+
 @pytest.mark.parametrize("receive", ["tiled", "bulk"])
 @pytest.mark.parametrize("model", [si.BRUNEL, si.VOGELS])
 def test_instances_larger_than_one_tile(gpu, model, receive):
