@@ -342,11 +342,11 @@ snn_status init_state(snn_ctx* c)
 // instance b per step (null: proportional to its synapses).
 snn_status plan_tiles(snn_ctx* c, const double* work)
 {
-    // accumulators of one tile: 224 KB (tiled), or what the copy ring leaves
-    // of the 227 KB (bulk); one CTA per SM either way
+    // accumulators of one tile: 112 KB (tiled, two CTAs per SM), or what the
+    // copy ring leaves of the 227 KB (bulk, one CTA per SM)
     const uint32_t ch = c->vogels ? 2u : 1u;
     const uint32_t bulk_len = (uint32_t)((227u * 1024u - 1024u - kBulkSlots * bulk_slot_bytes(c->w16)) / 4u / 256u * 256u);
-    const uint32_t max_len = (c->use_bulk ? bulk_len : 57344u) / ch / 256u * 256u;
+    const uint32_t max_len = (c->use_bulk ? bulk_len : kTiledMaxWords) / ch / 256u * 256u;
     snn_status st = tiled_plan(c->tiled, c->net, c->params.data(), c->pbase.data(), c->cfg.n_inst, (int)ch, max_len,
                                work, c->inst_edges.data(), sm_count(), [c](size_t b) { return dev_alloc(c, b); },
                                [c](void* p) { dev_free(c, p); }, c->stream, !c->use_bulk);

@@ -53,7 +53,7 @@ struct TileDev {
     uint32_t lo, len;               // padded id range [lo, lo + len); len is a multiple of 256
     uint32_t tau, ntiles;           // tile index inside the instance, tiles of the instance
     uint32_t nparts;                // static plan: spike parts of this tile
-    uint32_t pad;
+    uint32_t lpieces;               // per-step plan: a row segment is cut into 2^lpieces pieces
     float seg;                      // per-step plan: expected work per arriving spike (edges)
     unsigned long long split;       // base of the instance's split table: n_b rows x (ntiles-1) uint32
     unsigned long long part_base;   // static plan: base of the partials (nparts x CH x len int32) if nparts > 1
@@ -91,7 +91,12 @@ struct TiledPlan {
     size_t smem = 0;
 };
 
-constexpr int kTiledThreads = 1024;
+// Two CTAs of 16 warps per SM, each with up to 112 KB of accumulators: while
+// one waits at a barrier (its slowest warp, its copy-out), the other keeps
+// the SM's loads in flight.
+constexpr int kTiledThreads = 512;
+constexpr int kTiledCtasPerSm = 2;
+constexpr uint32_t kTiledMaxWords = 28672;  // int32 accumulators of one CTA (112 KB)
 constexpr int kVec = 4;            // 4-edge vectors in flight per lane
 constexpr uint32_t kMaxParts = 255;
 constexpr uint32_t kMergeChunk = 4096;
@@ -100,6 +105,8 @@ constexpr uint32_t kPlanMaxTiles = 4096;
 constexpr uint32_t kRankSortMax = 1024;  // up to this many tiles the plan sorts by rank, above by a bitonic network
 constexpr float kItemsPerCta = 1.5f;     // per-step plan: items per CTA at the target size
 constexpr float kSpikeCost = 8.0f;     // fixed work of one arriving spike, in edges
+constexpr uint32_t kPieceEdges = 512;  // edges of one vector pass of a warp (32 lanes x kVec x 4)
+constexpr uint32_t kMaxLogPieces = 3;
 
 // Edges are read once per step and never again before the rest of the
 // (larger than L2) graph has streamed by, so their loads carry an L2
@@ -231,44 +238,53 @@ __device__ __forceinline__ void add_segment(const Net& n, int32_t* a, uint64_t s
 }
 
 // Delivers the spikes [s_beg, s_end) of the instance's queue q (local ids
-// from pbase) to tile T: one spike per warp, warps strided; the next spike's
-// row record is fetched while the current row is delivered.
+// from pbase) to tile T.  The work is cut into units, piece u % K of the row
+// segment of spike s_beg + u / K (K = 2^T.lpieces), strided over the warps;
+// the row record (and split offsets) of a warp's next unit and the spike of
+// the unit after it are fetched while the current unit is delivered, so no
+// load waits on another.
 template <bool W16, int CH>
 __device__ __forceinline__ void deliver_part(const Net& n, const TileDev& T, const uint32_t* q, uint32_t pbase,
                                              const uint32_t* sp, int32_t* acc_s, uint32_t s_beg, uint32_t s_end,
                                              unsigned long long pol, unsigned long long& ev, bool& bad)
 {
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const uint32_t nsplit = T.ntiles - 1;
-    uint32_t s = s_beg + warp;
-    uint32_t j = 0;
-    uint4 r = make_uint4(0, 0, 0, 0);
-    if (s < s_end) {
-        j = q[s];
+    const uint32_t nsplit = T.ntiles - 1, lk = T.lpieces;
+    const uint32_t u_end = (s_end - s_beg) << lk;
+    // segment of the row of spike j inside the tile, relative to the row's start
+    auto fetch = [&](uint32_t j, uint4& r, uint32_t& ylo, uint32_t& yhi) {
         r = __ldg(n.rinfo + j);
-    }
-    while (s < s_end) {
-        const uint32_t s_next = s + nwarps;
-        uint32_t j_next = 0;
-        uint4 r_next = make_uint4(0, 0, 0, 0);
-        if (s_next < s_end) {
-            j_next = q[s_next];
-            r_next = __ldg(n.rinfo + j_next);
-        }
-        uint64_t sb = ((unsigned long long)r.y << 32) | r.x;
-        uint64_t se = sb + r.z;
+        ylo = 0;
+        yhi = 0xffffffffu;  // the row's end
         if (nsplit) {
             const uint32_t* sj = sp + (size_t)(j - pbase) * nsplit;
-            const uint64_t beg = sb;
-            if (T.tau > 0) sb = beg + __ldg(sj + T.tau - 1);
-            if (T.tau < nsplit) se = beg + __ldg(sj + T.tau);
+            if (T.tau > 0) ylo = __ldg(sj + T.tau - 1);
+            if (T.tau < nsplit) yhi = __ldg(sj + T.tau);
         }
-        ev += se - sb;
-        int32_t* a = acc_s + ((CH == 2 && (r.w & 0x80u)) ? T.len : 0u);
-        add_segment<W16>(n, a, sb, se, r.w & 31u, T.lo, T.len, lane, pol, bad);
-        s = s_next;
-        j = j_next;
-        r = r_next;
+    };
+    uint32_t u = warp;
+    uint4 r0 = make_uint4(0, 0, 0, 0);
+    uint32_t ylo0 = 0, yhi0 = 0, jn = 0;
+    if (u < u_end) fetch(q[s_beg + (u >> lk)], r0, ylo0, yhi0);
+    if (u + nwarps < u_end) jn = q[s_beg + ((u + nwarps) >> lk)];
+    while (u < u_end) {
+        const uint32_t u1 = u + nwarps, u2 = u1 + nwarps;
+        uint4 r1 = make_uint4(0, 0, 0, 0);
+        uint32_t ylo1 = 0, yhi1 = 0, jn2 = 0;
+        if (u1 < u_end) fetch(jn, r1, ylo1, yhi1);
+        if (u2 < u_end) jn2 = q[s_beg + (u2 >> lk)];
+        const uint64_t beg = ((unsigned long long)r0.y << 32) | r0.x;
+        const uint64_t sb = beg + ylo0, se = beg + (yhi0 == 0xffffffffu ? r0.z : yhi0);
+        const uint64_t len = se - sb, c = u & ((1u << lk) - 1u);
+        const uint64_t pb = sb + ((len * c) >> lk), pe = sb + ((len * (c + 1)) >> lk);
+        ev += pe - pb;
+        int32_t* a = acc_s + ((CH == 2 && (r0.w & 0x80u)) ? T.len : 0u);
+        add_segment<W16>(n, a, pb, pe, r0.w & 31u, T.lo, T.len, lane, pol, bad);
+        u = u1;
+        r0 = r1;
+        ylo0 = ylo1;
+        yhi0 = yhi1;
+        jn = jn2;
     }
 }
 
@@ -432,7 +448,7 @@ __device__ __forceinline__ void bulk_out(int32_t* g, const int32_t* s, uint32_t 
 
 // The receive of one step under the per-step plan.
 template <bool W16, int CH>
-__global__ void __launch_bounds__(kTiledThreads, 1) k_receive_tiled(Net n, const TileDev* __restrict__ tiles,
+__global__ void __launch_bounds__(kTiledThreads, kTiledCtasPerSm) k_receive_tiled(Net n, const TileDev* __restrict__ tiles,
                                                                     uint32_t n_tiles, StepPlan sp,
                                                                     const uint32_t* __restrict__ split, uint32_t max_len)
 {
@@ -634,8 +650,12 @@ inline snn_status tiled_plan(TiledPlan& P, const Net& n, const snn_params* param
             d.tau = tau;
             d.ntiles = T;
             d.nparts = 1;
-            // mean segment of a row in this tile, plus the fixed cost of a spike
-            d.seg = (params[b].n ? (float)((double)inst_edges[b] / params[b].n * d.len / npad) : 0.0f) + kSpikeCost;
+            // mean segment of a row in this tile, plus the fixed cost of a spike;
+            // pieces of about one vector pass each
+            const double mseg = params[b].n ? (double)inst_edges[b] / params[b].n * d.len / npad : 0.0;
+            d.seg = (float)mseg + kSpikeCost;
+            d.lpieces = 0;
+            while (d.lpieces < kMaxLogPieces && mseg >= (double)(2u << d.lpieces) * kPieceEdges * 0.75) ++d.lpieces;
             d.split = split_base[b];
             tiles.push_back(d);
             tile_work.push_back(wk[b] * d.len / npad);
