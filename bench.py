@@ -31,13 +31,14 @@ import snn_inputs as si  # noqa: E402
 
 DT_MS = 0.1
 METRIC = "synaptic events/s and realtime factor on 1 B300, batched+int16 vs plain FP32"
-# algorithmic bytes (what the method must move): per delivered event a
-# 4-byte target and a 2-byte (int16) or 4-byte (binary32) weight; per
+# algorithmic bytes (what the method must move): per delivered event the
+# edge as the receive stores it -- a 4-byte target and a 2-byte (int16) or
+# 4-byte (binary32) weight, or one 4-byte packed edge (16-bit target offset
+# in its instance, int16 code; the library reports which); per
 # delivered spike its two row offsets (16 B) and its queue entry (4 B); per
 # emitted spike the queue write (4 B) and the log entry (8 B); per neuron and
 # step the state the update reads and writes (Brunel: V 4+4, refractory 1+1,
 # input 4 read + 4 cleared = 18 B; Vogels 44 B; STDP traces +16 B).
-B_EVENT_W16, B_EVENT_F32 = 6, 8
 B_SPIKE_DELIVERED, B_SPIKE_EMITTED = 20, 12
 B_NEURON = {si.BRUNEL: 18, si.VOGELS: 44}
 B_NEURON_STDP = 16
@@ -197,9 +198,9 @@ def delivered_spikes(net, prob, t0: int, t1: int) -> int:
     return len(steps)
 
 
-def step_bytes(prob, w16: bool, events: int, delivered: int, emitted: int, steps: int) -> float:
+def step_bytes(prob, edge_bytes: int, events: int, delivered: int, emitted: int, steps: int) -> float:
     per_neuron = B_NEURON[prob.model] + (B_NEURON_STDP if prob.stdp else 0)
-    return (events * (B_EVENT_W16 if w16 else B_EVENT_F32) + delivered * B_SPIKE_DELIVERED +
+    return (events * edge_bytes + delivered * B_SPIKE_DELIVERED +
             emitted * B_SPIKE_EMITTED + per_neuron * prob.n * steps)
 
 
@@ -279,9 +280,9 @@ def run_ours(args, rank, world, dist):
     ev_total = sum_over_ranks(ev_main)
     value = ev_total / t_max
     recv_ms = phases["receive"] / n_prof
-    recv_bytes = (ev_p * B_EVENT_W16 + deliv_p * B_SPIKE_DELIVERED) / n_prof
+    recv_bytes = (ev_p * info["edge_bytes"] + deliv_p * B_SPIKE_DELIVERED) / n_prof
     achieved = recv_bytes / (recv_ms * 1e-3) / 1e9
-    step_b = step_bytes(prob, True, ev_main, deliv_main, sp_main, args.steps)
+    step_b = step_bytes(prob, info["edge_bytes"], ev_main, deliv_main, sp_main, args.steps)
     step_frac = (step_b / (hbm * 1e9)) / t_main
 
     out = {"metric": METRIC, "value": value, "unit": "synaptic events/s", "n_gpus": world, "steps": args.steps,
@@ -291,6 +292,7 @@ def run_ours(args, rank, world, dist):
            "config": {"workload": args.workload, "networks": len(prob.instances), "neurons": prob.n,
                       "synapses": prob.n_edges, "delay_steps": prob.delay, "dt_ms": DT_MS,
                       "receive": recv_kind, "tiles": info["n_tiles"], "weights": "int16 x 2^shift(row)",
+                      "edge_bytes": info["edge_bytes"],
                       "l2": "inputs larger than L2 (edge arrays %.1f GB >> 126 MB)" % (prob.n_edges * 6 / 1e9),
                       "parallelism": f"replicas x{world} (independent networks, no collective)",
                       "graph_gen_s": round(t_gen, 1), "device_bytes": mem},

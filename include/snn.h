@@ -65,6 +65,9 @@ typedef enum {
 #define SNN_F_STDP 1u  /* pair STDP on exc -> exc synapses (Brunel only; "Brunel+") */
 #define SNN_F_W16 2u   /* weights stored as int16 codes x 2^shift(row); else binary32 */
 #define SNN_F_STATS 4u /* keep per-neuron spike counts and ISI moments for snn_stats */
+#define SNN_F_UNPACKED 8u /* tiled receive: read the u32 target and int16 code arrays even where the
+                             packed layout applies (SNN_F_W16, no STDP, every instance of at most
+                             65,536 neurons: one u32 per edge, target offset << 16 | code) */
 
 /* snn_config.receive */
 #define SNN_RECV_AUTO 0u   /* the library picks: tiled when the rows are sorted, else global */
@@ -244,6 +247,8 @@ typedef struct {
     uint32_t rows_sorted;  /* 1 if every row's targets ascend */
     uint64_t edges;        /* synapses loaded */
     uint64_t device_bytes; /* device memory held */
+    uint32_t edge_bytes;   /* bytes the receive reads per delivered edge: 4 (packed), 6 (int16 codes), 8 */
+    uint32_t reserved;
 } snn_info;
 snn_status snn_get_info(snn_ctx* ctx, snn_info* info);
 

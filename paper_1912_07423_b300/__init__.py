@@ -17,10 +17,10 @@ import numpy as np
 from .build import LIB, build as _build
 
 __all__ = ["Network", "SnnError", "load", "VOGELS", "BRUNEL", "RECV_AUTO", "RECV_GLOBAL", "RECV_TILED", "RECV_BULK",
-           "F_STDP", "F_W16", "F_STATS", "FIELDS"]
+           "F_STDP", "F_W16", "F_STATS", "F_UNPACKED", "FIELDS"]
 
 VOGELS, BRUNEL = 0, 1
-F_STDP, F_W16, F_STATS = 1, 2, 4
+F_STDP, F_W16, F_STATS, F_UNPACKED = 1, 2, 4, 8
 RECV_AUTO, RECV_GLOBAL, RECV_TILED, RECV_BULK = 0, 1, 2, 3
 FIELDS = {"V": 0, "ge": 1, "gi": 2, "r": 3, "x": 4, "y": 5, "acc0": 6, "acc1": 7, "w": 8}
 _FIELD_DTYPE = {"V": np.float32, "ge": np.float32, "gi": np.float32, "r": np.int32, "x": np.float32,
@@ -56,7 +56,8 @@ class Params(ctypes.Structure):
 
 class Info(ctypes.Structure):
     _fields_ = [("receive", ctypes.c_uint32), ("n_tiles", ctypes.c_uint32), ("n_padded", ctypes.c_uint32),
-                ("rows_sorted", ctypes.c_uint32), ("edges", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64)]
+                ("rows_sorted", ctypes.c_uint32), ("edges", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                ("edge_bytes", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(_vp, ctypes.c_size_t, _vp, _vp)
@@ -159,7 +160,7 @@ class Network:
 
     def __init__(self, problem, *, w16: bool = True, receive: int = RECV_AUTO, log_capacity: int | None = None,
                  stats: bool = False, steps_per_graph: int = 0, tune_steps: int = 0, device: str = "cuda:0",
-                 stream=None, build_graph: bool = True):
+                 stream=None, build_graph: bool = True, packed: bool = True):
         import torch
         if not torch.cuda.is_available():
             raise SnnError(-3, "no CUDA device: libsnn has no CPU fallback")
@@ -170,7 +171,8 @@ class Network:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.mem = _TorchMemory(self.device)
         self.dev = Device(self.mem.alloc_cb, self.mem.free_cb, None, self.stream.cuda_stream)
-        flags = (F_STDP if problem.stdp else 0) | (F_W16 if w16 else 0) | (F_STATS if stats else 0)
+        flags = (F_STDP if problem.stdp else 0) | (F_W16 if w16 else 0) | (F_STATS if stats else 0) | \
+            (0 if packed else F_UNPACKED)
         if log_capacity is None:
             log_capacity = max(1 << 16, int(problem.n) * 64)
         self.cfg = Config(problem.model, flags, problem.delay, len(problem.instances), problem.seed, log_capacity,
@@ -280,4 +282,4 @@ class Network:
         self._check(self.lib.snn_get_info(self.ctx, ctypes.byref(i)), "snn_get_info")
         return {"receive": {RECV_GLOBAL: "global", RECV_TILED: "tiled", RECV_BULK: "bulk"}.get(i.receive, "?"), "n_tiles": i.n_tiles,
                 "n_padded": i.n_padded, "rows_sorted": bool(i.rows_sorted), "edges": i.edges,
-                "device_bytes": i.device_bytes}
+                "device_bytes": i.device_bytes, "edge_bytes": i.edge_bytes}

@@ -69,6 +69,8 @@ struct snn_ctx {
     TiledPlan tiled{};
     bool use_tiled = false;
     bool use_bulk = false;             // tiled plan, bulk-copy kernel
+    bool packed = false;               // the tiled receive reads pk32
+    uint32_t* pk32 = nullptr;          // packed edges: (target - instance base) << 16 | int16 code
     uint32_t tune_count = 0;           // re-plans done (at most 2)
     uint64_t tune_next = 0;            // step of the next re-plan
     std::vector<unsigned long long> spk_seen;  // instance spike counts at the last re-plan
@@ -256,7 +258,7 @@ snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr, u
             CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_join, 0));
         else
             CUDA_TRY(c, enqueue_tiled_plan(c->tiled, n, s));
-        CUDA_TRY(c, enqueue_tiled_receive(c->tiled, n, c->w16, s));
+        CUDA_TRY(c, enqueue_tiled_receive(c->tiled, n, c->packed ? kWPacked : (c->w16 ? kW16 : kWF32), s));
         if (mid) cudaEventRecord(mid, s);  // no merge: the parts add into the accumulators
     } else {
         if (c->w16)
@@ -338,6 +340,25 @@ snn_status init_state(snn_ctx* c)
     return SNN_OK;
 }
 
+// The tiled receive can read packed edges: int16 codes, no plasticity, every
+// instance's offsets within 16 bits, and the caller did not opt out.
+bool packable(const snn_ctx* c)
+{
+    if (c->use_bulk || !c->w16 || c->stdp || (c->cfg.flags & SNN_F_UNPACKED)) return false;
+    for (uint32_t b = 0; b < c->cfg.n_inst; ++b)
+        if (c->pbase[b + 1] - c->pbase[b] > 65536u) return false;
+    return true;
+}
+
+// (Re)build the packed edges from the target and code arrays.
+snn_status pack_edges(snn_ctx* c)
+{
+    if (!c->packed) return SNN_OK;
+    k_pack_edges<<<(uint32_t)sm_count() * 16, 256, 0, c->stream>>>(c->net, c->Np, c->pk32);
+    CUDA_TRY(c, cudaGetLastError());
+    return SNN_OK;
+}
+
 // Cut the tiles of the tiled receive; work[b] = expected delivered edges of
 // instance b per step (null: proportional to its synapses).
 snn_status plan_tiles(snn_ctx* c, const double* work)
@@ -347,9 +368,10 @@ snn_status plan_tiles(snn_ctx* c, const double* work)
     const uint32_t ch = c->vogels ? 2u : 1u;
     const uint32_t bulk_len = (uint32_t)((227u * 1024u - 1024u - kBulkSlots * bulk_slot_bytes(c->w16)) / 4u / 256u * 256u);
     const uint32_t max_len = (c->use_bulk ? bulk_len : kTiledMaxWords) / ch / 256u * 256u;
+    const int wm = packable(c) ? kWPacked : (c->w16 ? kW16 : kWF32);
     snn_status st = tiled_plan(c->tiled, c->net, c->params.data(), c->pbase.data(), c->cfg.n_inst, (int)ch, max_len,
                                work, c->inst_edges.data(), sm_count(), [c](size_t b) { return dev_alloc(c, b); },
-                               [c](void* p) { dev_free(c, p); }, c->stream, !c->use_bulk);
+                               [c](void* p) { dev_free(c, p); }, c->stream, !c->use_bulk, 128u * vec_of(wm));
     if (st == SNN_OK && c->use_bulk) {
         int dev = 0, optin = 0;
         cudaGetDevice(&dev);
@@ -578,9 +600,12 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
     tiled_free(c->tiled, [c](void* p) { dev_free(c, p); });
     c->use_tiled = false;
     for (void* p : {(void*)c->roff, (void*)c->tgt, (void*)c->w16p, (void*)c->w32p, (void*)c->meta, (void*)c->coff,
-                    (void*)c->cedge, (void*)c->cpre, (void*)c->w_init, (void*)c->rinfo})
+                    (void*)c->cedge, (void*)c->cpre, (void*)c->w_init, (void*)c->rinfo, (void*)c->pk32})
         dev_free(c, p);
     c->rinfo = nullptr;
+    c->pk32 = nullptr;
+    c->packed = false;
+    c->net.pk = nullptr;
     c->roff = nullptr; c->tgt = nullptr; c->w16p = nullptr; c->w32p = nullptr; c->meta = nullptr;
     c->coff = nullptr; c->cedge = nullptr; c->cpre = nullptr; c->w_init = nullptr;
     c->graph_loaded = false;
@@ -738,6 +763,15 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
         snn_status st = c->rows_sorted ? plan_tiles(c, nullptr) : SNN_E_ARG;
         if (st == SNN_OK) {
             c->use_tiled = true;
+            if (packable(c)) {
+                c->pk32 = alloc_n<uint32_t>(c, E + 16);
+                if (!c->pk32) return fail(c, SNN_E_NOMEM, "packed edges");
+                CUDA_TRY(c, cudaMemsetAsync(c->pk32, 0, (E + 16) * 4, s));
+                c->packed = true;
+                n.pk = c->pk32;
+                st = pack_edges(c);
+                if (st != SNN_OK) return st;
+            }
         } else {
             tiled_free(c->tiled, [c](void* p) { dev_free(c, p); });
             if (c->cfg.receive == SNN_RECV_TILED || c->cfg.receive == SNN_RECV_BULK)
@@ -978,7 +1012,9 @@ snn_status snn_write_state(snn_ctx* c, snn_field f, const void* host)
         dev_free(c, tmp);
         if (e != cudaSuccess) return fail(c, SNN_E_CUDA, "weight upload: %s", cudaGetErrorString(e));
         if (err & kErrBadWeight) return fail(c, SNN_E_ARG, "a weight does not fit its row's int16 code and shift");
-        return SNN_OK;
+        snn_status st = pack_edges(c);
+        if (st == SNN_OK) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        return st;
     }
     void* p;
     size_t elem;
@@ -1064,6 +1100,8 @@ snn_status snn_get_info(snn_ctx* c, snn_info* info)
     info->rows_sorted = c->rows_sorted ? 1 : 0;
     info->edges = c->E;
     info->device_bytes = c->bytes_held;
+    info->edge_bytes = c->use_tiled ? edge_bytes_of(c->packed ? kWPacked : (c->w16 ? kW16 : kWF32)) : (c->w16 ? 6u : 8u);
+    info->reserved = 0;
     return SNN_OK;
 }
 

@@ -83,6 +83,7 @@ struct Net {
     float* w32;
     const uint8_t* meta;
     const uint4* rinfo;     // per padded row: start (lo, hi), length, meta -- one load per spike
+    const uint32_t* pk;     // packed edges for the tiled receive (null when not used)
     const uint64_t* coff;   // STDP: plastic in-edges per padded post id
     const uint32_t* cedge;  // STDP: edge index of each plastic in-edge
     const uint32_t* cpre;   // STDP: padded presynaptic id of each plastic in-edge

@@ -54,7 +54,9 @@ struct TileDev {
     uint32_t tau, ntiles;           // tile index inside the instance, tiles of the instance
     uint32_t nparts;                // static plan: spike parts of this tile
     uint32_t lpieces;               // per-step plan: a row segment is cut into 2^lpieces pieces
+    uint32_t pbase;                 // the instance's first padded id
     float seg;                      // per-step plan: expected work per arriving spike (edges)
+    uint32_t pad;
     unsigned long long split;       // base of the instance's split table: n_b rows x (ntiles-1) uint32
     unsigned long long part_base;   // static plan: base of the partials (nparts x CH x len int32) if nparts > 1
 };
@@ -63,11 +65,17 @@ struct MergeDev {  // one chunk of a multi-part tile to add up
     uint32_t tile, off, len, pad;
 };
 
+// One work item of a step: spikes [s_beg, s_end) of tile k's instance, one of
+// the tile's P parts.
+struct ItemDev {
+    uint32_t k, s_beg, s_end, P;
+};
+
 // The plan of one step, written by k_plan and read by the receive.
 struct StepPlan {
-    uint32_t* hdr = nullptr;    // [0] items
-    uint32_t* items = nullptr;  // (tile << 8 | part), heaviest first
-    uint32_t* parts = nullptr;  // P_k (0: no spike arrives)
+    uint32_t* hdr = nullptr;   // [0] items
+    ItemDev* items = nullptr;  // heaviest first
+    uint32_t* parts = nullptr; // P_k (0: no spike arrives)
 };
 
 struct TiledPlan {
@@ -105,7 +113,6 @@ constexpr uint32_t kPlanMaxTiles = 4096;
 constexpr uint32_t kRankSortMax = 1024;  // up to this many tiles the plan sorts by rank, above by a bitonic network
 constexpr float kItemsPerCta = 1.5f;     // per-step plan: items per CTA at the target size
 constexpr float kSpikeCost = 8.0f;     // fixed work of one arriving spike, in edges
-constexpr uint32_t kPieceEdges = 512;  // edges of one vector pass of a warp (32 lanes x kVec x 4)
 constexpr uint32_t kMaxLogPieces = 3;
 
 // Edges are read once per step and never again before the rest of the
@@ -149,23 +156,27 @@ __device__ __forceinline__ uint16_t ld_edge16(const int16_t* ptr, unsigned long 
     return v;
 }
 
-template <bool W16>
-__device__ __forceinline__ int32_t weight_at(const Net& n, uint64_t e, uint32_t shift, unsigned long long pol)
-{
-    if (W16) return (int32_t)(int16_t)ld_edge16(n.w16 + e, pol) << shift;
-    return __float2int_rz(__uint_as_float(ld_edge(reinterpret_cast<const uint32_t*>(n.w32 + e), pol)));
-}
+// Edge layouts the receive reads: binary32 weights and u32 targets, int16
+// weight codes and u32 targets, or one u32 per edge holding the target's
+// offset in its instance (high half) and the int16 code (low half).
+enum : int { kWF32 = 0, kW16 = 1, kWPacked = 2 };
+__host__ __device__ constexpr int vec_of(int wm) { return wm == kWPacked ? 8 : kVec; }
+__host__ __device__ constexpr uint32_t edge_bytes_of(int wm) { return wm == kWF32 ? 8u : (wm == kW16 ? 6u : 4u); }
 
 // Adds the edges [sb, se) of one row into the tile's accumulators a (one
-// warp, all lanes; targets are padded ids, lo the tile's first).  Edges
-// [a4, b4) are read 4 at a time (16-byte target, 8- or 16-byte weight
-// loads); the unaligned head and tail, one edge per lane, are loaded with
-// the first vectors so that they cost no round trip of their own.
-template <bool W16>
+// warp, all lanes).  x0 maps a stored target to its accumulator: padded id -
+// x0 (u32 targets: x0 = the tile's first id) or instance offset - x0 (packed:
+// x0 = the tile's first id - the instance's).  Edges [a4, b4) are read 4 per
+// 16-byte load (targets or packed edges; 8- or 16-byte weight loads beside
+// them), vec_of(WM) loads in flight per lane; the unaligned head and tail,
+// one edge per lane, are loaded with the first vectors so that they cost no
+// round trip of their own.
+template <int WM>
 __device__ __forceinline__ void add_segment(const Net& n, int32_t* a, uint64_t sb, uint64_t se, uint32_t shift,
-                                            uint32_t lo, uint32_t len, uint32_t lane, unsigned long long pol,
+                                            uint32_t x0, uint32_t len, uint32_t lane, unsigned long long pol,
                                             bool& bad)
 {
+    constexpr int V = vec_of(WM);
     const uint64_t up4 = (sb + 3) & ~3ull, dn4 = se & ~3ull;
     const uint64_t a4 = up4 < se ? up4 : se;
     const uint64_t b4 = dn4 > a4 ? dn4 : a4;
@@ -179,33 +190,40 @@ __device__ __forceinline__ void add_segment(const Net& n, int32_t* a, uint64_t s
         else if (lane >= 4 && lane - 4 < se - b4)
             e = b4 + (lane - 4);
         if (e != ~0ull) {
-            hx = ld_edge(n.tgt + e, pol) - lo;
-            hw = weight_at<W16>(n, e, shift, pol);
+            if constexpr (WM == kWPacked) {
+                const uint32_t v = ld_edge(n.pk + e, pol);
+                hx = (v >> 16) - x0;
+                hw = (int32_t)(int16_t)(v & 0xffffu) << shift;
+            } else if constexpr (WM == kW16) {
+                hx = ld_edge(n.tgt + e, pol) - x0;
+                hw = (int32_t)(int16_t)ld_edge16(n.w16 + e, pol) << shift;
+            } else {
+                hx = ld_edge(n.tgt + e, pol) - x0;
+                hw = __float2int_rz(__uint_as_float(ld_edge(reinterpret_cast<const uint32_t*>(n.w32 + e), pol)));
+            }
             head = true;
         }
     }
-    for (uint64_t base = a4; base < b4; base += 128 * kVec) {
-        uint4 tv[kVec];
-        int32_t wv[kVec][4];
+    for (uint64_t base = a4; base < b4; base += 128 * V) {
+        uint4 tv[V];
+        uint4 wr[WM == kWPacked ? 1 : V];  // raw weights: 4 x int16 in .x/.y, or 4 x binary32
 #pragma unroll
-        for (int u = 0; u < kVec; ++u) {
+        for (int u = 0; u < V; ++u) {
             const uint64_t e = base + 128 * u + 4 * lane;
-            tv[u] = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
-            wv[u][0] = wv[u][1] = wv[u][2] = wv[u][3] = 0;
+            tv[u] = make_uint4(0, 0, 0, 0);
+            if constexpr (WM != kWPacked) wr[u] = make_uint4(0, 0, 0, 0);
             if (e < b4) {
-                tv[u] = ld_edges4(n.tgt + e, pol);
-                if (W16) {
-                    const uint2 h = ld_edges2(n.w16 + e, pol);
-                    wv[u][0] = (int32_t)(int16_t)(h.x & 0xffffu) << shift;
-                    wv[u][1] = (int32_t)(int16_t)(h.x >> 16) << shift;
-                    wv[u][2] = (int32_t)(int16_t)(h.y & 0xffffu) << shift;
-                    wv[u][3] = (int32_t)(int16_t)(h.y >> 16) << shift;
+                if constexpr (WM == kWPacked) {
+                    tv[u] = ld_edges4(n.pk + e, pol);
                 } else {
-                    const uint4 f = ld_edges4(n.w32 + e, pol);
-                    wv[u][0] = __float2int_rz(__uint_as_float(f.x));
-                    wv[u][1] = __float2int_rz(__uint_as_float(f.y));
-                    wv[u][2] = __float2int_rz(__uint_as_float(f.z));
-                    wv[u][3] = __float2int_rz(__uint_as_float(f.w));
+                    tv[u] = ld_edges4(n.tgt + e, pol);
+                    if constexpr (WM == kW16) {
+                        const uint2 h = ld_edges2(n.w16 + e, pol);
+                        wr[u].x = h.x;
+                        wr[u].y = h.y;
+                    } else {
+                        wr[u] = ld_edges4(n.w32 + e, pol);
+                    }
                 }
             }
         }
@@ -217,13 +235,38 @@ __device__ __forceinline__ void add_segment(const Net& n, int32_t* a, uint64_t s
             head = false;
         }
 #pragma unroll
-        for (int u = 0; u < kVec; ++u) {
+        for (int u = 0; u < V; ++u) {
             if (base + 128 * u + 4 * lane >= b4) continue;
-            const uint32_t xs[4] = {tv[u].x - lo, tv[u].y - lo, tv[u].z - lo, tv[u].w - lo};
+            uint32_t xs[4];
+            int32_t wv[4];
+            if constexpr (WM == kWPacked) {
+                const uint32_t v[4] = {tv[u].x, tv[u].y, tv[u].z, tv[u].w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    xs[k] = (v[k] >> 16) - x0;
+                    wv[k] = (int32_t)(int16_t)(v[k] & 0xffffu) << shift;
+                }
+            } else {
+                xs[0] = tv[u].x - x0;
+                xs[1] = tv[u].y - x0;
+                xs[2] = tv[u].z - x0;
+                xs[3] = tv[u].w - x0;
+                if constexpr (WM == kW16) {
+                    wv[0] = (int32_t)(int16_t)(wr[u].x & 0xffffu) << shift;
+                    wv[1] = (int32_t)(int16_t)(wr[u].x >> 16) << shift;
+                    wv[2] = (int32_t)(int16_t)(wr[u].y & 0xffffu) << shift;
+                    wv[3] = (int32_t)(int16_t)(wr[u].y >> 16) << shift;
+                } else {
+                    wv[0] = __float2int_rz(__uint_as_float(wr[u].x));
+                    wv[1] = __float2int_rz(__uint_as_float(wr[u].y));
+                    wv[2] = __float2int_rz(__uint_as_float(wr[u].z));
+                    wv[3] = __float2int_rz(__uint_as_float(wr[u].w));
+                }
+            }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (xs[k] < len)
-                    atomicAdd(a + xs[k], wv[u][k]);
+                    atomicAdd(a + xs[k], wv[k]);
                 else
                     bad = true;
             }
@@ -243,7 +286,7 @@ __device__ __forceinline__ void add_segment(const Net& n, int32_t* a, uint64_t s
 // the row record (and split offsets) of a warp's next unit and the spike of
 // the unit after it are fetched while the current unit is delivered, so no
 // load waits on another.
-template <bool W16, int CH>
+template <int WM, int CH>
 __device__ __forceinline__ void deliver_part(const Net& n, const TileDev& T, const uint32_t* q, uint32_t pbase,
                                              const uint32_t* sp, int32_t* acc_s, uint32_t s_beg, uint32_t s_end,
                                              unsigned long long pol, unsigned long long& ev, bool& bad)
@@ -279,7 +322,7 @@ __device__ __forceinline__ void deliver_part(const Net& n, const TileDev& T, con
         const uint64_t pb = sb + ((len * c) >> lk), pe = sb + ((len * (c + 1)) >> lk);
         ev += pe - pb;
         int32_t* a = acc_s + ((CH == 2 && (r0.w & 0x80u)) ? T.len : 0u);
-        add_segment<W16>(n, a, pb, pe, r0.w & 31u, T.lo, T.len, lane, pol, bad);
+        add_segment<WM>(n, a, pb, pe, r0.w & 31u, WM == kWPacked ? T.lo - T.pbase : T.lo, T.len, lane, pol, bad);
         u = u1;
         r0 = r1;
         ylo0 = ylo1;
@@ -289,7 +332,7 @@ __device__ __forceinline__ void deliver_part(const Net& n, const TileDev& T, con
 }
 
 // Shared memory of k_plan for n_pad (a power of two >= the tiles) entries.
-__host__ __device__ inline size_t plan_smem(uint32_t n_pad) { return (size_t)n_pad * 16; }
+__host__ __device__ inline size_t plan_smem(uint32_t n_pad) { return (size_t)n_pad * 20; }
 
 // The plan of step t's receive (one block).  Tile k gets P_k parts as the
 // header of this file states; the items are ordered by work per part,
@@ -313,6 +356,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1) k_plan(Net n, const TileDev* 
     uint32_t* pk = reinterpret_cast<uint32_t*>(key + n_pad);                 // spikes, then P_k
     float* wk = reinterpret_cast<float*>(pk + n_pad);                        // later: rank, then tile by position
     uint32_t* at = reinterpret_cast<uint32_t*>(wk);
+    uint32_t* ck = reinterpret_cast<uint32_t*>(wk + n_pad);                  // spikes
     uint32_t* off = reinterpret_cast<uint32_t*>(key);
     if (threadIdx.x == 0) s_act = 0;
     const unsigned long long ts = t + 1 - n.d;
@@ -322,6 +366,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1) k_plan(Net n, const TileDev* 
         const uint32_t c = cnt[__ldg(&tiles[k].inst)];
         const float w = (float)c * __ldg(&tiles[k].seg);
         pk[k] = c;
+        ck[k] = c;
         wk[k] = w;
         wsum += w;
     }
@@ -428,7 +473,9 @@ __global__ void __launch_bounds__(kPlanThreads, 1) k_plan(Net n, const TileDev* 
             else
                 hi = mid;
         }
-        sp.items[i] = (at[lo] << 8) | (i - off[lo]);
+        const uint32_t k = at[lo], part = i - off[lo], P = pk[k], c = ck[k];
+        sp.items[i] = ItemDev{k, (uint32_t)((unsigned long long)c * part / P),
+                              (uint32_t)((unsigned long long)c * (part + 1) / P), P};
     }
 }
 
@@ -446,14 +493,19 @@ __device__ __forceinline__ void bulk_out(int32_t* g, const int32_t* s, uint32_t 
                      : "memory");
 }
 
-// The receive of one step under the per-step plan.
-template <bool W16, int CH>
+// The receive of one step under the per-step plan.  CTA c starts with item c
+// and takes the next ones from an atomic counter; thread 0 takes and reads
+// the CTA's next item when it is done with its own units of the current
+// one, while the other warps finish theirs.
+template <int WM, int CH>
 __global__ void __launch_bounds__(kTiledThreads, kTiledCtasPerSm) k_receive_tiled(Net n, const TileDev* __restrict__ tiles,
                                                                     uint32_t n_tiles, StepPlan sp,
                                                                     const uint32_t* __restrict__ split, uint32_t max_len)
 {
     extern __shared__ __align__(16) int32_t acc_s[];  // CH * max_len (the current tile uses CH * len)
-    __shared__ uint32_t s_item;
+    __shared__ TileDev s_T[2];
+    __shared__ ItemDev s_I[2];
+    __shared__ uint32_t s_ok[2];
     const unsigned long long t = n.ctl->t + n.k;
     const uint32_t lane = threadIdx.x & 31u;
     unsigned int* ctr = n.tile_ctr + (t & 1ull);
@@ -461,45 +513,49 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledCtasPerSm) k_receive_tile
     const unsigned long long ts = t + 1 >= n.d ? t + 1 - n.d : 0ull;
     unsigned long long ev = 0;  // every lane of a warp counts the warp's segments; lane 0 reports
     bool bad = false;           // a target outside the tile: the split table does not match the rows
-    if (n_items == 0) return;
+    if (blockIdx.x >= n_items) return;
     const unsigned long long pol = evict_first_policy();
+    const uint32_t* qs = n.q + (size_t)(ts % n.D) * n.Np;
+    // item it's record and tile into buffer b (thread 0); false when the plan is done
+    auto take = [&](uint32_t it, uint32_t b) {
+        bool ok = it < n_items;
+        if (ok) {
+            const ItemDev I = sp.items[it];
+            if (I.k < n_tiles && I.s_beg <= I.s_end) {
+                s_I[b] = I;
+                s_T[b] = tiles[I.k];
+            } else {  // not produced by a correct plan: report, touch nothing
+                atomicOr(&n.ctl->err, kErrPlan);
+                ok = false;
+            }
+        }
+        s_ok[b] = ok ? 1u : 0u;
+    };
+    if (threadIdx.x == 0) take(blockIdx.x, 0);
     // the accumulators start at zero, and every item leaves them at zero
     for (uint32_t i = threadIdx.x; i < CH * max_len / 4; i += blockDim.x)
         reinterpret_cast<int4*>(acc_s)[i] = make_int4(0, 0, 0, 0);
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1u);
-        __syncthreads();
-        const uint32_t item = s_item;
-        if (item >= n_items) break;
-        const uint32_t code = sp.items[item];
-        const uint32_t k = code >> 8, part = code & 0xffu;
-        const uint32_t P = k < n_tiles ? sp.parts[k] : 0u;
-        if (part >= P) {  // not produced by a correct plan: report, touch nothing
-            if (threadIdx.x == 0) atomicOr(&n.ctl->err, kErrPlan);
-            __syncthreads();
-            continue;
-        }
-        const TileDev T = tiles[k];
-        const uint32_t cnt = n.icount[(size_t)(ts & (n.cr - 1)) * n.n_inst + T.inst];
-        const uint32_t pbase = __ldg(&n.inst[T.inst].pbase);
-        const uint32_t* q = n.q + (size_t)(ts % n.D) * n.Np + pbase;
-        deliver_part<W16, CH>(n, T, q, pbase, split + T.split, acc_s,
-                              (uint32_t)((unsigned long long)cnt * part / P),
-                              (uint32_t)((unsigned long long)cnt * (part + 1) / P), pol, ev, bad);
+    __syncthreads();
+    for (uint32_t b = 0; s_ok[b]; b ^= 1u) {
+        const ItemDev& I = s_I[b];  // read from shared memory where used
+        const TileDev& T = s_T[b];
+        deliver_part<WM, CH>(n, T, qs + T.pbase, T.pbase, split + T.split, acc_s, I.s_beg, I.s_end, pol, ev, bad);
+        if (threadIdx.x == 0) take(atomicAdd(ctr, 1u) + gridDim.x, b ^ 1u);
         // the tile's pending input for the next update, or this part's share
         // of it: the shared-memory adds are made visible to the copy engine,
         // which reads them out before they are cleared
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (threadIdx.x == 0) {
-            bulk_out(n.acc0 + T.lo, acc_s, T.len * 4u, P > 1);
-            if (CH == 2) bulk_out(n.acc1 + T.lo, acc_s + T.len, T.len * 4u, P > 1);
+            bulk_out(n.acc0 + T.lo, acc_s, T.len * 4u, I.P > 1);
+            if (CH == 2) bulk_out(n.acc1 + T.lo, acc_s + T.len, T.len * 4u, I.P > 1);
             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
             asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
         }
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < CH * T.len / 4; i += blockDim.x)
             reinterpret_cast<int4*>(acc_s)[i] = make_int4(0, 0, 0, 0);
+        __syncthreads();
     }
     if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     if (lane == 0 && ev) atomicAdd(&n.ctl->events, ev);
@@ -587,10 +643,13 @@ inline cudaError_t tiled_set_smem(size_t smem)
 {
     cudaError_t e = cudaSuccess;
     const int s = (int)smem;
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_receive_tiled<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_receive_tiled<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_receive_tiled<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_receive_tiled<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_receive_tiled<kWF32, 1>, attr, s);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_receive_tiled<kW16, 1>, attr, s);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_receive_tiled<kWPacked, 1>, attr, s);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_receive_tiled<kWF32, 2>, attr, s);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_receive_tiled<kW16, 2>, attr, s);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_receive_tiled<kWPacked, 2>, attr, s);
     return e;
 }
 
@@ -620,7 +679,8 @@ inline void tiled_free(TiledPlan& P, const std::function<void(void*)>& release)
 inline snn_status tiled_plan(TiledPlan& P, const Net& n, const snn_params* params, const uint32_t* pbase,
                              uint32_t n_inst, int channels, uint32_t max_len, const double* work,
                              const uint64_t* inst_edges, int sms, const std::function<void*(size_t)>& alloc,
-                             const std::function<void(void*)>& release, cudaStream_t s, bool dynamic)
+                             const std::function<void(void*)>& release, cudaStream_t s, bool dynamic,
+                             uint32_t piece_edges)
 {
     max_len = std::max<uint32_t>(256, max_len / 256 * 256);
     std::vector<double> wk(n_inst, 0.0);
@@ -650,12 +710,13 @@ inline snn_status tiled_plan(TiledPlan& P, const Net& n, const snn_params* param
             d.tau = tau;
             d.ntiles = T;
             d.nparts = 1;
+            d.pbase = pbase[b];
             // mean segment of a row in this tile, plus the fixed cost of a spike;
             // pieces of about one vector pass each
             const double mseg = params[b].n ? (double)inst_edges[b] / params[b].n * d.len / npad : 0.0;
             d.seg = (float)mseg + kSpikeCost;
             d.lpieces = 0;
-            while (d.lpieces < kMaxLogPieces && mseg >= (double)(2u << d.lpieces) * kPieceEdges * 0.75) ++d.lpieces;
+            while (d.lpieces < kMaxLogPieces && mseg >= (double)(2u << d.lpieces) * piece_edges * 0.75) ++d.lpieces;
             d.split = split_base[b];
             tiles.push_back(d);
             tile_work.push_back(wk[b] * d.len / npad);
@@ -672,8 +733,8 @@ inline snn_status tiled_plan(TiledPlan& P, const Net& n, const snn_params* param
     if (tiled_set_smem(smem) != cudaSuccess) return SNN_E_CUDA;
     int ctas = 0;
     cudaError_t oe = channels == 2
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_receive_tiled<true, 2>, kTiledThreads, smem)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_receive_tiled<true, 1>, kTiledThreads, smem);
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_receive_tiled<kW16, 2>, kTiledThreads, smem)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_receive_tiled<kW16, 1>, kTiledThreads, smem);
     if (oe != cudaSuccess || ctas < 1) {
         cudaGetLastError();
         ctas = 1;
@@ -724,7 +785,7 @@ inline snn_status tiled_plan(TiledPlan& P, const Net& n, const snn_params* param
         Q.items_cap = (uint32_t)std::ceil(kItemsPerCta * n_ctas) + 16 + (uint32_t)tiles.size();
         Q.grid = n_ctas;
         Q.step.hdr = static_cast<uint32_t*>(alloc(4 * sizeof(uint32_t)));
-        Q.step.items = static_cast<uint32_t*>(alloc((size_t)Q.items_cap * 4));
+        Q.step.items = static_cast<ItemDev*>(alloc((size_t)Q.items_cap * sizeof(ItemDev)));
         Q.step.parts = static_cast<uint32_t*>(alloc(tiles.size() * 4));
         uint32_t n_pad = 1;
         while (n_pad < tiles.size()) n_pad <<= 1;
@@ -780,21 +841,41 @@ inline cudaError_t enqueue_tiled_plan(const TiledPlan& P, const Net& n, cudaStre
     return cudaGetLastError();
 }
 
-// The receive of one step under its plan.
-inline cudaError_t enqueue_tiled_receive(const TiledPlan& P, const Net& n, bool w16, cudaStream_t s)
+// The receive of one step under its plan; wm: the edge layout to read.
+inline cudaError_t enqueue_tiled_receive(const TiledPlan& P, const Net& n, int wm, cudaStream_t s)
 {
+#define SNN_RECV_ARGS <<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.n_tiles, P.step, P.split, P.max_len)
     if (P.channels == 2) {
-        if (w16)
-            k_receive_tiled<true, 2><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.n_tiles, P.step, P.split, P.max_len);
+        if (wm == kWPacked)
+            k_receive_tiled<kWPacked, 2> SNN_RECV_ARGS;
+        else if (wm == kW16)
+            k_receive_tiled<kW16, 2> SNN_RECV_ARGS;
         else
-            k_receive_tiled<false, 2><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.n_tiles, P.step, P.split, P.max_len);
+            k_receive_tiled<kWF32, 2> SNN_RECV_ARGS;
     } else {
-        if (w16)
-            k_receive_tiled<true, 1><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.n_tiles, P.step, P.split, P.max_len);
+        if (wm == kWPacked)
+            k_receive_tiled<kWPacked, 1> SNN_RECV_ARGS;
+        else if (wm == kW16)
+            k_receive_tiled<kW16, 1> SNN_RECV_ARGS;
         else
-            k_receive_tiled<false, 1><<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.n_tiles, P.step, P.split, P.max_len);
+            k_receive_tiled<kWF32, 1> SNN_RECV_ARGS;
     }
+#undef SNN_RECV_ARGS
     return cudaGetLastError();
+}
+
+// Packed edges (kWPacked) of every row: (target - instance base) << 16 | code.
+__global__ void k_pack_edges(Net n, uint32_t Np, uint32_t* pk)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t pj = warp; pj < Np; pj += nwarps) {
+        const uint32_t pb = n.inst[n.inst_of_w32[pj >> 5]].pbase;
+        const uint64_t beg = n.roff[pj], end = n.roff[pj + 1];
+        for (uint64_t e = beg + lane; e < end; e += 32)
+            pk[e] = ((n.tgt[e] - pb) << 16) | (uint16_t)n.w16[e];
+    }
 }
 
 }  // namespace snn

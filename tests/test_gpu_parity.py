@@ -25,13 +25,14 @@ def _fields(prob):
     return f
 
 
-def run_gpu(snn, prob, n_steps=None, *, w16=True, receive="global", overrides=(), state=None, chunk=None):
+def run_gpu(snn, prob, n_steps=None, *, w16=True, receive="global", overrides=(), state=None, chunk=None,
+            packed=True):
     """Simulate through the C ABI; overrides (step, id, V) are written
     between steps, before that step's update, like the oracle applies them."""
     n_steps = prob.n_steps if n_steps is None else n_steps
     total = prob.n * max(n_steps, 1)
     cap = total + 4096 if total < 10_000_000 else total // 10 + 4096
-    net = snn.Network(prob, w16=w16, receive=RECV[receive], log_capacity=cap)
+    net = snn.Network(prob, w16=w16, receive=RECV[receive], log_capacity=cap, packed=packed)
     try:
         if state:
             for k, v in state.items():
@@ -265,6 +266,29 @@ def test_reset_repeats_the_run(gpu):
     net.close()
 
 
+@pytest.mark.parametrize("packed", [True, False])
+def test_weight_write_reaches_the_receive(gpu, packed):
+    """Weights written through the ABI are the ones the tiled receive
+    delivers (the packed edges are rebuilt from them)."""
+    import dataclasses
+    prob = si.batched_sweep(n_nets=4, base_seed=3, n_steps=300, n_lo=500, n_hi=3000)
+    w = prob.w.copy()
+    w[::3] = 0
+    w[1::7] = -w[1::7]
+    changed = dataclasses.replace(prob, w=w)
+    o = oracle.run(changed)
+    net = gpu.Network(prob, receive=RECV["tiled"], log_capacity=prob.n * 300, packed=packed)
+    assert net.info()["edge_bytes"] == (4 if packed else 6)
+    net.write("w", w)
+    net.step(300)
+    g = {f: net.read(f) for f in _fields(prob)}
+    g["steps"], g["ids"] = net.spikes()
+    g["counters"] = net.counters()
+    net.close()
+    assert len(o["ids"]) > 1000
+    assert_parity(g, o, changed)
+
+
 def test_stats_match_raster(gpu):
     """The binary64 device reductions equal rate and ISI CV computed from
     the raster."""
@@ -304,16 +328,17 @@ def test_retuned_tiles_keep_parity(gpu, tune_steps, receive):
     assert_parity(g, o, prob)
 
 
+@pytest.mark.parametrize("packed", [True, False])
 @pytest.mark.parametrize("n_inst,delay", [(1, 1), (2, 2), (3, 1), (33, 2), (1100, 2)])
-def test_per_step_plan_tile_counts(gpu, n_inst, delay):
+def test_per_step_plan_tile_counts(gpu, n_inst, delay, packed):
     """The tiled receive's per-step plan over 1 to 1,100 tiles (its rank sort
     up to 1,024 tiles, its sorting network above), with the plan beside the
     update (delay 2) and before the receive (delay 1)."""
     insts = [si.brunel_instance(200 + 37 * (b % 7), k=20 + (b % 5), nu_ratio=3.0, graph_seed=b + 1)
              for b in range(n_inst)]
     prob = si.problem(si.BRUNEL, insts, delay=delay, n_steps=80, seed=7)
-    o = oracle.run(prob)
-    g = run_gpu(gpu, prob, w16=True, receive="tiled")
+    o = oracle_run(("plan", n_inst, delay), prob)
+    g = run_gpu(gpu, prob, w16=True, receive="tiled", packed=packed)
     assert len(o["ids"]) > 10 * n_inst
     assert_parity(g, o, prob)
 
