@@ -57,6 +57,7 @@ struct snn_ctx {
     InstDev* inst = nullptr;
     uint32_t* inst_of_w32 = nullptr;
     uint32_t* pois = nullptr;
+    uint8_t* pois_start = nullptr;
     uint64_t* roff = nullptr;
     uint32_t* tgt = nullptr;
     int16_t* w16p = nullptr;
@@ -506,6 +507,18 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
         if (cfg->model == SNN_BRUNEL) np = poisson_table(params[b].lambda, &hpois[(size_t)b * kPoissonCap], kPoissonCap);
         hinst[b] = make_inst(params[b], c->pbase[b], b * kPoissonCap, np);
     }
+    // bucket table of every instance: thresholds below each 2^24 boundary
+    std::vector<uint8_t> hstart((size_t)cfg->n_inst * kPoissonBuckets, 0);
+    for (uint32_t b = 0; b < cfg->n_inst; ++b) {
+        const uint32_t* T = &hpois[(size_t)b * kPoissonCap];
+        const uint32_t nT = hinst[b].pois_n;
+        uint32_t k = 0;
+        for (uint32_t h = 0; h < (uint32_t)kPoissonBuckets; ++h) {
+            const uint64_t lo = (uint64_t)h << 24;
+            while (k < nT && T[k] < lo) ++k;
+            hstart[(size_t)b * kPoissonBuckets + h] = (uint8_t)k;
+        }
+    }
     std::vector<uint32_t> hmap(c->Np / 32, 0);
     for (uint32_t b = 0; b < cfg->n_inst; ++b)
         for (uint32_t w = c->pbase[b] / 32; w < c->pbase[b + 1] / 32; ++w) hmap[w] = b;
@@ -529,11 +542,12 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     c->inst = alloc_n<InstDev>(c, cfg->n_inst);
     c->inst_of_w32 = alloc_n<uint32_t>(c, Npz / 32);
     c->pois = alloc_n<uint32_t>(c, hpois.size());
+    c->pois_start = alloc_n<uint8_t>(c, hstart.size());
     n.V = alloc_n<float>(c, Npz);
     n.r = alloc_n<uint8_t>(c, Npz);
     n.acc0 = alloc_n<int32_t>(c, Npz);
     n.q = alloc_n<uint32_t>(c, (size_t)c->D * Npz);
-    bool ok = c->ctl && c->inst && c->inst_of_w32 && c->pois && n.V && n.r && n.acc0 && n.q && n.count && n.icount && n.lbase &&
+    bool ok = c->ctl && c->inst && c->inst_of_w32 && c->pois && c->pois_start && n.V && n.r && n.acc0 && n.q && n.count && n.icount && n.lbase &&
               n.inst_spikes && n.tile_ctr;
     if (c->vogels) {
         n.ge = alloc_n<float>(c, Npz);
@@ -567,11 +581,14 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     n.inst = c->inst;
     n.inst_of_w32 = c->inst_of_w32;
     n.pois = c->pois;
+    n.pois_start = c->pois_start;
     cudaError_t e = cudaMemcpyAsync(c->inst, hinst.data(), hinst.size() * sizeof(InstDev), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->inst_of_w32, hmap.data(), hmap.size() * 4, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->pois, hpois.data(), hpois.size() * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->pois_start, hstart.data(), hstart.size(), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {

@@ -23,6 +23,7 @@ namespace snn {
 
 constexpr int kPad = 256;         // instance alignment in neurons
 constexpr int kPoissonCap = 64;   // Poisson threshold table entries per instance
+constexpr int kPoissonBuckets = 256;  // buckets of the top 8 bits of a draw
 constexpr float kLattice = 1.0f / 65536.0f;  // 2^-16 mV
 
 enum : uint32_t {
@@ -69,6 +70,7 @@ struct Net {
     const InstDev* inst;
     const uint32_t* inst_of_w32;  // instance of each 32-neuron word
     const uint32_t* pois;         // Poisson thresholds, kPoissonCap per instance
+    const uint8_t* pois_start;    // per instance kPoissonBuckets counts: thresholds < h 2^24
     float* V;
     float* ge;
     float* gi;

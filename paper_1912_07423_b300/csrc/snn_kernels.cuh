@@ -24,16 +24,16 @@ constexpr unsigned kFull = 0xffffffffu;
 
 constexpr int kUpdateNeurons = 8;  // neurons per thread of the update (4 or 8)
 
-// Number of Poisson thresholds <= u: branch-free binary search over the
-// instance's 64-entry table (entries past the real length are 0xffffffff;
-// the count is capped at the real length nT).
-__device__ __forceinline__ uint32_t poisson_count(const uint32_t* __restrict__ T, uint32_t nT, uint32_t u)
+// Number of Poisson thresholds <= u (thresholds T[0..nT) ascending): the
+// instance's bucket table S gives the count below the start of u's bucket
+// (S[h] = thresholds < h 2^24), and the thresholds inside the bucket are
+// passed one by one -- usually none or one.
+__device__ __forceinline__ uint32_t poisson_count(const uint32_t* __restrict__ T, const uint8_t* __restrict__ S,
+                                                  uint32_t nT, uint32_t u)
 {
-    uint32_t k = 0;
-#pragma unroll
-    for (uint32_t step = 32; step; step >>= 1)
-        if (__ldg(T + k + step - 1) <= u) k += step;
-    return min(k, nT);
+    uint32_t k = __ldg(S + (u >> 24));
+    while (k < nT && __ldg(T + k) <= u) ++k;
+    return k;
 }
 
 template <int MODEL, bool STDP, bool STATS>
@@ -62,6 +62,19 @@ __global__ void __launch_bounds__(256) k_update(Net n)
     const bool active = g < G;  // whole warps: Np is a multiple of 256
     const uint32_t id0 = g * NPT;
     uint32_t spk = 0;  // bit k: neuron id0 + k spiked
+    // the state is loaded first: its addresses do not depend on the instance
+    // (padding slots are loaded too and left as they are)
+    float V[NPT];
+    uint8_t r[NPT];
+    int32_t a0[NPT];
+    if (active) {
+#pragma unroll
+        for (int h = 0; h < NPT / 4; ++h) {
+            *reinterpret_cast<float4*>(V + 4 * h) = *reinterpret_cast<const float4*>(n.V + id0 + 4 * h);
+            *reinterpret_cast<uint32_t*>(r + 4 * h) = *reinterpret_cast<const uint32_t*>(n.r + id0 + 4 * h);
+            *reinterpret_cast<int4*>(a0 + 4 * h) = *reinterpret_cast<const int4*>(n.acc0 + id0 + 4 * h);
+        }
+    }
     const uint32_t b = active ? __ldg(n.inst_of_w32 + (id0 >> 5)) : 0u;  // uniform across the warp
     const InstDev* I = n.inst + b;
     const uint32_t pbase = active ? __ldg(&I->pbase) : 0u;
@@ -72,15 +85,6 @@ __global__ void __launch_bounds__(256) k_update(Net n)
         if (local0 < nloc) {
             const float v_th = __ldg(&I->v_th), v_reset = __ldg(&I->v_reset), Pm = __ldg(&I->Pm);
             const uint32_t R = __ldg(&I->R);
-            float V[NPT];
-            uint8_t r[NPT];
-            int32_t a0[NPT];
-#pragma unroll
-            for (int h = 0; h < NPT / 4; ++h) {
-                *reinterpret_cast<float4*>(V + 4 * h) = *reinterpret_cast<const float4*>(n.V + id0 + 4 * h);
-                *reinterpret_cast<uint32_t*>(r + 4 * h) = *reinterpret_cast<const uint32_t*>(n.r + id0 + 4 * h);
-                *reinterpret_cast<int4*>(a0 + 4 * h) = *reinterpret_cast<const int4*>(n.acc0 + id0 + 4 * h);
-            }
 
             if (MODEL == 0) {  // Vogels-Abbott CUBA
                 const float Pe = __ldg(&I->Pe), Pi = __ldg(&I->Pi), e_l = __ldg(&I->e_l);
@@ -128,6 +132,7 @@ __global__ void __launch_bounds__(256) k_update(Net n)
                 const int32_t jext = __ldg(&I->jext);
                 const uint32_t* T = n.pois + __ldg(&I->pois_off);
                 const uint32_t nT = __ldg(&I->pois_n);
+                const uint8_t* S = n.pois_start + (size_t)b * kPoissonBuckets;
                 uint32_t words[8];
                 philox_words8(n.seed, b, local0 >> 3, t, 1, words);
                 const uint32_t wofs = local0 & 7u & ~(uint32_t)(NPT - 1);  // 0 for 8 per thread
@@ -140,7 +145,7 @@ __global__ void __launch_bounds__(256) k_update(Net n)
                         rk -= 1;
                         v = v_reset;
                     } else {
-                        const uint32_t next = poisson_count(T, nT, words[(wofs + k) & 7u]);
+                        const uint32_t next = poisson_count(T, S, nT, words[(wofs + k) & 7u]);
                         const int32_t in = a0[k] + (int32_t)next * jext;
                         v = __fadd_rn(__fmul_rn(v, Pm), __fmul_rn(__int2float_rn(in), kLattice));
                         if (v >= v_th) {
