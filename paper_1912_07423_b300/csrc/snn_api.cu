@@ -259,7 +259,10 @@ snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr, u
             CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_join, 0));
         else
             CUDA_TRY(c, enqueue_tiled_plan(c->tiled, n, s));
-        CUDA_TRY(c, enqueue_tiled_receive(c->tiled, n, c->packed ? kWPacked : (c->w16 ? kW16 : kWF32), s));
+        // with the plan beside the update and no plasticity in between, the
+        // receive follows the update as its programmatic dependent
+        CUDA_TRY(c, enqueue_tiled_receive(c->tiled, n, c->packed ? kWPacked : (c->w16 ? kW16 : kWF32), s,
+                                          fork && !c->stdp && !ev));
         if (mid) cudaEventRecord(mid, s);  // no merge: the parts add into the accumulators
     } else {
         if (c->w16)

@@ -57,6 +57,9 @@ __global__ void __launch_bounds__(256) k_update(Net n)
             n.tile_ctr[(t + 1) & 1ull] = 0;
         }
     }
+    // a receive launched as this kernel's programmatic dependent may start
+    // (it waits for this kernel before touching what it writes)
+    if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const uint32_t G = n.Np / NPT;
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = g < G;  // whole warps: Np is a multiple of 256

@@ -496,11 +496,16 @@ __device__ __forceinline__ void bulk_out(int32_t* g, const int32_t* s, uint32_t 
 // The receive of one step under the per-step plan.  CTA c starts with item c
 // and takes the next ones from an atomic counter; thread 0 takes and reads
 // the CTA's next item when it is done with its own units of the current
-// one, while the other warps finish theirs.
+// one, while the other warps finish theirs.  With pdl set the kernel was
+// launched while the step's update may still run (programmatic dependent
+// launch): it reads nothing the update writes, and waits for the update to
+// finish before its first copy into the accumulators, which the update
+// reads and clears.
 template <int WM, int CH>
 __global__ void __launch_bounds__(kTiledThreads, kTiledCtasPerSm) k_receive_tiled(Net n, const TileDev* __restrict__ tiles,
                                                                     uint32_t n_tiles, StepPlan sp,
-                                                                    const uint32_t* __restrict__ split, uint32_t max_len)
+                                                                    const uint32_t* __restrict__ split, uint32_t max_len,
+                                                                    uint32_t pdl)
 {
     extern __shared__ __align__(16) int32_t acc_s[];  // CH * max_len (the current tile uses CH * len)
     __shared__ TileDev s_T[2];
@@ -547,6 +552,10 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledCtasPerSm) k_receive_tile
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (threadIdx.x == 0) {
+            if (pdl) {  // the update before this kernel reads and clears the accumulators: wait for it
+                asm volatile("griddepcontrol.wait;" ::: "memory");
+                pdl = 0;
+            }
             bulk_out(n.acc0 + T.lo, acc_s, T.len * 4u, I.P > 1);
             if (CH == 2) bulk_out(n.acc1 + T.lo, acc_s + T.len, T.len * 4u, I.P > 1);
             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
@@ -841,27 +850,30 @@ inline cudaError_t enqueue_tiled_plan(const TiledPlan& P, const Net& n, cudaStre
     return cudaGetLastError();
 }
 
-// The receive of one step under its plan; wm: the edge layout to read.
-inline cudaError_t enqueue_tiled_receive(const TiledPlan& P, const Net& n, int wm, cudaStream_t s)
+// The receive of one step under its plan; wm: the edge layout to read; pdl:
+// launch it as a programmatic dependent of the kernel before it on s.
+inline cudaError_t enqueue_tiled_receive(const TiledPlan& P, const Net& n, int wm, cudaStream_t s, bool pdl = false)
 {
-#define SNN_RECV_ARGS <<<P.grid, P.threads, P.smem, s>>>(n, P.tiles, P.n_tiles, P.step, P.split, P.max_len)
-    if (P.channels == 2) {
-        if (wm == kWPacked)
-            k_receive_tiled<kWPacked, 2> SNN_RECV_ARGS;
-        else if (wm == kW16)
-            k_receive_tiled<kW16, 2> SNN_RECV_ARGS;
-        else
-            k_receive_tiled<kWF32, 2> SNN_RECV_ARGS;
-    } else {
-        if (wm == kWPacked)
-            k_receive_tiled<kWPacked, 1> SNN_RECV_ARGS;
-        else if (wm == kW16)
-            k_receive_tiled<kW16, 1> SNN_RECV_ARGS;
-        else
-            k_receive_tiled<kWF32, 1> SNN_RECV_ARGS;
-    }
-#undef SNN_RECV_ARGS
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(P.grid);
+    cfg.blockDim = dim3(P.threads);
+    cfg.dynamicSmemBytes = P.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    const uint32_t flag = pdl ? 1u : 0u;
+    auto go = [&](auto kernel) {
+        return cudaLaunchKernelEx(&cfg, kernel, n, (const TileDev*)P.tiles, P.n_tiles, P.step, (const uint32_t*)P.split,
+                                  P.max_len, flag);
+    };
+    if (P.channels == 2)
+        return wm == kWPacked ? go(k_receive_tiled<kWPacked, 2>) : wm == kW16 ? go(k_receive_tiled<kW16, 2>)
+                                                                             : go(k_receive_tiled<kWF32, 2>);
+    return wm == kWPacked ? go(k_receive_tiled<kWPacked, 1>) : wm == kW16 ? go(k_receive_tiled<kW16, 1>)
+                                                                         : go(k_receive_tiled<kWF32, 1>);
 }
 
 // Packed edges (kWPacked) of every row: (target - instance base) << 16 | code.
