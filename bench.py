@@ -198,6 +198,21 @@ def delivered_spikes(net, prob, t0: int, t1: int) -> int:
     return len(steps)
 
 
+def launch_bytes(net, prob, t0: int, n: int, edge_bytes: int) -> list:
+    """Algorithmic bytes of the receive launches of steps t0 .. t0+n-1, from
+    the spike log and the row lengths: the receive of step t delivers the
+    spikes of step t+1-d, each a whole row (an ncu capture of one of these
+    launches compares with its entry)."""
+    a = max(0, t0 - prob.delay + 1)
+    steps, ids = net.spikes(a, a + n)
+    deg = np.diff(prob.row_off.astype(np.int64))
+    out = []
+    for t in range(t0, t0 + n):
+        m = steps == t + 1 - prob.delay
+        out.append(int(deg[ids[m]].sum()) * edge_bytes + int(m.sum()) * B_SPIKE_DELIVERED)
+    return out
+
+
 def step_bytes(prob, edge_bytes: int, events: int, delivered: int, emitted: int, steps: int) -> float:
     per_neuron = B_NEURON[prob.model] + (B_NEURON_STDP if prob.stdp else 0)
     return (events * edge_bytes + delivered * B_SPIKE_DELIVERED +
@@ -265,10 +280,11 @@ def run_ours(args, rank, world, dist):
     deliv_main = delivered_spikes(net, prob, t_a, t_a + args.steps)
     # ---- per-kernel times (CUDA events around every kernel, same stream)
     n_prof = min(args.steps, args.profile_steps)
+    t_p0 = t_a + args.steps
     c0 = net.counters()
     phases = net.step_profiled(n_prof)
     c1 = net.counters()
-    t_p0 = t_a + args.steps
+    bytes_each = launch_bytes(net, prob, t_p0, min(n_prof, 16), info["edge_bytes"])
     ev_p, sp_p = c1["events"] - c0["events"], c1["spikes"] - c0["spikes"]
     deliv_p = delivered_spikes(net, prob, t_p0, t_p0 + n_prof)
     mem = info["device_bytes"]
@@ -302,7 +318,8 @@ def run_ours(args, rank, world, dist):
                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
                         "traffic": (traffic_ratio() * recv_bytes if traffic_ratio() and recv_kind == "tiled" else None),
                         "launch_ms": recv_ms,
-                        "bytes_per_launch": recv_bytes, "launches": n_prof},
+                        "bytes_per_launch": recv_bytes, "launches": n_prof,
+                        "bytes_each": bytes_each[:16]},
            "step_roofline": {"bytes_per_step": step_b / args.steps, "frac": step_frac, "peak": hbm,
                              "unit": "GB/s", "achieved": step_b / t_main / 1e9},
            "phase_ms_per_step": {k: v / n_prof for k, v in phases.items()},

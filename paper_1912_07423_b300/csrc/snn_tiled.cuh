@@ -551,22 +551,27 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledCtasPerSm) k_receive_tile
         // which reads them out before they are cleared
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (threadIdx.x == 0) {
-            if (pdl) {  // the update before this kernel reads and clears the accumulators: wait for it
-                asm volatile("griddepcontrol.wait;" ::: "memory");
-                pdl = 0;
+        {  // warp w copies out and clears slice w of the CH * len words (1/16 of a
+           // channel or more: slices are multiples of 16 words, inside one channel)
+            const uint32_t nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5;
+            const uint32_t per = CH * T.len / nwarps, w0 = warp * per;
+            if (lane == 0) {
+                if (pdl) {  // the update before this kernel reads and clears the accumulators: wait for it
+                    asm volatile("griddepcontrol.wait;" ::: "memory");
+                    pdl = 0;
+                }
+                const uint32_t ch = CH == 2 && w0 >= T.len ? 1u : 0u;
+                bulk_out((ch ? n.acc1 : n.acc0) + T.lo + (w0 - ch * T.len), acc_s + w0, per * 4u, I.P > 1);
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
             }
-            bulk_out(n.acc0 + T.lo, acc_s, T.len * 4u, I.P > 1);
-            if (CH == 2) bulk_out(n.acc1 + T.lo, acc_s + T.len, T.len * 4u, I.P > 1);
-            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            __syncwarp();
+            for (uint32_t i = lane; i < per / 4; i += 32)
+                reinterpret_cast<int4*>(acc_s + w0)[i] = make_int4(0, 0, 0, 0);
         }
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < CH * T.len / 4; i += blockDim.x)
-            reinterpret_cast<int4*>(acc_s)[i] = make_int4(0, 0, 0, 0);
-        __syncthreads();
     }
-    if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     if (lane == 0 && ev) atomicAdd(&n.ctl->events, ev);
     if (bad) atomicOr(&n.ctl->err, kErrBadTarget);
 }
