@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(256) k_update(Net n)
     const bool active = g < G;  // whole warps: Np is a multiple of 256
     const uint32_t id0 = g * NPT;
     uint32_t spk = 0;  // bit k: neuron id0 + k spiked
+    bool have = false;  // the group holds neurons (not only padding): its state is stored
     // the state is loaded first: its addresses do not depend on the instance
     // (padding slots are loaded too and left as they are)
     float V[NPT];
@@ -193,12 +194,7 @@ __global__ void __launch_bounds__(256) k_update(Net n)
                     }
                 }
             }
-#pragma unroll
-            for (int h = 0; h < NPT / 4; ++h) {
-                *reinterpret_cast<float4*>(n.V + id0 + 4 * h) = *reinterpret_cast<float4*>(V + 4 * h);
-                *reinterpret_cast<uint32_t*>(n.r + id0 + 4 * h) = *reinterpret_cast<uint32_t*>(r + 4 * h);
-                *reinterpret_cast<int4*>(n.acc0 + id0 + 4 * h) = make_int4(0, 0, 0, 0);
-            }
+            have = true;
             if (STATS && spk) {
 #pragma unroll
                 for (int k = 0; k < NPT; ++k)
@@ -241,12 +237,21 @@ __global__ void __launch_bounds__(256) k_update(Net n)
         if (lane >= (uint32_t)o) incl += v;
     }
     const uint32_t total = __shfl_sync(kFull, incl, 31);
-    if (total == 0) return;
     uint32_t wbase = 0, lpos = 0;
-    if (lane == 31) {
+    if (lane == 31 && total) {
         wbase = atomicAdd(&n.icount[(size_t)slot_c * n.n_inst + b], total);
         lpos = atomicAdd(&n.count[slot_c], total);
     }
+    // the state goes back while the atomics are in flight
+    if (have) {
+#pragma unroll
+        for (int h = 0; h < NPT / 4; ++h) {
+            *reinterpret_cast<float4*>(n.V + id0 + 4 * h) = *reinterpret_cast<float4*>(V + 4 * h);
+            *reinterpret_cast<uint32_t*>(n.r + id0 + 4 * h) = *reinterpret_cast<uint32_t*>(r + 4 * h);
+            *reinterpret_cast<int4*>(n.acc0 + id0 + 4 * h) = make_int4(0, 0, 0, 0);
+        }
+    }
+    if (total == 0) return;
     wbase = __shfl_sync(kFull, wbase, 31);
     lpos = __shfl_sync(kFull, lpos, 31);
     if (!spk) return;
