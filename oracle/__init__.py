@@ -98,6 +98,12 @@ def _load():
             lib.orc_run_f64.restype = ctypes.c_int
             lib.orc_raster_free.argtypes = [ctypes.POINTER(_Raster)]
             lib.orc_raster_free.restype = None
+            lib.orc_neg_ln.argtypes = [ctypes.c_float]
+            lib.orc_neg_ln.restype = ctypes.c_float
+            lib.orc_job_from_uniforms.argtypes = [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp, _vp, _vp]
+            lib.orc_job_from_uniforms.restype = ctypes.c_int
+            lib.orc_expand_jobs.argtypes = [_vp, ctypes.c_uint64, ctypes.c_uint64, _vp, ctypes.c_uint64]
+            lib.orc_expand_jobs.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -121,6 +127,41 @@ def philox4x64_10(ctr, key) -> np.ndarray:
 
 def rand_word(seed: int, inst: int, local: int, step: int, tag: int) -> int:
     return int(_load().orc_rand_word(seed, inst, local, step, tag))
+
+
+# a job of the adjacency construction (Fig. 2): n, a, b, reserved, o
+JOB_DTYPE = np.dtype([("n", "<u4"), ("a", "<u4"), ("b", "<u4"), ("reserved", "<u4"), ("o", "<u8")])
+
+
+def neg_ln(u: float) -> float:
+    """-ln(u), u in (0, 1], the oracle's own binary32 logarithm (Fig. 2)."""
+    return float(_load().orc_neg_ln(ctypes.c_float(u)))
+
+
+def job_from_uniforms(u, a: int, b: int):
+    """The steps of one job (Fig. 2) from its uniforms u[0..n]: returns
+    (q, c, out) -- integer spacings, exclusive running sums (c[n+1] is the
+    total) and the n output values."""
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    n = u.size - 1
+    q = np.zeros(n + 1, dtype=np.uint32)
+    c = np.zeros(n + 2, dtype=np.uint64)
+    out = np.zeros(max(n, 1), dtype=np.uint32)
+    st = _load().orc_job_from_uniforms(_ptr(u), n, a, b, _ptr(q), _ptr(c), _ptr(out))
+    if st != 0:
+        raise OracleError(f"job_from_uniforms failed ({st})")
+    return q, c, out[:n]
+
+
+def expand_jobs(jobs: np.ndarray, seed: int, out_len: int) -> np.ndarray:
+    """Expand jobs (JOB_DTYPE records) into a uint32 array of out_len values;
+    entries no job writes stay 0xffffffff."""
+    jobs = np.ascontiguousarray(jobs, dtype=JOB_DTYPE)
+    out = np.full(max(out_len, 1), 0xffffffff, dtype=np.uint32)
+    st = _load().orc_expand_jobs(_ptr(jobs), jobs.size, seed, _ptr(out), out_len)
+    if st != 0:
+        raise OracleError(f"expand_jobs failed ({st})")
+    return out[:out_len]
 
 
 def poisson_table(lam: float) -> np.ndarray:

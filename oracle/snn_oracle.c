@@ -61,6 +61,20 @@
  *     i in S_t; potentiation w += rint(Ap*x_j) for the in-edges of i in
  *     S_t; each change is clipped to [0, w_max].  Ap = a_plus*w_max and
  *     Am = a_minus*w_max are rounded to binary32 once.
+ *
+ * Adjacency construction (Section III-A-2, Fig. 2), a separate function: a
+ * job (n, a, b, o) writes n sorted, unique, uniformly distributed random
+ * integers from [a, b) at offset o.  Readings: the figure draws n + 2
+ * uniforms but the last one's spacing is never used (its running sum is
+ * exclusive: it starts at 0 and ends at the normaliser), so n + 1 spacings
+ * are drawn; the scale is b - a - n (the figure's "b - n" with a = 0), so
+ * that adding a and 0 .. n-1 keeps the values in [a, b); spacings are held
+ * as integers (2^-24 units of the binary32 -ln u) so that running sums do
+ * not depend on their order, and the logarithm is this file's own
+ * (range reduction and the atanh series), so that both sides round every
+ * decision the same way.  The figure's row (d) does not follow from its row
+ * (c) at two positions (2.32/3.88 printed as 0.4, 2.53/3.88 as 0.6); the
+ * tests pin its other steps.
  */
 #include <math.h>
 #include <stdint.h>
@@ -578,6 +592,87 @@ done:
     free(step_start); free(T); free(nT);
     free(L.step); free(L.id);
     return st;
+}
+
+/* ------------------------------------------------------------------ */
+/* Adjacency construction, Fig. 2: sorted random integers by           */
+/* exponential spacings.                                                */
+/* ------------------------------------------------------------------ */
+
+/* -ln(u) for u in (0, 1], binary32, one operation at a time: u = m 2^e with
+ * m in [1, 2) (read from the bits), ln m = 2 atanh(s) = 2 (s + s^3/3 + ... +
+ * s^13/13) with s = (m - 1) / (m + 1) < 1/3, ln u = e ln 2 + ln m. */
+float orc_neg_ln(float u)
+{
+    uint32_t bits;
+    memcpy(&bits, &u, 4);
+    const int32_t e = (int32_t)((bits >> 23) & 0xffu) - 127;
+    const uint32_t mb = (bits & 0x7fffffu) | 0x3f800000u;
+    float m;
+    memcpy(&m, &mb, 4);
+    const float s = (m - 1.0f) / (m + 1.0f);
+    const float s2 = s * s;
+    float t = s, sum = s;
+    for (int k = 3; k <= 13; k += 2) {
+        t = t * s2;
+        sum = sum + t / (float)k;
+    }
+    const float ln_u = (float)e * 0.693147182f + 2.0f * sum;
+    return -ln_u;
+}
+
+/* The steps of one job from its n + 1 uniforms u[0..n] in (0, 1]:
+ * exponential spacings E_k = -ln u_k, held as q_k = E_k 2^24 rounded
+ * (binary32, then an integer, so the sums are exact in any order); the
+ * exclusive running sums c_0 = 0, c_k = q_0 + ... + q_{k-1} (c_{n+1} the
+ * total, which normalises); output k = 1..n: a + round(c_k / c_{n+1} M) +
+ * (k - 1) with M = b - a - n, the added k - 1 keeping the values distinct
+ * (binary32 ratio and product, rounded half up, at most M).  q and c may
+ * be NULL.  Needs n <= b - a and M <= 2^24. */
+int orc_job_from_uniforms(const float* u, uint32_t n, uint32_t a, uint32_t b, uint32_t* q, uint64_t* c,
+                          uint32_t* out)
+{
+    if (b < a || n > b - a || b - a - n > (1u << 24)) return ORC_E_ARG;
+    const uint32_t M = b - a - n;
+    uint64_t* cc = c ? c : (uint64_t*)malloc(((size_t)n + 2) * sizeof(uint64_t));
+    if (!cc) return ORC_E_NOMEM;
+    cc[0] = 0;
+    for (uint32_t k = 0; k <= n; ++k) {
+        const uint32_t qk = (uint32_t)(orc_neg_ln(u[k]) * 16777216.0f + 0.5f);
+        if (q) q[k] = qk;
+        cc[k + 1] = cc[k] + qk;
+    }
+    const uint64_t total = cc[n + 1];
+    for (uint32_t k = 1; k <= n; ++k) {
+        uint32_t r = 0;
+        if (total) {
+            const float x = (float)cc[k] / (float)total * (float)M + 0.5f;
+            r = (uint32_t)x;
+            if (r > M) r = M;
+        }
+        out[k - 1] = a + r + (k - 1);
+    }
+    if (!c) free(cc);
+    return ORC_OK;
+}
+
+/* Every job j draws its uniforms from Philox4x64-10 with key (seed, j),
+ * counter (k >> 3, 0, 2, 0), word k & 7: u_k = (word >> 8 + 1) 2^-24. */
+int orc_expand_jobs(const orc_job* jobs, uint64_t n_jobs, uint64_t seed, uint32_t* out, uint64_t out_len)
+{
+    for (uint64_t j = 0; j < n_jobs; ++j) {
+        const orc_job J = jobs[j];
+        if (J.b < J.a || J.n > J.b - J.a || J.b - J.a - J.n > (1u << 24) || J.o > out_len || J.n > out_len - J.o)
+            return ORC_E_ARG;
+        float* u = (float*)malloc(((size_t)J.n + 1) * sizeof(float));
+        if (!u) return ORC_E_NOMEM;
+        for (uint32_t k = 0; k <= J.n; ++k)
+            u[k] = (float)((orc_rand_word(seed, j, k, 0, 2) >> 8) + 1u) * (1.0f / 16777216.0f);
+        const int st = orc_job_from_uniforms(u, J.n, J.a, J.b, NULL, NULL, out + J.o);
+        free(u);
+        if (st != ORC_OK) return st;
+    }
+    return ORC_OK;
 }
 
 void orc_raster_free(orc_raster* R)

@@ -70,6 +70,13 @@ typedef struct {
     uint64_t events; /* delivered synaptic events */
 } orc_raster;
 
+/* A job of the adjacency construction (Fig. 2): write n sorted, unique,
+ * uniformly distributed random integers from [a, b) to out[o .. o + n). */
+typedef struct {
+    uint32_t n, a, b, reserved;
+    uint64_t o;
+} orc_job;
+
 void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
 uint32_t orc_rand_word(uint64_t seed, uint64_t inst, uint64_t local, uint64_t step, uint64_t tag);
 int orc_poisson_table(double lambda, uint32_t* T, int cap);
@@ -78,6 +85,10 @@ int orc_receive(const orc_problem* P, const int32_t* w, const uint32_t* spikes, 
                 int64_t* acc0, int64_t* acc1, uint64_t* events);
 int orc_run(const orc_problem* P, orc_state* S, orc_raster* R);
 int orc_run_f64(const orc_problem* P, const double* w_mV, double* V_out, orc_raster* R);
+float orc_neg_ln(float u);
+int orc_job_from_uniforms(const float* u, uint32_t n, uint32_t a, uint32_t b, uint32_t* q, uint64_t* c,
+                          uint32_t* out);
+int orc_expand_jobs(const orc_job* jobs, uint64_t n_jobs, uint64_t seed, uint32_t* out, uint64_t out_len);
 void orc_raster_free(orc_raster* R);
 
 #endif
