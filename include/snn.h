@@ -239,6 +239,26 @@ snn_status snn_rate_cv_static(const uint32_t* count, const unsigned long long* i
                               const unsigned long long* isi_sq, uint32_t n, uint64_t window_steps, double dt_ms,
                               void* stream, double* rate_hz, double* isi_cv);
 
+/* A job of the adjacency construction (Section III-A-2, Fig. 2): n sorted,
+ * unique, uniformly distributed random integers from [a, b), written at
+ * out[o .. o + n). */
+typedef struct {
+    uint32_t n, a, b, reserved;
+    uint64_t o;
+} snn_job;
+
+/* Expand n_jobs jobs on the GPU (no context needed).  Job j draws its n + 1
+ * exponential spacings from Philox4x64-10 with key (seed, j) and counter
+ * (k >> 3, 0, 2, 0), word k & 7; value k = 1..n is a + round(c_k / c_{n+1}
+ * (b - a - n)) + (k - 1), c_k the exclusive running sum of the spacings.
+ * jobs and out are device pointers (out_len elements); stream is a CUDA
+ * stream (NULL: the legacy default stream).  Waits for the stream.  Errors:
+ * SNN_E_ARG for n_jobs >= 2^32 or a job with b < a, n > b - a,
+ * b - a - n > 2^24 or o + n > out_len (that job writes nothing; the others
+ * are written); SNN_E_CUDA.  Allocates nothing. */
+snn_status snn_expand_jobs(const snn_job* jobs, uint64_t n_jobs, uint64_t seed, uint32_t* out, uint64_t out_len,
+                           void* stream);
+
 /* What the context chose and holds. */
 typedef struct {
     uint32_t receive;      /* SNN_RECV_GLOBAL or SNN_RECV_TILED (after snn_build_graph) */

@@ -96,6 +96,7 @@ def load():
                 "snn_get_info": (S, [_vp, ctypes.POINTER(Info)]),
                 "snn_rate_cv_static": (S, [_vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double, _vp,
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+                "snn_expand_jobs": (S, [_vp, ctypes.c_uint64, ctypes.c_uint64, _vp, ctypes.c_uint64, _vp]),
                 "snn_last_error": (ctypes.c_char_p, [_vp]),
                 "snn_status_string": (ctypes.c_char_p, [ctypes.c_int]),
                 "snn_destroy": (None, [_vp]),
@@ -112,7 +113,39 @@ def exported_symbols() -> list:
     return ["snn_create", "snn_build_graph", "snn_reset", "snn_step", "snn_step_profiled", "snn_sync",
             "snn_read_spikes",
             "snn_log_clear", "snn_read_state", "snn_write_state", "snn_counters", "snn_stats", "snn_stats_clear",
-            "snn_get_info", "snn_rate_cv_static", "snn_last_error", "snn_status_string", "snn_destroy"]
+            "snn_get_info", "snn_rate_cv_static", "snn_expand_jobs", "snn_last_error", "snn_status_string",
+            "snn_destroy"]
+
+
+# a job of the adjacency construction (snn_job): n, a, b, reserved, o
+JOB_DTYPE = np.dtype([("n", "<u4"), ("a", "<u4"), ("b", "<u4"), ("reserved", "<u4"), ("o", "<u8")])
+
+
+def expand_jobs(jobs, seed: int, out_len: int, *, out=None, device: str = "cuda:0", stream=None):
+    """Adjacency construction on the GPU (snn_expand_jobs, Fig. 2).  jobs: a
+    JOB_DTYPE array (host) or a uint8 CUDA tensor of such records; returns
+    the uint32 values as an int32 CUDA tensor of out_len elements (out, if
+    given, is written instead; slots no job writes keep their contents)."""
+    import torch
+    if not torch.cuda.is_available():
+        raise SnnError(-3, "no CUDA device: libsnn has no CPU fallback")
+    lib = load()
+    dev = torch.device(device)
+    if isinstance(jobs, np.ndarray):
+        jobs = np.ascontiguousarray(jobs, dtype=JOB_DTYPE)
+        n_jobs = jobs.size
+        djobs = torch.from_numpy(jobs.view(np.uint8)).to(dev)
+    else:
+        djobs = jobs
+        n_jobs = djobs.numel() // JOB_DTYPE.itemsize
+    if out is None:
+        out = torch.empty(max(out_len, 1), dtype=torch.int32, device=dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    rc = lib.snn_expand_jobs(djobs.data_ptr() if n_jobs else None, n_jobs, seed, out.data_ptr(), out_len,
+                             st.cuda_stream)
+    if rc != 0:
+        raise SnnError(rc, "snn_expand_jobs: " + lib.snn_status_string(rc).decode())
+    return out[:out_len]
 
 
 def _params_array(instances) -> ctypes.Array:

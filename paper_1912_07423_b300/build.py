@@ -7,7 +7,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = [os.path.join(CSRC, "snn_api.cu"), os.path.join(CSRC, "snn_static.cu")]
+SOURCES = [os.path.join(CSRC, "snn_api.cu"), os.path.join(CSRC, "snn_static.cu"), os.path.join(CSRC, "snn_graph.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")] + \
     [os.path.join(ROOT, "include", "snn.h")]
 LIB = os.path.join(HERE, "libsnn.so")

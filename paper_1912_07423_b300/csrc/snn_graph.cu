@@ -1,0 +1,169 @@
+// snn_graph.cu -- adjacency construction on the GPU (Section III-A-2, Fig. 2).
+//
+// A job (n, a, b, o) asks for n sorted, unique, uniformly distributed random
+// integers from [a, b), written at out[o .. o + n).  The running sums of
+// exponentially distributed spacings are, once normalised by their total,
+// the order statistics of uniform draws; scaled to b - a - n and rounded,
+// with 0 .. n-1 added to keep them distinct, they are the job's values.
+//
+// One warp per job.  Uniforms u_k, k = 0..n (n + 1 spacings, the figure's
+// two sentinels being the zero start and the normalising total), come from
+// Philox4x64-10 with key (seed, job) and counter (k >> 3, 0, 2, 0), word
+// k & 7: u_k = ((word >> 8) + 1) 2^-24 in (0, 1].  The spacing -ln u_k is
+// computed in binary32 by this file's own logarithm (range reduction to
+// m in [1, 2) from the bits, ln m = 2 atanh s by its series to s^13, s =
+// (m - 1) / (m + 1)) and held as an integer q_k = round(-ln u_k 2^24), so
+// that the warp's running sums are exact in any order.  A first pass sums
+// the q_k of the job, a second one recomputes them, scans them across the
+// warp and writes value k = a + round(c_k / c_total (b - a - n)) + (k - 1),
+// c_k the exclusive running sum (binary32 ratio and product, at most
+// b - a - n).  Every operation is rounded as written (-fmad=false), so the
+// values do not depend on the launch.
+#include <cuda_runtime.h>
+
+
+#include "../../include/snn.h"
+#include "snn_device.cuh"
+
+namespace {
+
+constexpr unsigned kJobThreads = 256;
+constexpr uint32_t kMaxScale = 1u << 24;  // b - a - n: the binary32 ratio keeps every integer below it apart
+
+// flag of an invalid job, one per device (no allocation)
+static __device__ unsigned int g_job_err;
+
+__device__ __forceinline__ float neg_ln_f32(float u)
+{
+    const uint32_t bits = __float_as_uint(u);
+    const int32_t e = (int32_t)((bits >> 23) & 0xffu) - 127;
+    const float m = __uint_as_float((bits & 0x7fffffu) | 0x3f800000u);
+    const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float s2 = __fmul_rn(s, s);
+    float t = s, sum = s;
+#pragma unroll
+    for (int k = 3; k <= 13; k += 2) {
+        t = __fmul_rn(t, s2);
+        sum = __fadd_rn(sum, __fdiv_rn(t, (float)k));
+    }
+    return -__fadd_rn(__fmul_rn(__int2float_rn(e), 0.693147182f), __fmul_rn(2.0f, sum));
+}
+
+// the 8 integer spacings of Philox block g of job j (k = 8g .. 8g + 7)
+__device__ __forceinline__ void spacings8(uint64_t seed, uint32_t j, uint32_t g, uint32_t q[8])
+{
+    uint32_t w[8];
+    snn::philox_words8(seed, j, g, 0, 2, w);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float u = __fmul_rn(__uint2float_rn((w[i] >> 8) + 1u), 1.0f / 16777216.0f);
+        q[i] = __float2uint_rz(__fadd_rn(__fmul_rn(neg_ln_f32(u), 16777216.0f), 0.5f));
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kJobThreads) k_expand_jobs(const snn_job* __restrict__ jobs, uint64_t n_jobs,
+                                                             uint64_t seed, uint32_t* __restrict__ out,
+                                                             uint64_t out_len)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t jj = warp; jj < n_jobs; jj += nwarps) {
+        const snn_job J = jobs[jj];
+        const uint32_t j = (uint32_t)jj;
+        if (J.b < J.a || J.n > J.b - J.a || J.b - J.a - J.n > kMaxScale || J.o > out_len || J.n > out_len - J.o) {
+            if (lane == 0) atomicOr(&g_job_err, 1u);
+            continue;
+        }
+        const uint32_t n = J.n, M = J.b - J.a - J.n;
+        if (n == 0) continue;
+        // pass 1: the total of the n + 1 spacings; lane l takes block l of
+        // every 256 spacings
+        unsigned long long part = 0;
+        for (uint64_t base = 0; base <= n; base += 256) {
+            const uint32_t g = (uint32_t)(base >> 3) + lane;
+            if ((uint64_t)g * 8 > n) continue;
+            uint32_t q[8];
+            spacings8(seed, j, g, q);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if ((uint64_t)g * 8 + i <= n) part += q[i];
+        }
+        const unsigned long long total = warp_sum(part);
+        const float ftotal = __ull2float_rn(total), fM = __uint2float_rn(M);
+        // pass 2: exclusive running sums and the values
+        unsigned long long carry = 0;
+        uint32_t* dst = out + J.o;
+        for (uint64_t base = 0; base <= n; base += 256) {
+            const uint32_t g = (uint32_t)(base >> 3) + lane;
+            uint32_t q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if ((uint64_t)g * 8 <= n) {
+                spacings8(seed, j, g, q);
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if ((uint64_t)g * 8 + i > n) q[i] = 0;
+            }
+            unsigned long long s8 = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) s8 += q[i];
+            unsigned long long incl = s8;  // inclusive scan of the lanes' sums
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (uint32_t)o) incl += y;
+            }
+            unsigned long long c = carry + incl - s8;  // c_k of the lane's first k
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const uint64_t k = (uint64_t)g * 8 + i;
+                if (k >= 1 && k <= n) {
+                    uint32_t r = 0;
+                    if (total) {
+                        const float x = __fadd_rn(__fmul_rn(__fdiv_rn(__ull2float_rn(c), ftotal), fM), 0.5f);
+                        r = __float2uint_rz(x);
+                        r = r > M ? M : r;
+                    }
+                    dst[k - 1] = J.a + r + (uint32_t)(k - 1);
+                }
+                c += q[i];
+            }
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" snn_status snn_expand_jobs(const snn_job* jobs, uint64_t n_jobs, uint64_t seed, uint32_t* out,
+                                      uint64_t out_len, void* stream)
+{
+    if (n_jobs == 0) return SNN_OK;
+    if (!jobs || (!out && out_len) || n_jobs > 0xffffffffull) return SNN_E_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned int* err = nullptr;
+    if (cudaGetSymbolAddress((void**)&err, g_job_err) != cudaSuccess) {
+        cudaGetLastError();
+        return SNN_E_CUDA;
+    }
+    if (cudaMemsetAsync(err, 0, sizeof(unsigned int), s) != cudaSuccess) return SNN_E_CUDA;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t warps_needed = n_jobs;
+    const uint64_t blocks = (warps_needed * 32 + kJobThreads - 1) / kJobThreads;
+    const uint32_t grid = (uint32_t)(blocks < (uint64_t)sms * 16 ? blocks : (uint64_t)sms * 16);
+    k_expand_jobs<<<grid, kJobThreads, 0, s>>>(jobs, n_jobs, seed, out, out_len);
+    if (cudaGetLastError() != cudaSuccess) return SNN_E_CUDA;
+    unsigned int h = 0;
+    if (cudaMemcpyAsync(&h, err, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return SNN_E_CUDA;
+    return h ? SNN_E_ARG : SNN_OK;
+}
