@@ -198,6 +198,42 @@ def delivered_spikes(net, prob, t0: int, t1: int) -> int:
     return len(steps)
 
 
+def graph_construction(prob, dev, hbm: float, reps: int = 3) -> dict:
+    """snn_expand_jobs (Fig. 2) with one job per neuron of the workload: n =
+    its out-degree, values from its own instance's id range, written at its
+    row offset -- the workload's adjacency, built on the device.  One
+    warm-up call, then reps calls timed with CUDA events on the stream (each
+    call also waits for its error flag).  Algorithmic bytes: 4 per value
+    written + 24 per job record read."""
+    import torch
+    import paper_1912_07423_b300 as snn
+    deg = np.diff(prob.row_off.astype(np.int64)).astype(np.uint32)
+    inst_of = np.repeat(np.arange(len(prob.instances)), np.diff(prob.inst_off.astype(np.int64)))
+    jobs = np.zeros(prob.n, dtype=snn.JOB_DTYPE)
+    jobs["n"] = deg
+    jobs["a"] = prob.inst_off[inst_of]
+    jobs["b"] = prob.inst_off[inst_of + 1]
+    jobs["o"] = prob.row_off[:-1]
+    djobs = torch.from_numpy(jobs.view(np.uint8)).to(dev)
+    E = int(prob.row_off[-1])
+    buf = torch.empty(E, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    snn.expand_jobs(djobs, 1, E, out=buf)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        snn.expand_jobs(djobs, 1, E, out=buf)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    nbytes = 4.0 * E + 24.0 * prob.n
+    del buf, djobs
+    torch.cuda.empty_cache()
+    return {"values": E, "jobs": int(prob.n), "seconds": t, "values_per_s": E / t,
+            "achieved_gbs": nbytes / t / 1e9, "frac_of_hbm": nbytes / t / 1e9 / hbm,
+            "what": "snn_expand_jobs: one job per neuron (out-degree values from its instance's ids)"}
+
+
 def launch_bytes(net, prob, t0: int, n: int, edge_bytes: int) -> list:
     """Algorithmic bytes of the receive launches of steps t0 .. t0+n-1, from
     the spike log and the row lengths: the receive of step t delivers the
@@ -360,6 +396,10 @@ def run_ours(args, rank, world, dist):
                       "seconds": t_e2e, "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                       "includes": "snn_create + snn_build_graph from host arrays + snn_step(K) + snn_read_spikes"}
 
+    # ---- adjacency construction on the GPU (Fig. 2) for the same networks
+    if not args.no_graph:
+        out["graph_construction"] = graph_construction(prob, dev, hbm)
+
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(prob, args.steps)
     return out
@@ -398,6 +438,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="skip timing the GPU adjacency construction")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -69,10 +69,11 @@
  * exclusive: it starts at 0 and ends at the normaliser), so n + 1 spacings
  * are drawn; the scale is b - a - n (the figure's "b - n" with a = 0), so
  * that adding a and 0 .. n-1 keeps the values in [a, b); spacings are held
- * as integers (2^-24 units of the binary32 -ln u) so that running sums do
- * not depend on their order, and the logarithm is this file's own
- * (range reduction and the atanh series), so that both sides round every
- * decision the same way.  The figure's row (d) does not follow from its row
+ * as integers (2^-22 units of the binary32 -ln u) so that running sums do
+ * not depend on their order, the normalise-and-scale step multiplies by one
+ * binary32 factor M / total, and the logarithm is this file's own (range
+ * reduction and the atanh series by Horner's rule), so that both sides
+ * round every decision the same way.  The figure's row (d) does not follow from its row
  * (c) at two positions (2.32/3.88 printed as 0.4, 2.53/3.88 as 0.6); the
  * tests pin its other steps.
  */
@@ -600,10 +601,13 @@ done:
 /* ------------------------------------------------------------------ */
 
 /* -ln(u) for u in (0, 1], binary32, one operation at a time: u = m 2^e with
- * m in [1, 2) (read from the bits), ln m = 2 atanh(s) = 2 (s + s^3/3 + ... +
- * s^13/13) with s = (m - 1) / (m + 1) < 1/3, ln u = e ln 2 + ln m. */
+ * m in [1, 2) (read from the bits), ln m = 2 atanh(s) = 2 s (1 + s^2/3 +
+ * s^4/5 + ... + s^12/13) with s = (m - 1) / (m + 1) < 1/3, the polynomial
+ * in s^2 by Horner's rule with binary32 coefficients 1/k, ln u = e ln 2 +
+ * ln m. */
 float orc_neg_ln(float u)
 {
+    static const float inv[7] = {1.0f, 1.0f / 3.0f, 1.0f / 5.0f, 1.0f / 7.0f, 1.0f / 9.0f, 1.0f / 11.0f, 1.0f / 13.0f};
     uint32_t bits;
     memcpy(&bits, &u, 4);
     const int32_t e = (int32_t)((bits >> 23) & 0xffu) - 127;
@@ -612,23 +616,20 @@ float orc_neg_ln(float u)
     memcpy(&m, &mb, 4);
     const float s = (m - 1.0f) / (m + 1.0f);
     const float s2 = s * s;
-    float t = s, sum = s;
-    for (int k = 3; k <= 13; k += 2) {
-        t = t * s2;
-        sum = sum + t / (float)k;
-    }
-    const float ln_u = (float)e * 0.693147182f + 2.0f * sum;
+    float p = inv[6];
+    for (int k = 5; k >= 0; --k) p = p * s2 + inv[k];
+    const float ln_u = (float)e * 0.693147182f + 2.0f * (s * p);
     return -ln_u;
 }
 
 /* The steps of one job from its n + 1 uniforms u[0..n] in (0, 1]:
- * exponential spacings E_k = -ln u_k, held as q_k = E_k 2^24 rounded
- * (binary32, then an integer, so the sums are exact in any order); the
- * exclusive running sums c_0 = 0, c_k = q_0 + ... + q_{k-1} (c_{n+1} the
- * total, which normalises); output k = 1..n: a + round(c_k / c_{n+1} M) +
- * (k - 1) with M = b - a - n, the added k - 1 keeping the values distinct
- * (binary32 ratio and product, rounded half up, at most M).  q and c may
- * be NULL.  Needs n <= b - a and M <= 2^24. */
+ * exponential spacings E_k = -ln u_k, held as q_k = E_k 2^22 rounded
+ * (binary32, then an integer: the sums are exact in any order, and 32 of
+ * them fit 32 bits); the exclusive running sums c_0 = 0, c_k = q_0 + ... +
+ * q_{k-1} (c_{n+1} the total, which normalises); output k = 1..n:
+ * a + round(c_k f) + (k - 1) with f = M / c_{n+1} in binary32, M = b - a - n
+ * (the added k - 1 keeps the values distinct; the rounding is half up, at
+ * most M).  q and c may be NULL.  Needs n <= b - a and M <= 2^24. */
 int orc_job_from_uniforms(const float* u, uint32_t n, uint32_t a, uint32_t b, uint32_t* q, uint64_t* c,
                           uint32_t* out)
 {
@@ -638,18 +639,15 @@ int orc_job_from_uniforms(const float* u, uint32_t n, uint32_t a, uint32_t b, ui
     if (!cc) return ORC_E_NOMEM;
     cc[0] = 0;
     for (uint32_t k = 0; k <= n; ++k) {
-        const uint32_t qk = (uint32_t)(orc_neg_ln(u[k]) * 16777216.0f + 0.5f);
+        const uint32_t qk = (uint32_t)(orc_neg_ln(u[k]) * 4194304.0f + 0.5f);
         if (q) q[k] = qk;
         cc[k + 1] = cc[k] + qk;
     }
     const uint64_t total = cc[n + 1];
+    const float f = total ? (float)M / (float)total : 0.0f;
     for (uint32_t k = 1; k <= n; ++k) {
-        uint32_t r = 0;
-        if (total) {
-            const float x = (float)cc[k] / (float)total * (float)M + 0.5f;
-            r = (uint32_t)x;
-            if (r > M) r = M;
-        }
+        uint32_t r = (uint32_t)((float)cc[k] * f + 0.5f);
+        if (r > M) r = M;
         out[k - 1] = a + r + (k - 1);
     }
     if (!c) free(cc);

@@ -39,7 +39,7 @@ def test_fig2_running_sum():
     the last spacing."""
     f = _fig2()
     q, c, _ = oracle.job_from_uniforms(f["a"][:7], 0, 100)
-    got = c.astype(np.float64) / 2**24
+    got = c.astype(np.float64) / 2**22
     assert got[0] == 0.0
     assert np.all(np.abs(got - np.array(f["c"])) <= 0.005 + 1e-6), got
 
