@@ -11,14 +11,16 @@
 // Philox4x64-10 with key (seed, job) and counter (k >> 3, 0, 2, 0), word
 // k & 7: u_k = ((word >> 8) + 1) 2^-24 in (0, 1].  The spacing -ln u_k is
 // computed in binary32 by this file's own logarithm (range reduction to
-// m in [1, 2) from the bits, ln m = 2 atanh s by its series to s^13, s =
-// (m - 1) / (m + 1)) and held as an integer q_k = round(-ln u_k 2^24), so
-// that the warp's running sums are exact in any order.  A first pass sums
-// the q_k of the job, a second one recomputes them, scans them across the
-// warp and writes value k = a + round(c_k / c_total (b - a - n)) + (k - 1),
-// c_k the exclusive running sum (binary32 ratio and product, at most
-// b - a - n).  Every operation is rounded as written (-fmad=false), so the
-// values do not depend on the launch.
+// m in [1, 2) from the bits, ln m = 2 s (1 + s^2/3 + ... + s^12/13) by
+// Horner's rule, s = (m - 1) / (m + 1)) and held as an integer q_k =
+// round(-ln u_k 2^22), so that running sums are exact in any order (and 32
+// of them fit 32 bits).  Pass 1 draws the spacings (a lane per Philox block
+// of 8), sums them and parks q_0 .. q_{n-1} in the job's own output slots
+// (through shared memory, so the stores are coalesced); pass 2 reads them
+// back 256 at a time, sums each lane's 8, scans the lanes' sums across the
+// warp and overwrites slot k with a + round(c_{k+1} f) + k, c the exclusive
+// running sum and f = (b - a - n) / total (binary32, at most b - a - n).  Every operation is rounded as
+// written (-fmad=false), so the values do not depend on the launch.
 #include <cuda_runtime.h>
 
 
@@ -40,13 +42,14 @@ __device__ __forceinline__ float neg_ln_f32(float u)
     const float m = __uint_as_float((bits & 0x7fffffu) | 0x3f800000u);
     const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
     const float s2 = __fmul_rn(s, s);
-    float t = s, sum = s;
-#pragma unroll
-    for (int k = 3; k <= 13; k += 2) {
-        t = __fmul_rn(t, s2);
-        sum = __fadd_rn(sum, __fdiv_rn(t, (float)k));
-    }
-    return -__fadd_rn(__fmul_rn(__int2float_rn(e), 0.693147182f), __fmul_rn(2.0f, sum));
+    float p = 1.0f / 13.0f;
+    p = __fadd_rn(__fmul_rn(p, s2), 1.0f / 11.0f);
+    p = __fadd_rn(__fmul_rn(p, s2), 1.0f / 9.0f);
+    p = __fadd_rn(__fmul_rn(p, s2), 1.0f / 7.0f);
+    p = __fadd_rn(__fmul_rn(p, s2), 1.0f / 5.0f);
+    p = __fadd_rn(__fmul_rn(p, s2), 1.0f / 3.0f);
+    p = __fadd_rn(__fmul_rn(p, s2), 1.0f);
+    return -__fadd_rn(__fmul_rn(__int2float_rn(e), 0.693147182f), __fmul_rn(2.0f, __fmul_rn(s, p)));
 }
 
 // the 8 integer spacings of Philox block g of job j (k = 8g .. 8g + 7)
@@ -57,22 +60,22 @@ __device__ __forceinline__ void spacings8(uint64_t seed, uint32_t j, uint32_t g,
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const float u = __fmul_rn(__uint2float_rn((w[i] >> 8) + 1u), 1.0f / 16777216.0f);
-        q[i] = __float2uint_rz(__fadd_rn(__fmul_rn(neg_ln_f32(u), 16777216.0f), 0.5f));
+        q[i] = __float2uint_rz(__fadd_rn(__fmul_rn(neg_ln_f32(u), 4194304.0f), 0.5f));
     }
 }
 
-__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
-{
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
+// a warp's 256 values in shared memory: value k (0..255) at (k / 8) 9 + k % 8,
+// so that lane l's 8 consecutive values and the 32 values of one coalesced
+// access both fall in (nearly) distinct banks
+__device__ __forceinline__ uint32_t stage_at(uint32_t k) { return (k >> 3) * 9u + (k & 7u); }
 
 __global__ void __launch_bounds__(kJobThreads) k_expand_jobs(const snn_job* __restrict__ jobs, uint64_t n_jobs,
                                                              uint64_t seed, uint32_t* __restrict__ out,
                                                              uint64_t out_len)
 {
+    __shared__ uint32_t stage[kJobThreads / 32][32 * 9];
     const uint32_t lane = threadIdx.x & 31u;
+    uint32_t* st = stage[threadIdx.x >> 5];
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t jj = warp; jj < n_jobs; jj += nwarps) {
@@ -84,56 +87,70 @@ __global__ void __launch_bounds__(kJobThreads) k_expand_jobs(const snn_job* __re
         }
         const uint32_t n = J.n, M = J.b - J.a - J.n;
         if (n == 0) continue;
-        // pass 1: the total of the n + 1 spacings; lane l takes block l of
-        // every 256 spacings
+        uint32_t* dst = out + J.o;
+        // pass 1: the total of the n + 1 spacings; q_0 .. q_{n-1} parked in
+        // the output (lane l draws block l of every 256 spacings)
         unsigned long long part = 0;
         for (uint64_t base = 0; base <= n; base += 256) {
             const uint32_t g = (uint32_t)(base >> 3) + lane;
-            if ((uint64_t)g * 8 > n) continue;
-            uint32_t q[8];
-            spacings8(seed, j, g, q);
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-                if ((uint64_t)g * 8 + i <= n) part += q[i];
-        }
-        const unsigned long long total = warp_sum(part);
-        const float ftotal = __ull2float_rn(total), fM = __uint2float_rn(M);
-        // pass 2: exclusive running sums and the values
-        unsigned long long carry = 0;
-        uint32_t* dst = out + J.o;
-        for (uint64_t base = 0; base <= n; base += 256) {
-            const uint32_t g = (uint32_t)(base >> 3) + lane;
             uint32_t q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            if ((uint64_t)g * 8 <= n) {
-                spacings8(seed, j, g, q);
+            if ((uint64_t)g * 8 <= n) spacings8(seed, j, g, q);
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    if ((uint64_t)g * 8 + i > n) q[i] = 0;
+            for (int i = 0; i < 8; ++i) {
+                if ((uint64_t)g * 8 + i > n) q[i] = 0;
+                part += q[i];
+                st[lane * 9 + i] = q[i];
             }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const uint64_t k = base + 32 * i + lane;
+                if (k < n) dst[k] = st[stage_at(32 * i + lane)];
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        const float f = part ? __fdiv_rn(__uint2float_rn(M), __ull2float_rn(part)) : 0.0f;
+        // pass 2, 256 at a time: lane l takes 8 consecutive spacings, sums
+        // them, and the lanes' sums are scanned across the warp; slot k gets
+        // a + round(c_{k+1} f) + k, c_{k+1} the running sum through q_k
+        unsigned long long carry = 0;
+        for (uint64_t base = 0; base < n; base += 256) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const uint64_t k = base + 32 * i + lane;
+                st[stage_at(32 * i + lane)] = k < n ? dst[k] : 0u;
+            }
+            __syncwarp();
+            uint32_t v[8];
             unsigned long long s8 = 0;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) s8 += q[i];
-            unsigned long long incl = s8;  // inclusive scan of the lanes' sums
+            for (int i = 0; i < 8; ++i) {
+                v[i] = st[lane * 9 + i];
+                s8 += v[i];
+            }
+            unsigned long long incl = s8;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= (uint32_t)o) incl += y;
             }
-            unsigned long long c = carry + incl - s8;  // c_k of the lane's first k
+            unsigned long long c = carry + incl - s8;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const uint64_t k = (uint64_t)g * 8 + i;
-                if (k >= 1 && k <= n) {
-                    uint32_t r = 0;
-                    if (total) {
-                        const float x = __fadd_rn(__fmul_rn(__fdiv_rn(__ull2float_rn(c), ftotal), fM), 0.5f);
-                        r = __float2uint_rz(x);
-                        r = r > M ? M : r;
-                    }
-                    dst[k - 1] = J.a + r + (uint32_t)(k - 1);
-                }
-                c += q[i];
+                c += v[i];  // c_{k+1}, k = base + 8 lane + i
+                uint32_t r = __float2uint_rz(__fadd_rn(__fmul_rn(__ull2float_rn(c), f), 0.5f));
+                r = r > M ? M : r;
+                st[lane * 9 + i] = J.a + r + (uint32_t)(base + 8 * lane + i);
             }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const uint64_t k = base + 32 * i + lane;
+                if (k < n) dst[k] = st[stage_at(32 * i + lane)];
+            }
+            __syncwarp();
             carry += __shfl_sync(0xffffffffu, incl, 31);
         }
     }
