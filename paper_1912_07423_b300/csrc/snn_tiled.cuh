@@ -160,7 +160,7 @@ __device__ __forceinline__ uint16_t ld_edge16(const int16_t* ptr, unsigned long 
 // weight codes and u32 targets, or one u32 per edge holding the target's
 // offset in its instance (high half) and the int16 code (low half).
 enum : int { kWF32 = 0, kW16 = 1, kWPacked = 2 };
-__host__ __device__ constexpr int vec_of(int wm) { return wm == kWPacked ? 8 : kVec; }
+__host__ __device__ constexpr int vec_of(int wm) { return wm == kWPacked ? 6 : kVec; }
 __host__ __device__ constexpr uint32_t edge_bytes_of(int wm) { return wm == kWF32 ? 8u : (wm == kW16 ? 6u : 4u); }
 
 // Adds the edges [sb, se) of one row into the tile's accumulators a (one
