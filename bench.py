@@ -383,9 +383,13 @@ def run_ours(args, rank, world, dist):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         net = snn.Network(prob, w16=True, receive=recv_mode, log_capacity=cap)  # h2d of the graph
+        t1 = time.perf_counter()
         net.step(args.steps)
+        net.sync()
+        t2 = time.perf_counter()
         steps_h, ids_h = net.spikes()  # d2h of the raster
         t_e2e = time.perf_counter() - t0
+        parts = {"create_and_build_s": t1 - t0, "steps_s": t2 - t1, "raster_readout_s": t0 + t_e2e - t2}
         c = net.counters()
         net.close()
         del net
@@ -394,7 +398,8 @@ def run_ours(args, rank, world, dist):
         d2h = 8 * int(c["spikes"])
         out["e2e"] = {"value": sum_over_ranks(c["events"]) / max_over_ranks(t_e2e), "unit": "synaptic events/s",
                       "seconds": t_e2e, "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-                      "includes": "snn_create + snn_build_graph from host arrays + snn_step(K) + snn_read_spikes"}
+                      "includes": "snn_create + snn_build_graph from host arrays + snn_step(K) + snn_read_spikes",
+                      "parts": parts}
 
     # ---- adjacency construction on the GPU (Fig. 2) for the same networks
     if not args.no_graph:

@@ -21,6 +21,8 @@
 #include "snn_tiled.cuh"
 #include "snn_bulk.cuh"
 
+#include <cub/device/device_radix_sort.cuh>
+
 using namespace snn;
 
 struct snn_ctx {
@@ -163,10 +165,11 @@ int poisson_table(double lambda, uint32_t* T, int cap)
     return -1;
 }
 
-InstDev make_inst(const snn_params& p, uint32_t pbase, uint32_t pois_off, int pois_n)
+InstDev make_inst(const snn_params& p, uint32_t pbase, uint32_t goff, uint32_t pois_off, int pois_n)
 {
     InstDev d{};
     d.pbase = pbase;
+    d.goff = goff;
     d.n = p.n;
     d.n_exc = p.n_exc;
     d.R = p.refractory_steps;
@@ -508,7 +511,7 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     for (uint32_t b = 0; b < cfg->n_inst; ++b) {
         int np = 0;
         if (cfg->model == SNN_BRUNEL) np = poisson_table(params[b].lambda, &hpois[(size_t)b * kPoissonCap], kPoissonCap);
-        hinst[b] = make_inst(params[b], c->pbase[b], b * kPoissonCap, np);
+        hinst[b] = make_inst(params[b], c->pbase[b], c->g_off[b], b * kPoissonCap, np);
     }
     // bucket table of every instance: thresholds below each 2^24 boundary
     std::vector<uint8_t> hstart((size_t)cfg->n_inst * kPoissonBuckets, 0);
@@ -914,29 +917,69 @@ snn_status snn_read_spikes(snn_ctx* c, uint32_t t0, uint32_t t1, uint32_t* steps
         total = lb + cnt;
     }
     const uint64_t avail = std::min<uint64_t>(total, c->cfg.log_capacity);
-    std::vector<unsigned long long> L(avail);
-    if (avail) CUDA_TRY(c, cudaMemcpy(L.data(), c->net.log, avail * 8, cudaMemcpyDeviceToHost));
-    std::vector<std::pair<uint32_t, uint32_t>> out;
-    out.reserve(avail);
-    for (uint64_t k = 0; k < avail; ++k) {
-        const uint32_t st = (uint32_t)(L[k] >> 32), pid = (uint32_t)L[k];
-        if (st < t0 || st >= t1) continue;
-        const auto it = std::upper_bound(c->pbase.begin(), c->pbase.end(), pid);
-        const uint32_t b = (uint32_t)(it - c->pbase.begin()) - 1;
-        out.emplace_back(st, pid - c->pbase[b] + c->g_off[b]);
-    }
-    std::sort(out.begin(), out.end());
-    *n_out = out.size();
+    // the log is in step order (steps append at increasing bases), so the
+    // entries of steps [t0, t1) are one range of it, found by bisection
+    auto first_at = [&](uint64_t t, uint64_t* idx) -> snn_status {
+        uint64_t lo = 0, hi = avail;
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) / 2;
+            unsigned long long v = 0;
+            CUDA_TRY(c, cudaMemcpy(&v, c->net.log + mid, 8, cudaMemcpyDeviceToHost));
+            if ((v >> 32) < t)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        *idx = lo;
+        return SNN_OK;
+    };
+    uint64_t lo = 0, hi = 0;
+    snn_status st = first_at(t0, &lo);
+    if (st == SNN_OK) st = first_at(t1, &hi);
+    if (st != SNN_OK) return st;
+    const uint64_t n = hi > lo ? hi - lo : 0;
+    *n_out = n;
     if (total > c->cfg.log_capacity)
         return fail(c, SNN_E_OVERFLOW, "the spike log overflowed (%llu spikes, capacity %llu)",
                     (unsigned long long)total, (unsigned long long)c->cfg.log_capacity);
-    if (cap == 0) return SNN_OK;
-    if (cap < out.size()) return fail(c, SNN_E_OVERFLOW, "output capacity %llu < %llu spikes", (unsigned long long)cap,
-                                      (unsigned long long)out.size());
-    for (size_t k = 0; k < out.size(); ++k) {
-        steps[k] = out[k].first;
-        ids[k] = out[k].second;
+    if (cap == 0 || n == 0) return SNN_OK;
+    if (cap < n) return fail(c, SNN_E_OVERFLOW, "output capacity %llu < %llu spikes", (unsigned long long)cap,
+                            (unsigned long long)n);
+    // keys (step - t0) << 32 | global id, radix-sorted on the device, split
+    // into the two output arrays
+    const uint64_t t_hi = std::min<uint64_t>(t1, h.t);
+    int end_bit = 32;
+    while (end_bit < 64 && (t_hi - t0) >= (1ull << (end_bit - 32))) ++end_bit;
+    unsigned long long* ka = alloc_n<unsigned long long>(c, n);
+    unsigned long long* kb = alloc_n<unsigned long long>(c, n);
+    size_t tmp_bytes = 0;
+    cub::DoubleBuffer<unsigned long long> db(ka, kb);
+    void* tmp = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (ka && kb) {
+        k_raster_keys<<<grid_for(n, 256), 256, 0, c->stream>>>(c->net, c->net.log + lo, n, t0, ka);
+        e = cub::DeviceRadixSort::SortKeys(nullptr, tmp_bytes, db, (int64_t)n, 0, end_bit, c->stream);
+        if (e == cudaSuccess) tmp = dev_alloc(c, std::max<size_t>(tmp_bytes, 16));
     }
+    if (!ka || !kb || !tmp) {
+        dev_free(c, ka);
+        dev_free(c, kb);
+        dev_free(c, tmp);
+        return fail(c, e == cudaSuccess ? SNN_E_NOMEM : SNN_E_CUDA, "raster sort buffers");
+    }
+    e = cub::DeviceRadixSort::SortKeys(tmp, tmp_bytes, db, (int64_t)n, 0, end_bit, c->stream);
+    uint32_t* split = reinterpret_cast<uint32_t*>(db.Alternate());  // steps then ids, n each
+    if (e == cudaSuccess) {
+        k_raster_split<<<grid_for(n, 256), 256, 0, c->stream>>>(db.Current(), n, t0, split, split + n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(steps, split, n * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ids, split + n, n * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, tmp);
+    dev_free(c, ka);
+    dev_free(c, kb);
+    if (e != cudaSuccess) return fail(c, SNN_E_CUDA, "raster readout: %s", cudaGetErrorString(e));
     return SNN_OK;
 }
 

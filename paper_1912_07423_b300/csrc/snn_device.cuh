@@ -39,6 +39,7 @@ enum : uint32_t {
 // rounded once (see snn_params in snn.h).
 struct InstDev {
     uint32_t pbase, n, n_exc, R;
+    uint32_t goff, pad;  // first global neuron id of the instance
     int32_t jext, wmax;
     uint32_t pois_off, pois_n;
     float Pm, Pe, Pi, Pp, Pn, Ap, Am;

@@ -282,6 +282,30 @@ __global__ void __launch_bounds__(256) k_update(Net n)
     }
 }
 
+// Raster readout: log entries (step << 32 | padded id) -> sortable keys
+// (step - t0) << 32 | global id.
+__global__ void k_raster_keys(Net n, const unsigned long long* __restrict__ log, uint64_t count, uint64_t t0,
+                              unsigned long long* __restrict__ keys)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned long long v = log[i];
+        const uint32_t pid = (uint32_t)v;
+        const InstDev& I = n.inst[n.inst_of_w32[pid >> 5]];
+        keys[i] = (((v >> 32) - t0) << 32) | (unsigned long long)(pid - I.pbase + I.goff);
+    }
+}
+
+// Sorted keys -> steps and global ids.
+__global__ void k_raster_split(const unsigned long long* __restrict__ keys, uint64_t count, uint64_t t0,
+                               uint32_t* __restrict__ steps, uint32_t* __restrict__ ids)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = keys[i];
+        steps[i] = (uint32_t)((k >> 32) + t0);
+        ids[i] = (uint32_t)k;
+    }
+}
+
 // The step counter advances once per captured graph (the kernels of a graph
 // carry their offset inside it); the per-step bookkeeping is done by the
 // next step's update kernel.
