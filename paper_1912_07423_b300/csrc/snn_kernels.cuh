@@ -23,6 +23,10 @@ constexpr unsigned kFull = 0xffffffffu;
 // ---------------------------------------------------------------------------
 
 constexpr int kUpdateNeurons = 8;  // neurons per thread of the update (4 or 8)
+// a warp of the update covers 32 * kUpdateNeurons neurons and must never
+// cross an instance (instances are padded to 256 slots): its spikes go to
+// one instance's queue region with one atomicAdd
+static_assert(256 % (32 * kUpdateNeurons) == 0, "a warp of the update must stay inside one 256-slot block");
 
 // Number of Poisson thresholds <= u (thresholds T[0..nT) ascending): the
 // instance's bucket table S gives the count below the start of u's bucket
