@@ -13,6 +13,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/snn.h"
@@ -366,6 +367,53 @@ snn_status pack_edges(snn_ctx* c)
     return SNN_OK;
 }
 
+// Host -> device copy of a large pageable array: chunks are copied into a
+// ring of pinned buffers by several host threads while the DMA engine
+// moves the previous chunks (the driver's own staging of pageable memory
+// copies with one thread).  Waits for the stream.
+snn_status upload(snn_ctx* c, void* dst, const void* src, size_t bytes, cudaStream_t s)
+{
+    constexpr size_t kChunk = 64u << 20;
+    constexpr int kBufs = 4;
+    if (bytes <= kChunk) {
+        CUDA_TRY(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+        return SNN_OK;
+    }
+    const unsigned hw = std::thread::hardware_concurrency();
+    const unsigned nth = std::max(1u, std::min(16u, hw ? hw : 1u));
+    void* buf[kBufs] = {};
+    cudaEvent_t done[kBufs] = {};
+    snn_status st = SNN_OK;
+    for (int i = 0; i < kBufs && st == SNN_OK; ++i)
+        if (cudaHostAlloc(&buf[i], kChunk, cudaHostAllocDefault) != cudaSuccess ||
+            cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming) != cudaSuccess)
+            st = fail(c, SNN_E_CUDA, "pinned staging buffers");
+    for (size_t off = 0, i = 0; off < bytes && st == SNN_OK; off += kChunk, i = (i + 1) % kBufs) {
+        const size_t len = std::min(kChunk, bytes - off);
+        if (cudaEventSynchronize(done[i]) != cudaSuccess) {
+            st = fail(c, SNN_E_CUDA, "staging wait");
+            break;
+        }
+        const char* from = static_cast<const char*>(src) + off;
+        char* to = static_cast<char*>(buf[i]);
+        const size_t part = (len / nth + 63) & ~size_t(63);
+        std::vector<std::thread> pool;
+        for (unsigned t = 1; t < nth && t * part < len; ++t)
+            pool.emplace_back([=]() { std::memcpy(to + t * part, from + t * part, std::min(part, len - t * part)); });
+        std::memcpy(to, from, std::min(part, len));
+        for (auto& th : pool) th.join();
+        if (cudaMemcpyAsync(static_cast<char*>(dst) + off, buf[i], len, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaEventRecord(done[i], s) != cudaSuccess)
+            st = fail(c, SNN_E_CUDA, "staged copy");
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess && st == SNN_OK) st = fail(c, SNN_E_CUDA, "staged copy");
+    for (int i = 0; i < kBufs; ++i) {
+        if (done[i]) cudaEventDestroy(done[i]);
+        if (buf[i]) cudaFreeHost(buf[i]);
+    }
+    return st;
+}
+
 // Cut the tiles of the tiled receive; work[b] = expected delivered edges of
 // instance b per step (null: proportional to its synapses).
 snn_status plan_tiles(snn_ctx* c, const double* work)
@@ -694,8 +742,12 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
     CUDA_TRY(c, cudaMemcpyAsync(dpb, c->pbase.data(), c->pbase.size() * 4, cudaMemcpyHostToDevice, s));
     CUDA_TRY(c, cudaMemcpyAsync(dnexc, hnexc.data(), hnexc.size() * 4, cudaMemcpyHostToDevice, s));
     if (E) {
-        CUDA_TRY(c, cudaMemcpyAsync(c->tgt, tgt_h, E * 4, cudaMemcpyHostToDevice, s));
-        CUDA_TRY(c, cudaMemcpyAsync(wtmp, w_q, E * 4, cudaMemcpyHostToDevice, s));
+        snn_status up = upload(c, c->tgt, tgt_h, E * 4, s);
+        if (up == SNN_OK) up = upload(c, wtmp, w_q, E * 4, s);
+        if (up != SNN_OK) {
+            cleanup_tmp();
+            return up;
+        }
     }
     CUDA_TRY(c, cudaMemsetAsync(&c->ctl->err, 0, sizeof(unsigned int), s));
     CUDA_TRY(c, cudaMemsetAsync(dunsorted, 0, sizeof(unsigned int), s));
