@@ -44,12 +44,13 @@ B_NEURON = {si.BRUNEL: 18, si.VOGELS: 44}
 B_NEURON_STDP = 16
 
 
-def gpu_launches(steps: int, recv_kind: str, stdp: bool, per_graph: int = 16) -> int:
+def gpu_launches(steps: int, recv_kind: str, stdp: bool, lazy: bool = False, per_graph: int = 16) -> int:
     """Kernels of this library launched by `steps` steps of snn_step: the
-    update, the two STDP passes, the receive (tiled: per-step plan and
-    receive; bulk: receive, merge; global: receive), and one step-counter
-    advance per captured graph (per_graph steps, the rest one by one)."""
-    per_step = 1 + (2 if stdp else 0) + {"tiled": 2, "bulk": 2, "global": 1}[recv_kind]
+    update, the STDP passes (eager: depression and potentiation; lazy: one
+    replay pass), the receive (tiled: per-step plan and receive; bulk:
+    receive, merge; global: receive), and one step-counter advance per
+    captured graph (per_graph steps, the rest one by one)."""
+    per_step = 1 + ((1 if lazy else 2) if stdp else 0) + {"tiled": 2, "bulk": 2, "global": 1}[recv_kind]
     return steps * per_step + steps // per_graph + steps % per_graph
 
 def kernel_source_hash() -> str:
@@ -303,7 +304,8 @@ def run_ours(args, rank, world, dist):
     # ---- headline: batched + int16, timed on the device
     recv_mode = {"auto": snn.RECV_AUTO, "global": snn.RECV_GLOBAL, "tiled": snn.RECV_TILED,
                  "bulk": snn.RECV_BULK}[args.receive]
-    net = snn.Network(prob, w16=True, receive=recv_mode, log_capacity=cap)
+    lazy = prob.stdp and args.plasticity == "lazy"
+    net = snn.Network(prob, w16=True, receive=recv_mode, log_capacity=cap, lazy=lazy, lazy_fifo=args.lazy_fifo)
     info = net.info()
     recv_kind = info["receive"]
     net.step(args.warmup)
@@ -347,7 +349,9 @@ def run_ours(args, rank, world, dist):
                       "edge_bytes": info["edge_bytes"],
                       "l2": "inputs larger than L2 (edge arrays %.1f GB >> 126 MB)" % (prob.n_edges * 6 / 1e9),
                       "parallelism": f"replicas x{world} (independent networks, no collective)",
-                      "graph_gen_s": round(t_gen, 1), "device_bytes": mem},
+                      "graph_gen_s": round(t_gen, 1), "device_bytes": mem,
+                      **({"plasticity": ("lazy, history %d steps" % (args.lazy_fifo or 50)) if lazy else "eager"}
+                         if prob.stdp else {})},
            "realtime_factor": args.steps * DT_MS * 1e-3 / t_max,
            "spikes": int(sp_main), "events": int(ev_main),
            "roofline": {"kernel": f"k_receive_{recv_kind}", "bound": "hbm", "achieved": achieved, "peak": hbm,
@@ -359,12 +363,13 @@ def run_ours(args, rank, world, dist):
            "step_roofline": {"bytes_per_step": step_b / args.steps, "frac": step_frac, "peak": hbm,
                              "unit": "GB/s", "achieved": step_b / t_main / 1e9},
            "phase_ms_per_step": {k: v / n_prof for k, v in phases.items()},
-           "gpu_launches": gpu_launches(args.steps, recv_kind, prob.stdp),
+           "gpu_launches": gpu_launches(args.steps, recv_kind, prob.stdp, lazy),
            "clocks": clk}
 
     # ---- plain single-precision weights + global-atomic receive, same networks
     if not args.no_plain:
-        net = snn.Network(prob, w16=False, receive=snn.RECV_GLOBAL, log_capacity=cap)
+        net = snn.Network(prob, w16=False, receive=snn.RECV_GLOBAL, log_capacity=cap, lazy=lazy,
+                          lazy_fifo=args.lazy_fifo)
         net.step(args.warmup)
         net.sync()
         t_pl, ev_pl, sp_pl = timed(net, args.steps)
@@ -382,7 +387,8 @@ def run_ours(args, rank, world, dist):
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        net = snn.Network(prob, w16=True, receive=recv_mode, log_capacity=cap)  # h2d of the graph
+        net = snn.Network(prob, w16=True, receive=recv_mode, log_capacity=cap, lazy=lazy,
+                          lazy_fifo=args.lazy_fifo)  # h2d of the graph
         t1 = time.perf_counter()
         net.step(args.steps)
         net.sync()
@@ -440,6 +446,9 @@ def main():
     ap.add_argument("--workload", default="batched_sweep_256")
     ap.add_argument("--profile-steps", type=int, default=500)
     ap.add_argument("--receive", choices=["auto", "global", "tiled", "bulk"], default="auto")
+    ap.add_argument("--plasticity", choices=["eager", "lazy"], default="eager",
+                    help="Update Synapses form for plastic workloads (brunel_stdp_100k)")
+    ap.add_argument("--lazy-fifo", type=int, default=0, help="lazy plasticity: history length (0: 50)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -68,6 +68,11 @@ typedef enum {
 #define SNN_F_UNPACKED 8u /* tiled receive: read the u32 target and int16 code arrays even where the
                              packed layout applies (SNN_F_W16, no STDP, every instance of at most
                              65,536 neurons: one u32 per edge, target offset << 16 | code) */
+#define SNN_F_LAZY 16u /* with SNN_F_STDP: lazy Update Synapses (Section III-A-1).  The plastic
+                          synapses of a row are left stale and brought up to date in one pass
+                          when the row transmits a spike or when its age reaches the history
+                          length lazy_fifo; the weights and traces are the eager rule's, bit for
+                          bit (snn_read_state / snn_write_state bring every row up to date first) */
 
 /* snn_config.receive */
 #define SNN_RECV_AUTO 0u   /* the library picks: tiled when the rows are sorted, else global */
@@ -89,7 +94,8 @@ typedef struct {
                               counts measured since the previous cut (0: 256, 0xffffffff:
                               never); the tiled receive cuts its items on the device every
                               step.  Results do not depend on the plan */
-    uint32_t reserved;
+    uint32_t lazy_fifo;    /* SNN_F_LAZY: steps of spike and trace history kept per neuron, the
+                              longest a row stays stale (0: 50, else 2..64) */
 } snn_config;
 
 /* Model constants of one instance.  Times in ms, potentials in mV, integer
@@ -126,8 +132,9 @@ typedef struct {
  * The instances are concatenated in order: global neuron id = sum of the
  * sizes of the earlier instances + local id.  Returns SNN_E_ARG for an
  * invalid config (delay 0 or > 1000, refractory > 255, STDP without
- * Brunel, non-positive time constants, lambda < 0 or so large that the
- * Poisson table would exceed 64 entries).  *out is NULL on failure. */
+ * Brunel, SNN_F_LAZY without SNN_F_STDP or lazy_fifo outside 2..64,
+ * non-positive time constants, lambda < 0 or so large that the Poisson
+ * table would exceed 64 entries).  *out is NULL on failure. */
 snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn_device* dev,
                       snn_ctx** out);
 
@@ -196,7 +203,9 @@ typedef enum {
 
 /* Copy a state field to / from host memory (synchronises).  Writing takes
  * effect before the next step; it is how tests force a spike.  The queues
- * of the delay FIFO are not part of these fields. */
+ * of the delay FIFO are not part of these fields.  With SNN_F_LAZY, reading
+ * or writing W or X first brings every stale row up to date (a pass over
+ * the plastic rows; the values are those of the eager rule). */
 snn_status snn_read_state(snn_ctx* ctx, snn_field field, void* host);
 snn_status snn_write_state(snn_ctx* ctx, snn_field field, const void* host);
 

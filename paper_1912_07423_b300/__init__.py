@@ -17,10 +17,10 @@ import numpy as np
 from .build import LIB, build as _build
 
 __all__ = ["Network", "SnnError", "load", "VOGELS", "BRUNEL", "RECV_AUTO", "RECV_GLOBAL", "RECV_TILED", "RECV_BULK",
-           "F_STDP", "F_W16", "F_STATS", "F_UNPACKED", "FIELDS"]
+           "F_STDP", "F_W16", "F_STATS", "F_UNPACKED", "F_LAZY", "FIELDS"]
 
 VOGELS, BRUNEL = 0, 1
-F_STDP, F_W16, F_STATS, F_UNPACKED = 1, 2, 4, 8
+F_STDP, F_W16, F_STATS, F_UNPACKED, F_LAZY = 1, 2, 4, 8, 16
 RECV_AUTO, RECV_GLOBAL, RECV_TILED, RECV_BULK = 0, 1, 2, 3
 FIELDS = {"V": 0, "ge": 1, "gi": 2, "r": 3, "x": 4, "y": 5, "acc0": 6, "acc1": 7, "w": 8}
 _FIELD_DTYPE = {"V": np.float32, "ge": np.float32, "gi": np.float32, "r": np.int32, "x": np.float32,
@@ -41,7 +41,7 @@ class Config(ctypes.Structure):
     _fields_ = [("model", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("delay", ctypes.c_uint32),
                 ("n_inst", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("log_capacity", ctypes.c_uint64),
                 ("receive", ctypes.c_uint32), ("steps_per_graph", ctypes.c_uint32), ("tune_steps", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("lazy_fifo", ctypes.c_uint32)]
 
 
 class Params(ctypes.Structure):
@@ -193,7 +193,8 @@ class Network:
 
     def __init__(self, problem, *, w16: bool = True, receive: int = RECV_AUTO, log_capacity: int | None = None,
                  stats: bool = False, steps_per_graph: int = 0, tune_steps: int = 0, device: str = "cuda:0",
-                 stream=None, build_graph: bool = True, packed: bool = True):
+                 stream=None, build_graph: bool = True, packed: bool = True, lazy: bool = False,
+                 lazy_fifo: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise SnnError(-3, "no CUDA device: libsnn has no CPU fallback")
@@ -205,11 +206,11 @@ class Network:
         self.mem = _TorchMemory(self.device)
         self.dev = Device(self.mem.alloc_cb, self.mem.free_cb, None, self.stream.cuda_stream)
         flags = (F_STDP if problem.stdp else 0) | (F_W16 if w16 else 0) | (F_STATS if stats else 0) | \
-            (0 if packed else F_UNPACKED)
+            (0 if packed else F_UNPACKED) | (F_LAZY if lazy else 0)
         if log_capacity is None:
             log_capacity = max(1 << 16, int(problem.n) * 64)
         self.cfg = Config(problem.model, flags, problem.delay, len(problem.instances), problem.seed, log_capacity,
-                          receive, steps_per_graph, tune_steps, 0)
+                          receive, steps_per_graph, tune_steps, lazy_fifo)
         self.params = _params_array(problem.instances)
         ctx = _vp()
         st = self.lib.snn_create(ctypes.byref(self.cfg), ctypes.addressof(self.params), ctypes.byref(self.dev),

@@ -42,6 +42,7 @@ struct snn_ctx {
     std::vector<uint32_t> g_off;   // global instance offsets (n_inst+1)
     std::vector<uint32_t> pbase;   // padded bases (n_inst+1)
     bool vogels = false, stdp = false, w16 = false, stats = false;
+    bool lazy = false;             // lazy Update Synapses (SNN_F_LAZY)
     bool graph_loaded = false;
     uint64_t host_steps = 0;       // steps enqueued since reset
 
@@ -224,7 +225,10 @@ snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr, u
         CUDA_TRY(c, enqueue_tiled_plan(c->tiled, n, c->side));
         CUDA_TRY(c, cudaEventRecord(c->ev_join, c->side));
     }
-    if (c->stdp) {
+    // eager plasticity: depression before the update, potentiation after it;
+    // lazy: one replay pass after the update over the transmitting and the
+    // expiring rows
+    if (c->stdp && !c->lazy) {
         if (c->w16)
             k_stdp_depress<true><<<wblocks, 256, 0, s>>>(n);
         else
@@ -233,22 +237,32 @@ snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr, u
     if (ev) cudaEventRecord(ev[1], s);
     if (c->vogels) {
         if (c->stats)
-            k_update<0, false, true><<<ublocks, 256, 0, s>>>(n);
+            k_update<0, 0, true><<<ublocks, 256, 0, s>>>(n);
         else
-            k_update<0, false, false><<<ublocks, 256, 0, s>>>(n);
+            k_update<0, 0, false><<<ublocks, 256, 0, s>>>(n);
+    } else if (c->lazy) {
+        if (c->stats)
+            k_update<1, 2, true><<<ublocks, 256, 0, s>>>(n);
+        else
+            k_update<1, 2, false><<<ublocks, 256, 0, s>>>(n);
     } else if (c->stdp) {
         if (c->stats)
-            k_update<1, true, true><<<ublocks, 256, 0, s>>>(n);
+            k_update<1, 1, true><<<ublocks, 256, 0, s>>>(n);
         else
-            k_update<1, true, false><<<ublocks, 256, 0, s>>>(n);
+            k_update<1, 1, false><<<ublocks, 256, 0, s>>>(n);
     } else {
         if (c->stats)
-            k_update<1, false, true><<<ublocks, 256, 0, s>>>(n);
+            k_update<1, 0, true><<<ublocks, 256, 0, s>>>(n);
         else
-            k_update<1, false, false><<<ublocks, 256, 0, s>>>(n);
+            k_update<1, 0, false><<<ublocks, 256, 0, s>>>(n);
     }
     if (ev) cudaEventRecord(ev[2], s);
-    if (c->stdp) {
+    if (c->lazy) {
+        if (c->w16)
+            k_stdp_lazy<true><<<wblocks, 256, 0, s>>>(n);
+        else
+            k_stdp_lazy<false><<<wblocks, 256, 0, s>>>(n);
+    } else if (c->stdp) {
         if (c->w16)
             k_stdp_potentiate<true><<<wblocks, 256, 0, s>>>(n);
         else
@@ -320,16 +334,40 @@ snn_status check_device_errors(snn_ctx* c)
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     if (err & kErrTimeout) return fail(c, SNN_E_TIMEOUT, "a bounded device-side wait gave up");
     if (err & kErrPlan) return fail(c, SNN_E_OVERFLOW, "the receive plan of a step did not fit its buffer");
+    if (err & kErrLazyAge) return fail(c, SNN_E_STATE, "a lazily updated row outlived its spike history");
     if (err & kErrLogOverflow)
         return fail(c, SNN_E_OVERFLOW, "the spike log is full (log_capacity = %llu)",
                     (unsigned long long)c->cfg.log_capacity);
     return SNN_OK;
 }
 
+// Lazy plasticity: bring every stale row up to date after the last step,
+// before the weights or the presynaptic traces are read or written.
+snn_status lazy_flush(snn_ctx* c)
+{
+    if (!c->lazy) return SNN_OK;
+    unsigned long long t = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&t, &c->ctl->t, sizeof t, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (t == 0) return SNN_OK;
+    Net n = c->net;
+    n.k = 0;
+    const uint32_t blocks = (uint32_t)sm_count() * 8;
+    if (c->w16)
+        k_stdp_flush<true><<<blocks, 256, 0, c->stream>>>(n, t - 1);
+    else
+        k_stdp_flush<false><<<blocks, 256, 0, c->stream>>>(n, t - 1);
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return SNN_OK;
+}
+
 snn_status init_state(snn_ctx* c)
 {
-    k_init_state<<<grid_for(c->Np / 4, 256), 256, 0, c->stream>>>(c->net, c->vogels ? 1 : 0, c->stdp ? 1 : 0);
+    k_init_state<<<grid_for(c->Np / 4, 256), 256, 0, c->stream>>>(c->net, c->vogels ? 1 : 0, c->stdp ? 1 : 0,
+                                                                   c->lazy ? 1 : 0);
     CUDA_TRY(c, cudaGetLastError());
+    if (c->lazy) CUDA_TRY(c, cudaMemsetAsync(c->net.xcount, 0, 2 * sizeof(unsigned int), c->stream));
     // control block: step 0, empty queues and log
     CUDA_TRY(c, cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), c->stream));
     if (c->stdp)
@@ -503,6 +541,9 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     if (!cfg || !params || cfg->n_inst == 0) return SNN_E_ARG;
     if (cfg->model > SNN_BRUNEL || cfg->delay < 1 || cfg->delay > 1000) return SNN_E_ARG;
     if ((cfg->flags & SNN_F_STDP) && cfg->model != SNN_BRUNEL) return SNN_E_ARG;
+    if ((cfg->flags & SNN_F_LAZY) &&
+        (!(cfg->flags & SNN_F_STDP) || cfg->lazy_fifo == 1 || cfg->lazy_fifo > (uint32_t)kLazyMaxF))
+        return SNN_E_ARG;
     if (cfg->receive > SNN_RECV_BULK) return SNN_E_ARG;
     uint64_t N = 0, Np = 0;
     for (uint32_t b = 0; b < cfg->n_inst; ++b) {
@@ -528,6 +569,7 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     c->stream = (cudaStream_t)c->dev.stream;
     c->vogels = cfg->model == SNN_VOGELS_CUBA;
     c->stdp = (cfg->flags & SNN_F_STDP) != 0;
+    c->lazy = c->stdp && (cfg->flags & SNN_F_LAZY) != 0;
     c->w16 = (cfg->flags & SNN_F_W16) != 0;
     c->stats = (cfg->flags & SNN_F_STATS) != 0;
     c->N = (uint32_t)N;
@@ -614,6 +656,15 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
         n.y = alloc_n<float>(c, Npz);
         n.bits = alloc_n<uint32_t>(c, (size_t)c->D * (Npz / 32));
         ok = ok && n.x && n.y && n.bits;
+    }
+    if (c->lazy) {
+        n.F = cfg->lazy_fifo ? cfg->lazy_fifo : 50;
+        n.hist = alloc_n<unsigned long long>(c, Npz);
+        n.yring = alloc_n<float>(c, (size_t)n.F * Npz);
+        n.age = alloc_n<uint32_t>(c, Npz);
+        n.xq = alloc_n<uint32_t>(c, Npz);
+        n.xcount = alloc_n<unsigned int>(c, 2);
+        ok = ok && n.hist && n.yring && n.age && n.xq && n.xcount;
     }
     if (c->stats) {
         n.st_cnt = alloc_n<uint32_t>(c, Npz);
@@ -773,7 +824,8 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
     }
 
     // STDP column index: plastic in-edges (exc -> exc) of every padded post id
-    if (c->stdp) {
+    // (eager potentiation only; the lazy replay walks rows)
+    if (c->stdp && !c->lazy) {
         std::vector<uint64_t> hcoff((size_t)Np + 1, 0);
         for (uint32_t b = 0; b < c->cfg.n_inst; ++b)
             for (uint32_t jl = 0; jl < c->params[b].n_exc; ++jl) {
@@ -1076,6 +1128,10 @@ snn_status snn_read_state(snn_ctx* c, snn_field f, void* host)
     if (!c || !host) return SNN_E_ARG;
     if (!c->graph_loaded) return fail(c, SNN_E_STATE, "no graph loaded");
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (f == SNN_FIELD_W || f == SNN_FIELD_X) {
+        snn_status st = lazy_flush(c);
+        if (st != SNN_OK) return st;
+    }
     if (f == SNN_FIELD_W) {
         int32_t* tmp = alloc_n<int32_t>(c, c->E);
         if (!tmp) return fail(c, SNN_E_NOMEM, "temporary weight buffer");
@@ -1111,6 +1167,10 @@ snn_status snn_write_state(snn_ctx* c, snn_field f, const void* host)
     if (!c || !host) return SNN_E_ARG;
     if (!c->graph_loaded) return fail(c, SNN_E_STATE, "no graph loaded");
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (f == SNN_FIELD_W || f == SNN_FIELD_X) {
+        snn_status st = lazy_flush(c);
+        if (st != SNN_OK) return st;
+    }
     if (f == SNN_FIELD_W) {
         int32_t* tmp = alloc_n<int32_t>(c, c->E);
         if (!tmp) return fail(c, SNN_E_NOMEM, "temporary weight buffer");

@@ -40,7 +40,9 @@ __device__ __forceinline__ uint32_t poisson_count(const uint32_t* __restrict__ T
     return k;
 }
 
-template <int MODEL, bool STDP, bool STATS>
+// SYN: 0 no plasticity, 1 eager traces (x and y every step), 2 lazy (y, the
+// ring of decayed y, the spike history and the expiry queue)
+template <int MODEL, int SYN, bool STATS>
 __global__ void __launch_bounds__(256) k_update(Net n)
 {
     constexpr int NPT = kUpdateNeurons;  // neurons per thread
@@ -59,6 +61,7 @@ __global__ void __launch_bounds__(256) k_update(Net n)
             if (t > 0) n.ctl->spikes += n.count[(t - 1) & (n.cr - 1)];
             n.count[sn] = 0;
             n.tile_ctr[(t + 1) & 1ull] = 0;
+            if (SYN == 2) n.xcount[(t + 1) & 1ull] = 0;
         }
     }
     // a receive launched as this kernel's programmatic dependent may start
@@ -69,6 +72,7 @@ __global__ void __launch_bounds__(256) k_update(Net n)
     const bool active = g < G;  // whole warps: Np is a multiple of 256
     const uint32_t id0 = g * NPT;
     uint32_t spk = 0;  // bit k: neuron id0 + k spiked
+    uint32_t xexp = 0;  // lazy plasticity, bit k: the row of id0 + k expires at this step
     bool have = false;  // the group holds neurons (not only padding): its state is stored
     // the state is loaded first: its addresses do not depend on the instance
     // (padding slots are loaded too and left as they are)
@@ -165,7 +169,7 @@ __global__ void __launch_bounds__(256) k_update(Net n)
                     V[k] = v;
                     r[k] = (uint8_t)rk;
                 }
-                if (STDP) {
+                if (SYN == 1) {
                     // traces of the excitatory neurons: x decays and counts
                     // the arrivals of S_{t-d}; y decays and counts S_t
                     const uint32_t n_exc = __ldg(&I->n_exc);
@@ -197,6 +201,55 @@ __global__ void __launch_bounds__(256) k_update(Net n)
                         *reinterpret_cast<float4*>(n.y + id0 + 4 * h) = *reinterpret_cast<float4*>(ys + 4 * h);
                     }
                 }
+                if (SYN == 2) {
+                    // lazy: y is kept every step (its decayed value y(t-1) P-
+                    // also goes to the ring slot of step t, where a pending
+                    // depression finds it), the spike history shifts, and a
+                    // row whose age reaches F is queued unless it transmits
+                    // at this step (j in S_{t-d+1}), which replays it anyway
+                    const uint32_t n_exc = __ldg(&I->n_exc);
+                    const float Pn = __ldg(&I->Pn);
+                    uint32_t tx = spk;
+                    if (n.d > 1) {
+                        tx = 0;
+                        if (t + 1 >= n.d) {
+                            const uint32_t slot = (uint32_t)((t + 1 - n.d) % n.D);
+                            tx = (n.bits[(size_t)slot * (n.Np >> 5) + (id0 >> 5)] >> (id0 & 31u)) & ((1u << NPT) - 1u);
+                        }
+                    }
+                    float ys[NPT], yp[NPT];
+                    unsigned long long hs[NPT];
+                    uint32_t ag[NPT];
+#pragma unroll
+                    for (int h = 0; h < NPT / 4; ++h) {
+                        *reinterpret_cast<float4*>(ys + 4 * h) = *reinterpret_cast<const float4*>(n.y + id0 + 4 * h);
+                        *reinterpret_cast<uint4*>(ag + 4 * h) = *reinterpret_cast<const uint4*>(n.age + id0 + 4 * h);
+                    }
+#pragma unroll
+                    for (int h = 0; h < NPT / 2; ++h)
+                        *reinterpret_cast<ulonglong2*>(hs + 2 * h) = *reinterpret_cast<const ulonglong2*>(n.hist + id0 + 2 * h);
+                    const uint32_t t31 = (uint32_t)t & 0x7fffffffu;
+#pragma unroll
+                    for (int k = 0; k < NPT; ++k) {
+                        yp[k] = 0.0f;
+                        if (local0 + k >= n_exc) continue;
+                        const float yd = __fmul_rn(ys[k], Pn);
+                        yp[k] = yd;
+                        ys[k] = (spk >> k & 1u) ? __fadd_rn(yd, 1.0f) : yd;
+                        hs[k] = (hs[k] << 1) | (unsigned long long)(spk >> k & 1u);
+                        const uint32_t lag = (t31 - (ag[k] & 0x7fffffffu)) & 0x7fffffffu;  // t - age
+                        if (lag + 1u >= n.F && !(tx >> k & 1u)) xexp |= 1u << k;
+                    }
+                    float* yr = n.yring + (size_t)(t % n.F) * n.Np;
+#pragma unroll
+                    for (int h = 0; h < NPT / 4; ++h) {
+                        *reinterpret_cast<float4*>(n.y + id0 + 4 * h) = *reinterpret_cast<float4*>(ys + 4 * h);
+                        *reinterpret_cast<float4*>(yr + id0 + 4 * h) = *reinterpret_cast<float4*>(yp + 4 * h);
+                    }
+#pragma unroll
+                    for (int h = 0; h < NPT / 2; ++h)
+                        *reinterpret_cast<ulonglong2*>(n.hist + id0 + 2 * h) = *reinterpret_cast<ulonglong2*>(hs + 2 * h);
+                }
             }
             have = true;
             if (STATS && spk) {
@@ -223,13 +276,35 @@ __global__ void __launch_bounds__(256) k_update(Net n)
         const unsigned long long tp = t - 1;
         n.lbase[slot_c] = (t > n.ctl->t_log0) ? n.lbase[tp & (n.cr - 1)] + n.count[tp & (n.cr - 1)] : 0ull;
     }
-    if (STDP) {
+    if (SYN != 0) {
         // 32 / NPT lanes cover one 32-neuron bitmask word
         constexpr uint32_t L = 32 / kUpdateNeurons;
         uint32_t word = spk << (kUpdateNeurons * (lane & (L - 1u)));
 #pragma unroll
         for (uint32_t o = 1; o < L; o <<= 1) word |= __shfl_xor_sync(kFull, word, o);
         if (active && (lane & (L - 1u)) == 0) n.bits[(size_t)slot_q * (n.Np >> 5) + (id0 >> 5)] = word;
+    }
+    if (SYN == 2) {
+        // expiring rows -> xq: warp scan, one atomicAdd per warp that has any
+        const uint32_t cx = __popc(xexp);
+        uint32_t ix = cx;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(kFull, ix, o);
+            if (lane >= (uint32_t)o) ix += v;
+        }
+        const uint32_t tot = __shfl_sync(kFull, ix, 31);
+        if (tot) {
+            uint32_t xb = 0;
+            if (lane == 31) xb = atomicAdd(&n.xcount[t & 1ull], tot);
+            xb = __shfl_sync(kFull, xb, 31) + ix - cx;
+            uint32_t m = xexp;
+            while (m) {
+                const int bit = __ffs(m) - 1;
+                m &= m - 1;
+                n.xq[xb++] = id0 + bit;
+            }
+        }
     }
     // warp compaction: exclusive scan of the per-thread spike counts, one
     // atomicAdd on the instance's queue index and one on the step's total
@@ -441,9 +516,157 @@ __global__ void __launch_bounds__(256) k_stdp_potentiate(Net n)
 }
 
 // ---------------------------------------------------------------------------
+// Lazy Update Synapses (Section III-A-1).  The exc -> exc synapses of a row
+// stay stale until the row transmits a spike (it is in S_{t-d+1}) or until
+// its age reaches the history length F; then one block brings the whole row
+// up to date in registers.  All synapses of a row share their age (they
+// transmit together), so one age per row is kept: a = the first step whose
+// events the row has not seen, with the presynaptic trace stored as x(a-1).
+// The pass replays, per synapse j -> i, the eager rule's events of steps
+// a..t in their order: the depression of step a if j's spike arrived then
+// (an arrival follows a transmission by one step, and a transmission always
+// brings the row up to date, so only step a can hold one: a flag records
+// it), with y_i(a-1) P- from the ring, then the potentiation of every step
+// s in a..t at which i spiked (bit t - s of i's history), with x_j(s).  The
+// row's x(s) sequence is the eager one, one rounded multiply per step.
+// ---------------------------------------------------------------------------
+constexpr int kLazyMaxF = 64;  // the history word has 64 bits
+constexpr int kLazyThreads = 256;
+constexpr int kLazyBatch = 4;  // edges per thread with their loads in flight together
+
+// One row, by the whole block (every thread calls it with the same j).
+template <bool W16>
+__device__ __forceinline__ void lazy_replay_row(const Net& n, uint32_t j, unsigned long long t, bool transmit,
+                                                float* xs)
+{
+    const uint32_t tid = threadIdx.x;
+    const InstDev* I = n.inst + __ldg(n.inst_of_w32 + (j >> 5));
+    const uint32_t pbase = __ldg(&I->pbase), n_exc = __ldg(&I->n_exc);
+    const float Pp = __ldg(&I->Pp), Ap = __ldg(&I->Ap), Am = __ldg(&I->Am);
+    const int32_t wmax = __ldg(&I->wmax);
+    const uint64_t beg = __ldg(n.roff + j), end = __ldg(n.roff + j + 1);
+    const uint32_t ag = n.age[j];
+    const bool arrived = (ag >> 31) != 0;
+    uint32_t L = ((((uint32_t)t & 0x7fffffffu) - (ag & 0x7fffffffu)) & 0x7fffffffu) + 1u;  // steps a..t
+    if (L > n.F) {  // the history no longer covers the row: report, and stay inside the buffers
+        if (tid == 0) atomicOr(&n.ctl->err, kErrLazyAge);
+        L = n.F;
+    }
+    if (tid == 0) {
+        float x = n.x[j];
+        for (uint32_t k = 0; k < L; ++k) {
+            x = __fmul_rn(x, Pp);
+            if (k == 0 && arrived) x = __fadd_rn(x, 1.0f);
+            xs[k] = x;
+        }
+    }
+    __syncthreads();
+    const unsigned long long win = L >= 64u ? ~0ull : (1ull << L) - 1ull;
+    // the ring slot of step a = t - (L - 1): an arrival implies a >= 1
+    const float* yr = arrived ? n.yring + (size_t)((t - (L - 1u)) % n.F) * n.Np : nullptr;
+    for (uint64_t e0 = beg + tid; e0 < end; e0 += kLazyBatch * kLazyThreads) {
+        uint32_t ii[kLazyBatch];
+#pragma unroll
+        for (int u = 0; u < kLazyBatch; ++u) {
+            const uint64_t e = e0 + (uint64_t)u * kLazyThreads;
+            ii[u] = e < end ? __ldg(n.tgt + e) : 0xffffffffu;  // padding: never plastic (pbase + n_exc < 2^31)
+        }
+        int32_t w0[kLazyBatch];
+        unsigned long long hm[kLazyBatch];
+        float yv[kLazyBatch];
+#pragma unroll
+        for (int u = 0; u < kLazyBatch; ++u) {
+            w0[u] = 0;
+            hm[u] = 0;
+            yv[u] = 0.0f;
+            if (ii[u] - pbase < n_exc) {  // excitatory target: plastic
+                const uint64_t e = e0 + (uint64_t)u * kLazyThreads;
+                w0[u] = W16 ? (int32_t)n.w16[e] : __float2int_rz(n.w32[e]);
+                hm[u] = n.hist[ii[u]] & win;
+                if (arrived) yv[u] = yr[ii[u]];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLazyBatch; ++u) {
+            if (ii[u] - pbase >= n_exc) continue;
+            int32_t w = w0[u];
+            if (arrived) w = min(max(w + __float2int_rn(__fmul_rn(Am, yv[u])), 0), wmax);
+            unsigned long long m = hm[u];
+            while (m) {
+                const int k = 63 - __clzll((long long)m);  // the earliest remaining step, t - k
+                m ^= 1ull << k;
+                w = min(max(w + __float2int_rn(__fmul_rn(Ap, xs[L - 1u - (uint32_t)k])), 0), wmax);
+            }
+            if (w != w0[u]) {
+                const uint64_t e = e0 + (uint64_t)u * kLazyThreads;
+                if (W16)
+                    n.w16[e] = (int16_t)w;
+                else
+                    n.w32[e] = (float)w;
+            }
+        }
+    }
+    // every thread has read the old age and the trajectory before they change
+    __syncthreads();
+    if (tid == 0) {
+        n.age[j] = (uint32_t)((t + 1) & 0x7fffffffull) | (transmit ? 0x80000000u : 0u);
+        n.x[j] = xs[L - 1u];
+    }
+}
+
+// One step of lazy Update Synapses, after the neuron update of step t and
+// before the receive: the excitatory rows of S_{t-d+1} (they transmit now,
+// with Syn_{t+1}) and then the rows of the expiry queue, a block per row,
+// spread over the grid.  The two sets are disjoint (the update queues no
+// transmitting row), so every row has one block.
+template <bool W16>
+__global__ void __launch_bounds__(kLazyThreads) k_stdp_lazy(Net n)
+{
+    __shared__ float xs[kLazyMaxF];
+    const unsigned long long t = n.ctl->t + n.k;
+    uint32_t next = blockIdx.x, base = 0;
+    if (t + 1 >= n.d) {
+        const unsigned long long ts = t + 1 - n.d;
+        const uint32_t* qs = n.q + (size_t)(ts % n.D) * n.Np;
+        const unsigned int* ic = n.icount + (size_t)(ts & (n.cr - 1)) * n.n_inst;
+        for (uint32_t b = 0; b < n.n_inst; ++b) {
+            const uint32_t cnt = ic[b];
+            if (next < base + cnt) {
+                const uint32_t* qb = qs + __ldg(&n.inst[b].pbase);
+                for (; next < base + cnt; next += gridDim.x) {
+                    const uint32_t j = qb[next - base];
+                    if (__ldg(n.meta + j) & 0x40u) lazy_replay_row<W16>(n, j, t, true, xs);  // excitatory source
+                }
+            }
+            base += cnt;
+        }
+    }
+    const uint32_t cnt = min(n.xcount[t & 1ull], n.Np);
+    for (uint32_t u = next - base; u < cnt; u += gridDim.x) lazy_replay_row<W16>(n, n.xq[u], t, false, xs);
+}
+
+// Bring every stale excitatory row up to date after step `now` (between
+// steps, before the weights or x are read or written).  A row that
+// transmitted at `now` is already current (its age is now + 1).
+template <bool W16>
+__global__ void __launch_bounds__(kLazyThreads) k_stdp_flush(Net n, unsigned long long now)
+{
+    __shared__ float xs[kLazyMaxF];
+    const uint32_t cur = (uint32_t)((now + 1) & 0x7fffffffull);
+    for (uint32_t j = blockIdx.x; j < n.Np; j += gridDim.x) {
+        if (!(__ldg(n.meta + j) & 0x40u)) continue;
+        if ((n.age[j] & 0x7fffffffu) == cur) continue;
+        lazy_replay_row<W16>(n, j, now, false, xs);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Init stage (Fig. 1 caption): N -> N_0.
 // ---------------------------------------------------------------------------
-__global__ void k_init_state(Net n, int vogels, int stdp)
+// With lazy plasticity a row's age starts at -(local id mod F) (mod 2^31):
+// the steps before 0 hold no events, and the staggered ages spread the rows'
+// expiries over F steps instead of replaying every row at once.
+__global__ void k_init_state(Net n, int vogels, int stdp, int lazy)
 {
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= (n.Np >> 3)) return;
@@ -471,6 +694,10 @@ __global__ void k_init_state(Net n, int vogels, int stdp)
         if (stdp) {
             n.x[id] = 0.0f;
             n.y[id] = 0.0f;
+        }
+        if (lazy) {
+            n.hist[id] = 0ull;
+            n.age[id] = (0u - (local0 + k) % n.F) & 0x7fffffffu;
         }
     }
 }

@@ -45,6 +45,11 @@ def test_argument_errors_without_device():
     assert ctx.value is None
     cfg = snn.Config(0, snn.F_STDP, 1, 1, 1, 0, 0, 0, 0, 0)  # STDP needs the Brunel model
     assert lib.snn_create(ctypes.byref(cfg), ctypes.addressof(p), None, ctypes.byref(ctx)) == -1
+    cfg = snn.Config(1, snn.F_LAZY, 1, 1, 1, 0, 0, 0, 0, 0)  # lazy plasticity needs STDP
+    assert lib.snn_create(ctypes.byref(cfg), ctypes.addressof(p), None, ctypes.byref(ctx)) == -1
+    for fifo in (1, 65):  # the history is 2..64 steps
+        cfg = snn.Config(1, snn.F_STDP | snn.F_LAZY, 1, 1, 1, 0, 0, 0, 0, fifo)
+        assert lib.snn_create(ctypes.byref(cfg), ctypes.addressof(p), None, ctypes.byref(ctx)) == -1
     cfg = snn.Config(1, 0, 1, 1, 1, 0, 0, 0, 0, 0)
     p[0].lam = 500.0  # Poisson table would exceed 64 entries
     assert lib.snn_create(ctypes.byref(cfg), ctypes.addressof(p), None, ctypes.byref(ctx)) == -1
