@@ -95,7 +95,8 @@ typedef struct {
                               never); the tiled receive cuts its items on the device every
                               step.  Results do not depend on the plan */
     uint32_t lazy_fifo;    /* SNN_F_LAZY: steps of spike and trace history kept per neuron, the
-                              longest a row stays stale (0: 50, else 2..64) */
+                              longest a row stays stale (0: 64, the most one 64-bit history
+                              word holds; else 2..64.  The paper's queue holds 50 entries) */
 } snn_config;
 
 /* Model constants of one instance.  Times in ms, potentials in mV, integer

@@ -85,6 +85,7 @@ struct snn_ctx {
     // CUDA graphs: one step, and steps_per_graph steps
     cudaGraphExec_t g1 = nullptr, gk = nullptr;
     uint32_t k_steps = 0;
+    uint32_t lazy_blocks = 0;          // grid of the lazy replay: the blocks resident at once
 };
 
 namespace {
@@ -259,9 +260,9 @@ snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr, u
     if (ev) cudaEventRecord(ev[2], s);
     if (c->lazy) {
         if (c->w16)
-            k_stdp_lazy<true><<<wblocks, 256, 0, s>>>(n);
+            k_stdp_lazy<true><<<c->lazy_blocks, kLazyThreads, 0, s>>>(n);
         else
-            k_stdp_lazy<false><<<wblocks, 256, 0, s>>>(n);
+            k_stdp_lazy<false><<<c->lazy_blocks, kLazyThreads, 0, s>>>(n);
     } else if (c->stdp) {
         if (c->w16)
             k_stdp_potentiate<true><<<wblocks, 256, 0, s>>>(n);
@@ -367,7 +368,10 @@ snn_status init_state(snn_ctx* c)
     k_init_state<<<grid_for(c->Np / 4, 256), 256, 0, c->stream>>>(c->net, c->vogels ? 1 : 0, c->stdp ? 1 : 0,
                                                                    c->lazy ? 1 : 0);
     CUDA_TRY(c, cudaGetLastError());
-    if (c->lazy) CUDA_TRY(c, cudaMemsetAsync(c->net.xcount, 0, 2 * sizeof(unsigned int), c->stream));
+    if (c->lazy) {
+        CUDA_TRY(c, cudaMemsetAsync(c->net.xcount, 0, 2 * sizeof(unsigned int), c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(c->net.hist, 0, (size_t)c->Np * sizeof(unsigned long long), c->stream));
+    }
     // control block: step 0, empty queues and log
     CUDA_TRY(c, cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), c->stream));
     if (c->stdp)
@@ -658,13 +662,17 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
         ok = ok && n.x && n.y && n.bits;
     }
     if (c->lazy) {
-        n.F = cfg->lazy_fifo ? cfg->lazy_fifo : 50;
+        n.F = cfg->lazy_fifo ? cfg->lazy_fifo : (uint32_t)kLazyMaxF;
         n.hist = alloc_n<unsigned long long>(c, Npz);
         n.yring = alloc_n<float>(c, (size_t)n.F * Npz);
         n.age = alloc_n<uint32_t>(c, Npz);
         n.xq = alloc_n<uint32_t>(c, Npz);
         n.xcount = alloc_n<unsigned int>(c, 2);
         ok = ok && n.hist && n.yring && n.age && n.xq && n.xcount;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stdp_lazy<true>, kLazyThreads, 0) != cudaSuccess)
+            cudaGetLastError();
+        c->lazy_blocks = (uint32_t)sm_count() * (uint32_t)std::max(1, per_sm);
     }
     if (c->stats) {
         n.st_cnt = alloc_n<uint32_t>(c, Npz);

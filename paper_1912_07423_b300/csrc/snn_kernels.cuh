@@ -527,127 +527,231 @@ __global__ void __launch_bounds__(256) k_stdp_potentiate(Net n)
 // (an arrival follows a transmission by one step, and a transmission always
 // brings the row up to date, so only step a can hold one: a flag records
 // it), with y_i(a-1) P- from the ring, then the potentiation of every step
-// s in a..t at which i spiked (bit t - s of i's history), with x_j(s).  The
-// row's x(s) sequence is the eager one, one rounded multiply per step.
+// s in a..t at which i spiked (bit t - s of i's history), with x_j(s).
+// The row's x(s) sequence is the eager one, one rounded multiply per step.
 // ---------------------------------------------------------------------------
-constexpr int kLazyMaxF = 64;  // the history word has 64 bits
+constexpr int kLazyMaxF = 64;    // longest history (steps): the bits of one 64-bit word
 constexpr int kLazyThreads = 256;
-constexpr int kLazyBatch = 4;  // edges per thread with their loads in flight together
+constexpr int kLazyBatch = 4;    // edges per thread with their loads in flight together
 
-// One row, by the whole block (every thread calls it with the same j).
-template <bool W16>
-__device__ __forceinline__ void lazy_replay_row(const Net& n, uint32_t j, unsigned long long t, bool transmit,
-                                                float* xs)
+// The row-level part of a replay: the window of steps and the constants
+// every synapse of the row uses.
+struct LazyRow {
+    uint32_t pbase, n_exc, L;
+    float Ap, Am;
+    int32_t wmax;
+    bool arrived;
+    unsigned long long win;   // history bits of steps a..t (bits 0 .. L-1)
+    const float* yr;          // ring slot of step a (when arrived)
+};
+
+__device__ __forceinline__ LazyRow lazy_row(const Net& n, uint32_t j, uint32_t ag, unsigned long long t, bool leader)
 {
-    const uint32_t tid = threadIdx.x;
+    LazyRow r;
     const InstDev* I = n.inst + __ldg(n.inst_of_w32 + (j >> 5));
-    const uint32_t pbase = __ldg(&I->pbase), n_exc = __ldg(&I->n_exc);
-    const float Pp = __ldg(&I->Pp), Ap = __ldg(&I->Ap), Am = __ldg(&I->Am);
-    const int32_t wmax = __ldg(&I->wmax);
-    const uint64_t beg = __ldg(n.roff + j), end = __ldg(n.roff + j + 1);
-    const uint32_t ag = n.age[j];
-    const bool arrived = (ag >> 31) != 0;
+    r.pbase = __ldg(&I->pbase);
+    r.n_exc = __ldg(&I->n_exc);
+    r.Ap = __ldg(&I->Ap);
+    r.Am = __ldg(&I->Am);
+    r.wmax = __ldg(&I->wmax);
+    r.arrived = (ag >> 31) != 0;
     uint32_t L = ((((uint32_t)t & 0x7fffffffu) - (ag & 0x7fffffffu)) & 0x7fffffffu) + 1u;  // steps a..t
     if (L > n.F) {  // the history no longer covers the row: report, and stay inside the buffers
-        if (tid == 0) atomicOr(&n.ctl->err, kErrLazyAge);
+        if (leader) atomicOr(&n.ctl->err, kErrLazyAge);
         L = n.F;
     }
-    if (tid == 0) {
-        float x = n.x[j];
-        for (uint32_t k = 0; k < L; ++k) {
-            x = __fmul_rn(x, Pp);
-            if (k == 0 && arrived) x = __fadd_rn(x, 1.0f);
-            xs[k] = x;
-        }
-    }
-    __syncthreads();
-    const unsigned long long win = L >= 64u ? ~0ull : (1ull << L) - 1ull;
+    r.L = L;
+    r.win = L >= 64u ? ~0ull : (1ull << L) - 1ull;
     // the ring slot of step a = t - (L - 1): an arrival implies a >= 1
-    const float* yr = arrived ? n.yring + (size_t)((t - (L - 1u)) % n.F) * n.Np : nullptr;
-    for (uint64_t e0 = beg + tid; e0 < end; e0 += kLazyBatch * kLazyThreads) {
-        uint32_t ii[kLazyBatch];
-#pragma unroll
-        for (int u = 0; u < kLazyBatch; ++u) {
-            const uint64_t e = e0 + (uint64_t)u * kLazyThreads;
-            ii[u] = e < end ? __ldg(n.tgt + e) : 0xffffffffu;  // padding: never plastic (pbase + n_exc < 2^31)
-        }
-        int32_t w0[kLazyBatch];
-        unsigned long long hm[kLazyBatch];
-        float yv[kLazyBatch];
-#pragma unroll
-        for (int u = 0; u < kLazyBatch; ++u) {
-            w0[u] = 0;
-            hm[u] = 0;
-            yv[u] = 0.0f;
-            if (ii[u] - pbase < n_exc) {  // excitatory target: plastic
-                const uint64_t e = e0 + (uint64_t)u * kLazyThreads;
-                w0[u] = W16 ? (int32_t)n.w16[e] : __float2int_rz(n.w32[e]);
-                hm[u] = n.hist[ii[u]] & win;
-                if (arrived) yv[u] = yr[ii[u]];
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kLazyBatch; ++u) {
-            if (ii[u] - pbase >= n_exc) continue;
-            int32_t w = w0[u];
-            if (arrived) w = min(max(w + __float2int_rn(__fmul_rn(Am, yv[u])), 0), wmax);
-            unsigned long long m = hm[u];
-            while (m) {
-                const int k = 63 - __clzll((long long)m);  // the earliest remaining step, t - k
-                m ^= 1ull << k;
-                w = min(max(w + __float2int_rn(__fmul_rn(Ap, xs[L - 1u - (uint32_t)k])), 0), wmax);
-            }
-            if (w != w0[u]) {
-                const uint64_t e = e0 + (uint64_t)u * kLazyThreads;
-                if (W16)
-                    n.w16[e] = (int16_t)w;
-                else
-                    n.w32[e] = (float)w;
-            }
-        }
-    }
-    // every thread has read the old age and the trajectory before they change
-    __syncthreads();
-    if (tid == 0) {
-        n.age[j] = (uint32_t)((t + 1) & 0x7fffffffull) | (transmit ? 0x80000000u : 0u);
-        n.x[j] = xs[L - 1u];
+    r.yr = r.arrived ? n.yring + (size_t)((t - (L - 1u)) % n.F) * n.Np : nullptr;
+    return r;
+}
+
+// x(s) for s = a..t into xs[0..L), one rounded multiply per step (the
+// arrival of step a, if any, added after its decay); one thread.
+__device__ __forceinline__ void lazy_trajectory(const Net& n, uint32_t j, const LazyRow& r, float* xs)
+{
+    const float Pp = __ldg(&n.inst[__ldg(n.inst_of_w32 + (j >> 5))].Pp);
+    float x = n.x[j];
+    for (uint32_t k = 0; k < r.L; ++k) {
+        x = __fmul_rn(x, Pp);
+        if (k == 0 && r.arrived) x = __fadd_rn(x, 1.0f);
+        xs[k] = x;
     }
 }
 
+// Targets of B synapses, `stride` apart from e0 (past the end: an id that is
+// never plastic, since pbase + n_exc < 2^31).
+template <int B>
+__device__ __forceinline__ void lazy_targets(const Net& n, uint64_t e0, uint64_t end, uint32_t stride, uint32_t* ii)
+{
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        const uint64_t e = e0 + (uint64_t)u * stride;
+        ii[u] = e < end ? __ldg(n.tgt + e) : 0xffffffffu;
+    }
+}
+
+// Replay B synapses whose targets are loaded: the weights, the pending
+// arrival's traces and the targets' histories are loaded at once,
+// then (after `sync`: the block waits for the trajectory) each synapse takes
+// the depression of the pending arrival and the potentiation of every step
+// at which its target spiked, in step order, each change clipped to
+// [0, w_max]; changed weights only are written back.
+template <bool W16, int B>
+__device__ __forceinline__ void lazy_apply(const Net& n, const LazyRow& r, const float* xs, const uint32_t* ii,
+                                           uint64_t e0, uint32_t stride, bool sync)
+{
+    int32_t w0[B];
+    float yv[B];
+    unsigned long long hm[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        w0[u] = 0;
+        yv[u] = 0.0f;
+        hm[u] = 0ull;
+        if (ii[u] - r.pbase < r.n_exc) {  // excitatory target: plastic
+            const uint64_t e = e0 + (uint64_t)u * stride;
+            w0[u] = W16 ? (int32_t)n.w16[e] : __float2int_rz(n.w32[e]);
+            if (r.arrived) yv[u] = r.yr[ii[u]];
+            hm[u] = n.hist[ii[u]] & r.win;
+        }
+    }
+    if (sync) __syncthreads();
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        if (ii[u] - r.pbase >= r.n_exc) continue;
+        int32_t w = w0[u];
+        if (r.arrived) w = min(max(w + __float2int_rn(__fmul_rn(r.Am, yv[u])), 0), r.wmax);
+        unsigned long long m = hm[u];
+        while (m) {
+            const int k = 63 - __clzll((long long)m);  // the earliest remaining step, t - k
+            m ^= 1ull << k;
+            w = min(max(w + __float2int_rn(__fmul_rn(r.Ap, xs[r.L - 1u - (uint32_t)k])), 0), r.wmax);
+        }
+        if (w != w0[u]) {
+            const uint64_t e = e0 + (uint64_t)u * stride;
+            if (W16)
+                n.w16[e] = (int16_t)w;
+            else
+                n.w32[e] = (float)w;
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t lazy_new_age(unsigned long long t, bool transmit)
+{
+    return (uint32_t)((t + 1) & 0x7fffffffull) | (transmit ? 0x80000000u : 0u);
+}
+
+// One row by the whole block (every thread calls it with the same row): the
+// first batch of targets is in flight while thread 0 computes the
+// trajectory; the block waits for it once; the row's age and x change after
+// every thread has read them.
+template <bool W16>
+__device__ __forceinline__ void lazy_replay_row(const Net& n, uint32_t j, uint32_t ag, uint64_t beg, uint64_t end,
+                                                unsigned long long t, bool transmit, float* xs)
+{
+    constexpr int B = kLazyBatch;
+    const uint32_t tid = threadIdx.x;
+    const LazyRow r = lazy_row(n, j, ag, t, tid == 0);
+    uint64_t e0 = beg + tid;
+    uint32_t ii[B];
+    lazy_targets<B>(n, e0, end, kLazyThreads, ii);
+    if (tid == 0) lazy_trajectory(n, j, r, xs);
+    lazy_apply<W16, B>(n, r, xs, ii, e0, kLazyThreads, true);
+    for (e0 += (uint64_t)B * kLazyThreads; e0 < end; e0 += (uint64_t)B * kLazyThreads) {  // longer rows
+        lazy_targets<B>(n, e0, end, kLazyThreads, ii);
+        lazy_apply<W16, B>(n, r, xs, ii, e0, kLazyThreads, false);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        n.age[j] = lazy_new_age(t, transmit);
+        n.x[j] = xs[r.L - 1u];
+    }
+}
+
+// The rows one lazy step replays, in a fixed order: the spikers of
+// S_{t-d+1} instance by instance (inhibitory ones included; they are
+// skipped), then the expiry queue.  at(r) returns row r; r must not
+// decrease between calls.
+struct LazyRows {
+    const Net* n;
+    const uint32_t* qs;       // queue slot of S_{t-d+1} (null before step d-1)
+    const unsigned int* ic;   // its per-instance counts
+    uint32_t b, base;         // current instance and the rows before it
+    uint32_t n_tx, n_x;       // rows of the two sets
+
+    __device__ __forceinline__ void init(const Net& net, unsigned long long t)
+    {
+        n = &net;
+        qs = nullptr;
+        ic = nullptr;
+        b = 0;
+        base = 0;
+        n_tx = 0;
+        if (t + 1 >= net.d) {
+            const unsigned long long ts = t + 1 - net.d;
+            qs = net.q + (size_t)(ts % net.D) * net.Np;
+            ic = net.icount + (size_t)(ts & (net.cr - 1)) * net.n_inst;
+            for (uint32_t k = 0; k < net.n_inst; ++k) n_tx += ic[k];
+        }
+        n_x = min(net.xcount[t & 1ull], net.Np);
+    }
+    __device__ __forceinline__ uint32_t total() const { return n_tx + n_x; }
+    __device__ __forceinline__ uint32_t at(uint32_t r)
+    {
+        if (r >= n_tx) return n->xq[r - n_tx];
+        while (r >= base + ic[b]) base += ic[b++];
+        return qs[__ldg(&n->inst[b].pbase) + (r - base)];
+    }
+};
+
 // One step of lazy Update Synapses, after the neuron update of step t and
 // before the receive: the excitatory rows of S_{t-d+1} (they transmit now,
-// with Syn_{t+1}) and then the rows of the expiry queue, a block per row,
-// spread over the grid.  The two sets are disjoint (the update queues no
-// transmitting row), so every row has one block.
+// with Syn_{t+1}) and the rows of the expiry queue, a block per row.  The
+// two sets are disjoint (the update queues no transmitting row), so every
+// row is replayed once.  The next row's record is loaded while the current
+// one is replayed.
 template <bool W16>
 __global__ void __launch_bounds__(kLazyThreads) k_stdp_lazy(Net n)
 {
     __shared__ float xs[kLazyMaxF];
     const unsigned long long t = n.ctl->t + n.k;
-    uint32_t next = blockIdx.x, base = 0;
-    if (t + 1 >= n.d) {
-        const unsigned long long ts = t + 1 - n.d;
-        const uint32_t* qs = n.q + (size_t)(ts % n.D) * n.Np;
-        const unsigned int* ic = n.icount + (size_t)(ts & (n.cr - 1)) * n.n_inst;
-        for (uint32_t b = 0; b < n.n_inst; ++b) {
-            const uint32_t cnt = ic[b];
-            if (next < base + cnt) {
-                const uint32_t* qb = qs + __ldg(&n.inst[b].pbase);
-                for (; next < base + cnt; next += gridDim.x) {
-                    const uint32_t j = qb[next - base];
-                    if (__ldg(n.meta + j) & 0x40u) lazy_replay_row<W16>(n, j, t, true, xs);  // excitatory source
-                }
-            }
-            base += cnt;
+    LazyRows rows;
+    rows.init(n, t);
+    const uint32_t R = rows.total();
+    uint32_t r = blockIdx.x;
+    if (r >= R) return;
+    uint32_t j = rows.at(r);
+    uint32_t meta = __ldg(n.meta + j), ag = n.age[j];
+    uint64_t beg = __ldg(n.roff + j), end = __ldg(n.roff + j + 1);
+    for (;;) {
+        const bool transmit = r < rows.n_tx;
+        const uint32_t rn = r + gridDim.x;  // the next row's record
+        uint32_t jn = 0, metan = 0, agn = 0;
+        uint64_t begn = 0, endn = 0;
+        if (rn < R) {
+            jn = rows.at(rn);
+            metan = __ldg(n.meta + jn);
+            agn = n.age[jn];
+            begn = __ldg(n.roff + jn);
+            endn = __ldg(n.roff + jn + 1);
         }
+        if (meta & 0x40u) lazy_replay_row<W16>(n, j, ag, beg, end, t, transmit, xs);  // excitatory source
+        if (rn >= R) break;
+        r = rn;
+        j = jn;
+        meta = metan;
+        ag = agn;
+        beg = begn;
+        end = endn;
     }
-    const uint32_t cnt = min(n.xcount[t & 1ull], n.Np);
-    for (uint32_t u = next - base; u < cnt; u += gridDim.x) lazy_replay_row<W16>(n, n.xq[u], t, false, xs);
 }
 
 // Bring every stale excitatory row up to date after step `now` (between
-// steps, before the weights or x are read or written).  A row that
-// transmitted at `now` is already current (its age is now + 1).
+// steps, before the weights or x are read or written), a block per row.  A
+// row that transmitted at `now` is already current (its age is now + 1).
 template <bool W16>
 __global__ void __launch_bounds__(kLazyThreads) k_stdp_flush(Net n, unsigned long long now)
 {
@@ -655,8 +759,9 @@ __global__ void __launch_bounds__(kLazyThreads) k_stdp_flush(Net n, unsigned lon
     const uint32_t cur = (uint32_t)((now + 1) & 0x7fffffffull);
     for (uint32_t j = blockIdx.x; j < n.Np; j += gridDim.x) {
         if (!(__ldg(n.meta + j) & 0x40u)) continue;
-        if ((n.age[j] & 0x7fffffffu) == cur) continue;
-        lazy_replay_row<W16>(n, j, now, false, xs);
+        const uint32_t ag = n.age[j];
+        if ((ag & 0x7fffffffu) == cur) continue;
+        lazy_replay_row<W16>(n, j, ag, __ldg(n.roff + j), __ldg(n.roff + j + 1), now, false, xs);
     }
 }
 
@@ -695,10 +800,7 @@ __global__ void k_init_state(Net n, int vogels, int stdp, int lazy)
             n.x[id] = 0.0f;
             n.y[id] = 0.0f;
         }
-        if (lazy) {
-            n.hist[id] = 0ull;
-            n.age[id] = (0u - (local0 + k) % n.F) & 0x7fffffffu;
-        }
+        if (lazy) n.age[id] = (0u - (local0 + k) % n.F) & 0x7fffffffu;
     }
 }
 
