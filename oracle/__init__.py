@@ -17,6 +17,9 @@ Parity status of the functions (what pins each one, see tests/test_oracle_*):
                  weight changes of a single pre/post pair
   run_f64     -- agreement with the binary32 run in population rate and
                  ISI CV (statistical; it is a comparison variant)
+  relay_raster -- a hand-worked raster of a four-neuron graph, breadth-first
+                 search over the CSR, and the binary32 run of the same graph
+                 in its LIF relay form
 """
 from __future__ import annotations
 
@@ -284,3 +287,48 @@ def receive(prob, spikes, w=None) -> tuple:
     if rc != 0:
         raise OracleError(f"orc_receive failed ({rc})")
     return acc0, acc1, int(ev.value)
+
+
+def relay_raster(prob, n_steps: int | None = None) -> dict:
+    """The tutorial model of Section III-B (Listing 1), written from its
+    definition with plain loops: every neuron holds a flag, set before step
+    0 for the first population of its instance (local id < n_exc); at each
+    step a neuron fires when its flag is set or the lattice weights it
+    received since its previous update sum to a nonzero value, and the flag
+    clears.  A spike of step t is delivered along its row at step t + d - 1
+    and so reaches the update of step t + d (the delay FIFO of Fig. 1).
+    Returns the raster sorted by (step, id), the events delivered within the
+    run, and the input pending for the next update (acc0)."""
+    T = prob.n_steps if n_steps is None else n_steps
+    d = int(prob.delay)
+    n = int(prob.n)
+    inst_off = [int(v) for v in prob.inst_off]
+    row_off = [int(v) for v in prob.row_off]
+    tgt = [int(v) for v in prob.tgt]
+    w = [int(v) for v in prob.w]
+    flag = [0] * n
+    for b, inst in enumerate(prob.instances):
+        for local in range(min(inst.n_exc, inst.n)):
+            flag[inst_off[b] + local] = 1
+    arrive = {}  # step -> {neuron: summed weight}
+    steps, ids, events = [], [], 0
+    for t in range(T):
+        got = arrive.pop(t, {})
+        fired = []
+        for i in range(n):
+            if flag[i] or got.get(i, 0) != 0:
+                fired.append(i)
+            flag[i] = 0
+        for i in fired:
+            steps.append(t)
+            ids.append(i)
+        if t + d - 1 <= T - 1:  # delivered inside the run
+            into = arrive.setdefault(t + d, {})
+            for j in fired:
+                for e in range(row_off[j], row_off[j + 1]):
+                    into[tgt[e]] = into.get(tgt[e], 0) + w[e]
+                events += row_off[j + 1] - row_off[j]
+    acc0 = np.zeros(n, np.int64)
+    for i, v in arrive.get(T, {}).items():
+        acc0[i] = v
+    return {"steps": np.array(steps, np.uint32), "ids": np.array(ids, np.uint32), "events": events, "acc0": acc0}
