@@ -15,6 +15,7 @@ through the C ABI from host buffers, and the CPU oracle on a bounded sample.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -382,6 +383,22 @@ def run_ours(args, rank, world, dist):
                              "realtime_factor": args.steps * DT_MS * 1e-3 / t_pl}
         out["speedup_vs_plain_fp32"] = out["value"] / out["plain_fp32"]["value"]
 
+    # ---- the same networks through the generic update (Section III-B): Brunel
+    # written as a specialisation of the LIF building block
+    if not args.no_generic and prob.model == si.BRUNEL and not prob.stdp:
+        gprob = dataclasses.replace(prob, model=snn.MODEL_BRUNEL_LIF)
+        net = snn.Network(gprob, w16=True, receive=recv_mode, log_capacity=cap)
+        net.step(args.warmup)
+        net.sync()
+        t_g, ev_g, sp_g = timed(net, args.steps)
+        net.close()
+        del net
+        torch.cuda.empty_cache()
+        out["generic_update"] = {"value": sum_over_ranks(ev_g) / max_over_ranks(t_g), "unit": "synaptic events/s",
+                                 "ms_per_step": t_g * 1e3 / args.steps,
+                                 "model": "Brunel from the LIF building block (SNN_MODEL_BRUNEL_LIF)",
+                                 "same_events_and_spikes": bool(ev_g == ev_main and sp_g == sp_main)}
+
     # ---- end to end through the C ABI from host buffers
     if not args.no_e2e:
         barrier()
@@ -451,6 +468,7 @@ def main():
     ap.add_argument("--lazy-fifo", type=int, default=0, help="lazy plasticity: history length (0: 64)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-generic", action="store_true", help="skip timing the generic-update model")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="skip timing the GPU adjacency construction")
     args = ap.parse_args()

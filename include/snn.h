@@ -58,7 +58,15 @@ typedef enum {
 
 typedef enum {
     SNN_VOGELS_CUBA = 0, /* LIF with exponential exc/inh currents and constant drive (Section IV) */
-    SNN_BRUNEL = 1       /* LIF with delta synapses and Poisson drive (Section IV) */
+    SNN_BRUNEL = 1,      /* LIF with delta synapses and Poisson drive (Section IV) */
+    /* Models of the generic update (Section III-B): device functors with init() and update()
+     * callbacks compiled into the library from csrc/snn_models.cuh; their per-neuron state is
+     * one record (SNN_FIELD_MODEL).  Receive Spikes stays the library's: a neuron's update sees
+     * the sum of the weights it received since its last update. */
+    SNN_MODEL_RELAY = 2,     /* the paper's tutorial model (Listing 1): a neuron fires at the step
+                                after it received input; local ids < n_exc fire at step 0 */
+    SNN_MODEL_BRUNEL_LIF = 3 /* Brunel written as a Poisson-driven specialisation of the LIF
+                                building block; the values of SNN_BRUNEL, bit for bit */
 } snn_model;
 
 /* snn_config.flags */
@@ -199,7 +207,10 @@ typedef enum {
     SNN_FIELD_Y = 5,    /* float, postsynaptic STDP trace */
     SNN_FIELD_ACC0 = 6, /* int32, pending input (channel 0: excitatory / all) */
     SNN_FIELD_ACC1 = 7, /* int32, pending input (channel 1: Vogels inhibitory) */
-    SNN_FIELD_W = 8     /* int32[E], weights in lattice units, CSR order of snn_build_graph */
+    SNN_FIELD_W = 8,    /* int32[E], weights in lattice units, CSR order of snn_build_graph */
+    SNN_FIELD_MODEL = 9 /* generic models: N records of snn_info.model_state_bytes bytes each, the
+                           model's neuron struct (SNN_MODEL_RELAY: uint8 flag; SNN_MODEL_BRUNEL_LIF:
+                           float V, uint8 refractory steps left, 3 bytes padding) */
 } snn_field;
 
 /* Copy a state field to / from host memory (synchronises).  Writing takes
@@ -278,7 +289,7 @@ typedef struct {
     uint64_t edges;        /* synapses loaded */
     uint64_t device_bytes; /* device memory held */
     uint32_t edge_bytes;   /* bytes the receive reads per delivered edge: 4 (packed), 6 (int16 codes), 8 */
-    uint32_t reserved;
+    uint32_t model_state_bytes; /* generic models: bytes of one neuron's state record (else 0) */
 } snn_info;
 snn_status snn_get_info(snn_ctx* ctx, snn_info* info);
 

@@ -16,13 +16,20 @@ import numpy as np
 
 from .build import LIB, build as _build
 
-__all__ = ["Network", "SnnError", "load", "VOGELS", "BRUNEL", "RECV_AUTO", "RECV_GLOBAL", "RECV_TILED", "RECV_BULK",
-           "F_STDP", "F_W16", "F_STATS", "F_UNPACKED", "F_LAZY", "FIELDS"]
+__all__ = ["Network", "SnnError", "load", "VOGELS", "BRUNEL", "MODEL_RELAY", "MODEL_BRUNEL_LIF", "MODEL_STATE_DTYPE",
+           "RECV_AUTO", "RECV_GLOBAL", "RECV_TILED", "RECV_BULK", "F_STDP", "F_W16", "F_STATS", "F_UNPACKED", "F_LAZY",
+           "FIELDS"]
 
 VOGELS, BRUNEL = 0, 1
+# models of the generic update (snn_models.cuh) and their per-neuron state records
+MODEL_RELAY, MODEL_BRUNEL_LIF = 2, 3
+MODEL_STATE_DTYPE = {
+    MODEL_RELAY: np.dtype([("flag", "u1")]),
+    MODEL_BRUNEL_LIF: np.dtype({"names": ["V", "r"], "formats": ["<f4", "u1"], "offsets": [0, 4], "itemsize": 8}),
+}
 F_STDP, F_W16, F_STATS, F_UNPACKED, F_LAZY = 1, 2, 4, 8, 16
 RECV_AUTO, RECV_GLOBAL, RECV_TILED, RECV_BULK = 0, 1, 2, 3
-FIELDS = {"V": 0, "ge": 1, "gi": 2, "r": 3, "x": 4, "y": 5, "acc0": 6, "acc1": 7, "w": 8}
+FIELDS = {"V": 0, "ge": 1, "gi": 2, "r": 3, "x": 4, "y": 5, "acc0": 6, "acc1": 7, "w": 8, "model": 9}
 _FIELD_DTYPE = {"V": np.float32, "ge": np.float32, "gi": np.float32, "r": np.int32, "x": np.float32,
                 "y": np.float32, "acc0": np.int32, "acc1": np.int32, "w": np.int32}
 
@@ -57,7 +64,7 @@ class Params(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("receive", ctypes.c_uint32), ("n_tiles", ctypes.c_uint32), ("n_padded", ctypes.c_uint32),
                 ("rows_sorted", ctypes.c_uint32), ("edges", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
-                ("edge_bytes", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("edge_bytes", ctypes.c_uint32), ("model_state_bytes", ctypes.c_uint32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(_vp, ctypes.c_size_t, _vp, _vp)
@@ -283,15 +290,22 @@ class Network:
     def log_clear(self):
         self._check(self.lib.snn_log_clear(self.ctx), "snn_log_clear")
 
+    def _dtype(self, field: str):
+        if field == "model":
+            if self.problem.model not in MODEL_STATE_DTYPE:
+                raise SnnError(-1, "the model field exists for the generic models only")
+            return MODEL_STATE_DTYPE[self.problem.model]
+        return _FIELD_DTYPE[field]
+
     def read(self, field: str) -> np.ndarray:
         size = self.n_edges if field == "w" else self.n
-        out = np.zeros(max(size, 1), _FIELD_DTYPE[field])
+        out = np.zeros(max(size, 1), self._dtype(field))
         self._check(self.lib.snn_read_state(self.ctx, FIELDS[field], out.ctypes.data), f"snn_read_state({field})")
         return out[:size]
 
     def write(self, field: str, values):
         size = self.n_edges if field == "w" else self.n
-        arr = np.ascontiguousarray(values, dtype=_FIELD_DTYPE[field])
+        arr = np.ascontiguousarray(values, dtype=self._dtype(field))
         if arr.size != size:
             raise ValueError(f"{field}: expected {size} values, got {arr.size}")
         buf = arr if arr.size else np.zeros(1, arr.dtype)
@@ -316,4 +330,4 @@ class Network:
         self._check(self.lib.snn_get_info(self.ctx, ctypes.byref(i)), "snn_get_info")
         return {"receive": {RECV_GLOBAL: "global", RECV_TILED: "tiled", RECV_BULK: "bulk"}.get(i.receive, "?"), "n_tiles": i.n_tiles,
                 "n_padded": i.n_padded, "rows_sorted": bool(i.rows_sorted), "edges": i.edges,
-                "device_bytes": i.device_bytes, "edge_bytes": i.edge_bytes}
+                "device_bytes": i.device_bytes, "edge_bytes": i.edge_bytes, "model_state_bytes": i.model_state_bytes}

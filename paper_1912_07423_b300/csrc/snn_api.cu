@@ -21,6 +21,7 @@
 #include "snn_kernels.cuh"
 #include "snn_tiled.cuh"
 #include "snn_bulk.cuh"
+#include "snn_models.cuh"
 
 #include <cub/device/device_radix_sort.cuh>
 
@@ -43,6 +44,9 @@ struct snn_ctx {
     std::vector<uint32_t> pbase;   // padded bases (n_inst+1)
     bool vogels = false, stdp = false, w16 = false, stats = false;
     bool lazy = false;             // lazy Update Synapses (SNN_F_LAZY)
+    bool generic = false;          // a model of the generic update (snn_models.cuh)
+    void* mstate = nullptr;        // generic models: one state record per neuron slot
+    size_t mbytes = 0;             // bytes of one record
     bool graph_loaded = false;
     uint64_t host_steps = 0;       // steps enqueued since reset
 
@@ -236,7 +240,9 @@ snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr, u
             k_stdp_depress<false><<<wblocks, 256, 0, s>>>(n);
     }
     if (ev) cudaEventRecord(ev[1], s);
-    if (c->vogels) {
+    if (c->generic) {
+        launch_update_model(c->cfg.model, n, c->mstate, c->stats, ublocks, s);
+    } else if (c->vogels) {
         if (c->stats)
             k_update<0, 0, true><<<ublocks, 256, 0, s>>>(n);
         else
@@ -368,6 +374,10 @@ snn_status init_state(snn_ctx* c)
     k_init_state<<<grid_for(c->Np / 4, 256), 256, 0, c->stream>>>(c->net, c->vogels ? 1 : 0, c->stdp ? 1 : 0,
                                                                    c->lazy ? 1 : 0);
     CUDA_TRY(c, cudaGetLastError());
+    if (c->generic) {
+        launch_init_model(c->cfg.model, c->net, c->mstate, grid_for(c->Np / 8, 256), c->stream);
+        CUDA_TRY(c, cudaGetLastError());
+    }
     if (c->lazy) {
         CUDA_TRY(c, cudaMemsetAsync(c->net.xcount, 0, 2 * sizeof(unsigned int), c->stream));
         CUDA_TRY(c, cudaMemsetAsync(c->net.hist, 0, (size_t)c->Np * sizeof(unsigned long long), c->stream));
@@ -543,7 +553,7 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     if (!out) return SNN_E_ARG;
     *out = nullptr;
     if (!cfg || !params || cfg->n_inst == 0) return SNN_E_ARG;
-    if (cfg->model > SNN_BRUNEL || cfg->delay < 1 || cfg->delay > 1000) return SNN_E_ARG;
+    if (cfg->model > SNN_MODEL_BRUNEL_LIF || cfg->delay < 1 || cfg->delay > 1000) return SNN_E_ARG;
     if ((cfg->flags & SNN_F_STDP) && cfg->model != SNN_BRUNEL) return SNN_E_ARG;
     if ((cfg->flags & SNN_F_LAZY) &&
         (!(cfg->flags & SNN_F_STDP) || cfg->lazy_fifo == 1 || cfg->lazy_fifo > (uint32_t)kLazyMaxF))
@@ -559,7 +569,7 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
             (!(p.tau_plus > 0) || !(p.tau_minus > 0) || p.w_max_q < 0 || p.w_max_q > 32767))
             return SNN_E_ARG;
         uint32_t T[kPoissonCap];
-        if (cfg->model == SNN_BRUNEL && poisson_table(p.lambda, T, kPoissonCap) < 0) return SNN_E_ARG;
+        if (cfg->model != SNN_VOGELS_CUBA && poisson_table(p.lambda, T, kPoissonCap) < 0) return SNN_E_ARG;
         N += p.n;
         Np += (p.n + kPad - 1) / kPad * kPad;
     }
@@ -572,6 +582,8 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     if (dev) c->dev = *dev;
     c->stream = (cudaStream_t)c->dev.stream;
     c->vogels = cfg->model == SNN_VOGELS_CUBA;
+    c->generic = is_generic_model(cfg->model);
+    c->mbytes = model_state_bytes(cfg->model);
     c->stdp = (cfg->flags & SNN_F_STDP) != 0;
     c->lazy = c->stdp && (cfg->flags & SNN_F_LAZY) != 0;
     c->w16 = (cfg->flags & SNN_F_W16) != 0;
@@ -604,7 +616,7 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     std::vector<uint32_t> hpois((size_t)cfg->n_inst * kPoissonCap, 0xffffffffu);
     for (uint32_t b = 0; b < cfg->n_inst; ++b) {
         int np = 0;
-        if (cfg->model == SNN_BRUNEL) np = poisson_table(params[b].lambda, &hpois[(size_t)b * kPoissonCap], kPoissonCap);
+        if (cfg->model != SNN_VOGELS_CUBA) np = poisson_table(params[b].lambda, &hpois[(size_t)b * kPoissonCap], kPoissonCap);
         hinst[b] = make_inst(params[b], c->pbase[b], c->g_off[b], b * kPoissonCap, np);
     }
     // bucket table of every instance: thresholds below each 2^24 boundary
@@ -649,6 +661,10 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     n.q = alloc_n<uint32_t>(c, (size_t)c->D * Npz);
     bool ok = c->ctl && c->inst && c->inst_of_w32 && c->pois && c->pois_start && n.V && n.r && n.acc0 && n.q && n.count && n.icount && n.lbase &&
               n.inst_spikes && n.tile_ctr;
+    if (c->generic) {
+        c->mstate = dev_alloc(c, c->mbytes * Npz);
+        ok = ok && c->mstate;
+    }
     if (c->vogels) {
         n.ge = alloc_n<float>(c, Npz);
         n.gi = alloc_n<float>(c, Npz);
@@ -1125,6 +1141,7 @@ static snn_status field_ptr(snn_ctx* c, snn_field f, void** p, size_t* elem, boo
     case SNN_FIELD_Y: *p = c->net.y; break;
     case SNN_FIELD_ACC0: *p = c->net.acc0; break;
     case SNN_FIELD_ACC1: *p = c->net.acc1; break;
+    case SNN_FIELD_MODEL: *p = c->mstate; *elem = c->mbytes; break;
     default: return fail(c, SNN_E_ARG, "unknown field %d", (int)f);
     }
     if (!*p) return fail(c, SNN_E_ARG, "field %d does not exist for this model", (int)f);
@@ -1157,7 +1174,8 @@ snn_status snn_read_state(snn_ctx* c, snn_field f, void* host)
     bool u8;
     snn_status st = field_ptr(c, f, &p, &elem, &u8);
     if (st != SNN_OK) return st;
-    std::vector<uint8_t> buf((size_t)c->Np * (u8 ? 1 : 4));
+    const size_t esz = u8 ? 1 : elem;
+    std::vector<uint8_t> buf((size_t)c->Np * esz);
     CUDA_TRY(c, cudaMemcpy(buf.data(), p, buf.size(), cudaMemcpyDeviceToHost));
     for (uint32_t b = 0; b < c->cfg.n_inst; ++b)
         for (uint32_t l = 0; l < c->params[b].n; ++l) {
@@ -1165,7 +1183,7 @@ snn_status snn_read_state(snn_ctx* c, snn_field f, void* host)
             if (u8)
                 static_cast<int32_t*>(host)[g] = buf[pid];
             else
-                std::memcpy(static_cast<uint8_t*>(host) + (size_t)g * 4, buf.data() + (size_t)pid * 4, 4);
+                std::memcpy(static_cast<uint8_t*>(host) + (size_t)g * esz, buf.data() + (size_t)pid * esz, esz);
         }
     return SNN_OK;
 }
@@ -1204,7 +1222,8 @@ snn_status snn_write_state(snn_ctx* c, snn_field f, const void* host)
     bool u8;
     snn_status st = field_ptr(c, f, &p, &elem, &u8);
     if (st != SNN_OK) return st;
-    std::vector<uint8_t> buf((size_t)c->Np * (u8 ? 1 : 4));
+    const size_t esz = u8 ? 1 : elem;
+    std::vector<uint8_t> buf((size_t)c->Np * esz);
     CUDA_TRY(c, cudaMemcpy(buf.data(), p, buf.size(), cudaMemcpyDeviceToHost));
     for (uint32_t b = 0; b < c->cfg.n_inst; ++b)
         for (uint32_t l = 0; l < c->params[b].n; ++l) {
@@ -1214,7 +1233,7 @@ snn_status snn_write_state(snn_ctx* c, snn_field f, const void* host)
                 if (v < 0 || v > 255) return fail(c, SNN_E_ARG, "refractory count out of range");
                 buf[pid] = (uint8_t)v;
             } else {
-                std::memcpy(buf.data() + (size_t)pid * 4, static_cast<const uint8_t*>(host) + (size_t)g * 4, 4);
+                std::memcpy(buf.data() + (size_t)pid * esz, static_cast<const uint8_t*>(host) + (size_t)g * esz, esz);
             }
         }
     CUDA_TRY(c, cudaMemcpy(p, buf.data(), buf.size(), cudaMemcpyHostToDevice));
@@ -1284,7 +1303,7 @@ snn_status snn_get_info(snn_ctx* c, snn_info* info)
     info->edges = c->E;
     info->device_bytes = c->bytes_held;
     info->edge_bytes = c->use_tiled ? edge_bytes_of(c->packed ? kWPacked : (c->w16 ? kW16 : kWF32)) : (c->w16 ? 6u : 8u);
-    info->reserved = 0;
+    info->model_state_bytes = (uint32_t)c->mbytes;
     return SNN_OK;
 }
 
