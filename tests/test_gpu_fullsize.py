@@ -7,6 +7,9 @@ but its networks are independent and each one's random draws depend only on
 oracle and must match bit for bit.  The 1M-neuron Vogels network and the
 100k-neuron Brunel+ network are compared whole over a window of steps.
 """
+import dataclasses
+import functools
+
 import numpy as np
 import pytest
 
@@ -16,8 +19,8 @@ import snn_inputs as si
 pytestmark = pytest.mark.gpu
 
 
-def _gpu_run(gpu, prob, steps, chunks=(100,)):
-    net = gpu.Network(prob, log_capacity=prob.n * steps // 5 + (1 << 20))
+def _gpu_run(gpu, prob, steps, chunks=(100,), **kw):
+    net = gpu.Network(prob, log_capacity=prob.n * steps // 5 + (1 << 20), **kw)
     t = 0
     for c in chunks:
         net.step(c)
@@ -25,17 +28,27 @@ def _gpu_run(gpu, prob, steps, chunks=(100,)):
     if t < steps:
         net.step(steps - t)
     net.sync()
-    out = {"steps_ids": net.spikes(), "V": net.read("V"), "info": net.info(), "counters": net.counters()}
+    V = net.read("model")["V"] if prob.model == gpu.MODEL_BRUNEL_LIF else net.read("V")
+    out = {"steps_ids": net.spikes(), "V": V, "info": net.info(), "counters": net.counters()}
     if prob.stdp:
         out["w"] = net.read("w")
     net.close()
     return out
 
 
-def test_batched_sweep_256_sampled_networks(gpu):
-    prob = si.batched_sweep(256, base_seed=1, n_steps=0)
+@functools.lru_cache(maxsize=1)
+def _sweep():
+    return si.batched_sweep(256, base_seed=1, n_steps=0)
+
+
+@pytest.mark.parametrize("model", ["fixed", "generic"])
+def test_batched_sweep_256_sampled_networks(gpu, model):
+    """model: the fixed Brunel kernel, or Brunel from the LIF building block
+    through the generic update (bench.py's generic_update line)."""
+    prob = _sweep()
     steps = 400  # crosses the first re-plan of the work items (step 256)
-    g = _gpu_run(gpu, prob, steps, chunks=(100, 200))
+    run = prob if model == "fixed" else dataclasses.replace(prob, model=gpu.MODEL_BRUNEL_LIF)
+    g = _gpu_run(gpu, run, steps, chunks=(100, 200))
     assert g["info"]["receive"] == "tiled"
     gs, gi = g["steps_ids"]
     sizes = np.array([inst.n for inst in prob.instances])
@@ -62,10 +75,17 @@ def test_vogels_1m_whole_network(gpu):
     assert g["counters"]["events"] == o["events"]
 
 
-def test_brunel_stdp_100k_whole_network(gpu):
+@functools.lru_cache(maxsize=1)
+def _stdp_100k():
     prob = si.brunel_stdp_100k(seed=1, n_steps=300)
-    g = _gpu_run(gpu, prob, 300)
-    o = oracle.run(prob)
+    return prob, oracle.run(prob)
+
+
+@pytest.mark.parametrize("lazy", [False, True])
+def test_brunel_stdp_100k_whole_network(gpu, lazy):
+    """Eager Update Synapses, and the lazy form bench.py times (64-step history)."""
+    prob, o = _stdp_100k()
+    g = _gpu_run(gpu, prob, 300, lazy=lazy)
     gs, gi = g["steps_ids"]
     assert len(o["ids"]) > 1000
     assert np.array_equal(gs, o["steps"]) and np.array_equal(gi, o["ids"])
