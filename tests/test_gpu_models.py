@@ -113,3 +113,26 @@ def test_model_state_write_is_read_back(gpu):
         assert len(net.spikes()[1]) == 0
     finally:
         net.close()
+
+
+def test_large_raster_readout(gpu):
+    """A raster larger than the readout's chunked host copy (150M spikes, 600 MB
+    per array): the tutorial model on a ring of 1M neurons that all start active
+    fires every neuron at every step."""
+    n, T = 1_000_000, 150
+    inst = si.brunel_instance(n, k=0)
+    inst.n_exc = n
+    prob = si.Problem(model=MODEL_RELAY, instances=[inst], delay=1, seed=1, n_steps=T,
+                      inst_off=np.array([0, n], np.uint32), row_off=np.arange(n + 1, dtype=np.uint64),
+                      tgt=((np.arange(n, dtype=np.uint64) + 1) % n).astype(np.uint32), w=np.full(n, 5, np.int32))
+    net = gpu.Network(prob, receive=RECV["tiled"], log_capacity=n * T)
+    try:
+        net.step(T)
+        net.sync()
+        steps, ids = net.spikes()
+        assert len(ids) == n * T
+        assert (steps.reshape(T, n) == np.arange(T, dtype=np.uint32)[:, None]).all()
+        assert (ids.reshape(T, n) == np.arange(n, dtype=np.uint32)[None, :]).all()
+        assert net.counters()["events"] == n * T
+    finally:
+        net.close()
