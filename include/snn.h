@@ -128,8 +128,13 @@ typedef struct {
 
 /* Device memory and stream.  alloc/free may be NULL (then cudaMalloc and
  * cudaFree are used).  stream is a cudaStream_t (NULL: the legacy default
- * stream).  The library calls alloc/free only inside snn_create,
- * snn_build_graph and snn_destroy. */
+ * stream).  The library calls alloc/free inside snn_create,
+ * snn_build_graph and snn_destroy, for temporary buffers inside
+ * snn_read_spikes, snn_read_state / snn_write_state of SNN_FIELD_W and
+ * snn_stats, and (SNN_RECV_BULK only) inside snn_step at the two re-plans
+ * of its work items; snn_rate_cv_static allocates nothing.  Large host copies go
+ * through a pinned staging ring of 256 MB that the context allocates at
+ * the first one and frees in snn_destroy. */
 typedef struct {
     void* (*alloc)(size_t bytes, void* stream, void* user);
     void (*free)(void* ptr, void* stream, void* user);

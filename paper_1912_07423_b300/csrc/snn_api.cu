@@ -86,6 +86,13 @@ struct snn_ctx {
     std::vector<uint64_t> inst_edges;  // synapses of each instance
     uint4* rinfo = nullptr;            // row records (start, length, meta)
 
+    // pinned staging ring of the large host copies (snn_build_graph's upload,
+    // snn_read_spikes' readout), allocated at the first one and kept
+    static constexpr int kStageBufs = 4;
+    static constexpr size_t kStageChunk = 64u << 20;
+    void* stage[kStageBufs] = {};
+    cudaEvent_t stage_ev[kStageBufs] = {};
+
     // CUDA graphs: one step, and steps_per_graph steps
     cudaGraphExec_t g1 = nullptr, gk = nullptr;
     uint32_t k_steps = 0;
@@ -419,27 +426,39 @@ snn_status pack_edges(snn_ctx* c)
     return SNN_OK;
 }
 
-// Host -> device copy of a large pageable array: chunks are copied into a
-// ring of pinned buffers by several host threads while the DMA engine
-// moves the previous chunks (the driver's own staging of pageable memory
-// copies with one thread).  Waits for the stream.
+// The context's pinned staging ring, allocated at its first use.
+snn_status stage_ring(snn_ctx* c)
+{
+    for (int i = 0; i < snn_ctx::kStageBufs; ++i) {
+        if (!c->stage[i] && cudaHostAlloc(&c->stage[i], snn_ctx::kStageChunk, cudaHostAllocDefault) != cudaSuccess) {
+            c->stage[i] = nullptr;
+            return fail(c, SNN_E_CUDA, "pinned staging buffers");
+        }
+        if (!c->stage_ev[i] && cudaEventCreateWithFlags(&c->stage_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+            c->stage_ev[i] = nullptr;
+            return fail(c, SNN_E_CUDA, "staging events");
+        }
+    }
+    return SNN_OK;
+}
+
+// Host -> device copy of a large pageable array: chunks are copied into the
+// pinned ring by several host threads while the DMA engine moves the
+// previous chunks (the driver's own staging of pageable memory copies with
+// one thread).  Waits for the stream.
 snn_status upload(snn_ctx* c, void* dst, const void* src, size_t bytes, cudaStream_t s)
 {
-    constexpr size_t kChunk = 64u << 20;
-    constexpr int kBufs = 4;
+    constexpr size_t kChunk = snn_ctx::kStageChunk;
+    constexpr int kBufs = snn_ctx::kStageBufs;
     if (bytes <= kChunk) {
         CUDA_TRY(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
         return SNN_OK;
     }
     const unsigned hw = std::thread::hardware_concurrency();
     const unsigned nth = std::max(1u, std::min(16u, hw ? hw : 1u));
-    void* buf[kBufs] = {};
-    cudaEvent_t done[kBufs] = {};
-    snn_status st = SNN_OK;
-    for (int i = 0; i < kBufs && st == SNN_OK; ++i)
-        if (cudaHostAlloc(&buf[i], kChunk, cudaHostAllocDefault) != cudaSuccess ||
-            cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming) != cudaSuccess)
-            st = fail(c, SNN_E_CUDA, "pinned staging buffers");
+    snn_status st = stage_ring(c);
+    void** buf = c->stage;
+    cudaEvent_t* done = c->stage_ev;
     for (size_t off = 0, i = 0; off < bytes && st == SNN_OK; off += kChunk, i = (i + 1) % kBufs) {
         const size_t len = std::min(kChunk, bytes - off);
         if (cudaEventSynchronize(done[i]) != cudaSuccess) {
@@ -459,10 +478,53 @@ snn_status upload(snn_ctx* c, void* dst, const void* src, size_t bytes, cudaStre
             st = fail(c, SNN_E_CUDA, "staged copy");
     }
     if (cudaStreamSynchronize(s) != cudaSuccess && st == SNN_OK) st = fail(c, SNN_E_CUDA, "staged copy");
-    for (int i = 0; i < kBufs; ++i) {
-        if (done[i]) cudaEventDestroy(done[i]);
-        if (buf[i]) cudaFreeHost(buf[i]);
+    return st;
+}
+
+// Device -> host copy into a large pageable array, the reverse of upload():
+// the DMA engine fills a ring of pinned buffers ahead while several host
+// threads copy the filled ones out (and take the page faults of a fresh
+// destination in parallel).  Waits for the stream.
+snn_status download(snn_ctx* c, void* dst, const void* src, size_t bytes, cudaStream_t s)
+{
+    constexpr size_t kChunk = snn_ctx::kStageChunk;
+    constexpr int kBufs = snn_ctx::kStageBufs;
+    if (bytes <= kChunk) {
+        CUDA_TRY(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        return SNN_OK;
     }
+    const unsigned hw = std::thread::hardware_concurrency();
+    const unsigned nth = std::max(1u, std::min(16u, hw ? hw : 1u));
+    snn_status st = stage_ring(c);
+    void** buf = c->stage;
+    cudaEvent_t* full = c->stage_ev;
+    const size_t n = (bytes + kChunk - 1) / kChunk;
+    auto fetch = [&](size_t k) {
+        const size_t off = k * kChunk, len = std::min(kChunk, bytes - off);
+        if (cudaMemcpyAsync(buf[k % kBufs], static_cast<const char*>(src) + off, len, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaEventRecord(full[k % kBufs], s) != cudaSuccess)
+            st = fail(c, SNN_E_CUDA, "staged copy");
+    };
+    for (size_t k = 0; k < n && k < (size_t)kBufs && st == SNN_OK; ++k) fetch(k);
+    for (size_t k = 0; k < n && st == SNN_OK; ++k) {
+        if (cudaEventSynchronize(full[k % kBufs]) != cudaSuccess) {
+            st = fail(c, SNN_E_CUDA, "staging wait");
+            break;
+        }
+        const size_t off = k * kChunk, len = std::min(kChunk, bytes - off);
+        const char* from = static_cast<const char*>(buf[k % kBufs]);
+        char* to = static_cast<char*>(dst) + off;
+        const size_t part = (len / nth + 63) & ~size_t(63);
+        std::vector<std::thread> pool;
+        for (unsigned t = 1; t < nth && t * part < len; ++t)
+            pool.emplace_back([=]() { std::memcpy(to + t * part, from + t * part, std::min(part, len - t * part)); });
+        std::memcpy(to, from, std::min(part, len));
+        for (auto& th : pool) th.join();
+        if (k + kBufs < n) fetch(k + kBufs);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess && st == SNN_OK) st = fail(c, SNN_E_CUDA, "staged copy");
     return st;
 }
 
@@ -1101,14 +1163,14 @@ snn_status snn_read_spikes(snn_ctx* c, uint32_t t0, uint32_t t1, uint32_t* steps
         k_raster_split<<<grid_for(n, 256), 256, 0, c->stream>>>(db.Current(), n, t0, split, split + n);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(steps, split, n * 4, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ids, split + n, n * 4, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    snn_status out = SNN_OK;
+    if (e == cudaSuccess) out = download(c, steps, split, n * 4, c->stream);
+    if (e == cudaSuccess && out == SNN_OK) out = download(c, ids, split + n, n * 4, c->stream);
     dev_free(c, tmp);
     dev_free(c, ka);
     dev_free(c, kb);
     if (e != cudaSuccess) return fail(c, SNN_E_CUDA, "raster readout: %s", cudaGetErrorString(e));
-    return SNN_OK;
+    return out;
 }
 
 snn_status snn_log_clear(snn_ctx* c)
@@ -1313,6 +1375,10 @@ void snn_destroy(snn_ctx* c)
     if (c->stream || c->cap_stream) cudaStreamSynchronize(c->stream);
     drop_graphs(c);
     while (!c->allocs.empty()) dev_free(c, c->allocs.back().p);
+    for (int i = 0; i < snn_ctx::kStageBufs; ++i) {
+        if (c->stage_ev[i]) cudaEventDestroy(c->stage_ev[i]);
+        if (c->stage[i]) cudaFreeHost(c->stage[i]);
+    }
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->side) cudaStreamDestroy(c->side);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
