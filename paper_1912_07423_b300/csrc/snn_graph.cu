@@ -20,7 +20,13 @@
 // back 256 at a time, sums each lane's 8, scans the lanes' sums across the
 // warp and overwrites slot k with a + round(c_{k+1} f) + k, c the exclusive
 // running sum and f = (b - a - n) / total (binary32, at most b - a - n).  Every operation is rounded as
-// written (-fmad=false), so the values do not depend on the launch.
+// written (-fmad=false), so the values do not depend on the launch.  A job
+// of at most 1,024 spacings (n <= 1023, the rows of the networks here) takes
+// one pass instead: the lanes draw the Philox blocks in turn into shared
+// memory, lane l takes spacings 32 l .. 32 l + 31 from there, the lanes'
+// sums are scanned, each lane turns its 32 running sums into values, and
+// the values leave through shared memory in coalesced stores -- the output
+// is written once.
 #include <cuda_runtime.h>
 
 
@@ -30,6 +36,7 @@
 namespace {
 
 constexpr unsigned kJobThreads = 256;
+constexpr uint32_t kOnePass = 1024;  // most spacings (n + 1) a job takes in one pass: 32 per lane
 constexpr uint32_t kMaxScale = 1u << 24;  // b - a - n: the binary32 ratio keeps every integer below it apart
 
 // flag of an invalid job, one per device (no allocation)
@@ -69,6 +76,70 @@ __device__ __forceinline__ void spacings8(uint64_t seed, uint32_t j, uint32_t g,
 // access both fall in (nearly) distinct banks
 __device__ __forceinline__ uint32_t stage_at(uint32_t k) { return (k >> 3) * 9u + (k & 7u); }
 
+// Jobs of at most kOnePass spacings, one pass each (see the file's header).
+__global__ void __launch_bounds__(kJobThreads) k_expand_short(const snn_job* __restrict__ jobs, uint64_t n_jobs,
+                                                              uint64_t seed, uint32_t* __restrict__ out,
+                                                              uint64_t out_len)
+{
+    __shared__ uint32_t stage1[kJobThreads / 32][kOnePass + 32];  // value k at k + k / 32
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t* st1 = stage1[threadIdx.x >> 5];
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t jj = warp; jj < n_jobs; jj += nwarps) {
+        const snn_job J = jobs[jj];
+        const uint32_t j = (uint32_t)jj;
+        if (J.b < J.a || J.n > J.b - J.a || J.b - J.a - J.n > kMaxScale || J.o > out_len || J.n > out_len - J.o)
+            continue;  // reported by k_expand_jobs
+        const uint32_t n = J.n, M = J.b - J.a - J.n;
+        if (n == 0 || n >= kOnePass) continue;
+        uint32_t* dst = out + J.o;
+        // draw: lane l takes Philox blocks l, l + 32, ... (spacings 8 g .. 8 g + 7)
+#pragma unroll 1
+        for (uint32_t g = lane; g * 8 <= n; g += 32) {
+            uint32_t w8[8];
+            spacings8(seed, j, g, w8);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const uint32_t k = 8 * g + i;
+                st1[k + (k >> 5)] = w8[i];
+            }
+        }
+        __syncwarp();
+        // lane l: spacings 32 l .. 32 l + 31 (none beyond n), summed, then
+        // replaced in place by their values
+        unsigned long long s32 = 0;
+#pragma unroll 8
+        for (int i = 0; i < 32; ++i)
+            if (32 * lane + i <= n) s32 += st1[33 * lane + i];
+        unsigned long long incl = s32;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
+        const float f = total ? __fdiv_rn(__uint2float_rn(M), __ull2float_rn(total)) : 0.0f;
+        unsigned long long c = incl - s32;
+#pragma unroll 1
+        for (int i = 0; i < 32; ++i) {
+            const uint32_t k = 32 * lane + i;
+            if (k >= n) break;
+            c += st1[33 * lane + i];  // c_{k+1}
+            uint32_t r = __float2uint_rz(__fadd_rn(__fmul_rn(__ull2float_rn(c), f), 0.5f));
+            r = r > M ? M : r;
+            st1[33 * lane + i] = J.a + r + k;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const uint32_t k = 32 * i + lane;
+            if (k < n) dst[k] = st1[33 * i + lane];
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void __launch_bounds__(kJobThreads) k_expand_jobs(const snn_job* __restrict__ jobs, uint64_t n_jobs,
                                                              uint64_t seed, uint32_t* __restrict__ out,
                                                              uint64_t out_len)
@@ -88,6 +159,8 @@ __global__ void __launch_bounds__(kJobThreads) k_expand_jobs(const snn_job* __re
         const uint32_t n = J.n, M = J.b - J.a - J.n;
         if (n == 0) continue;
         uint32_t* dst = out + J.o;
+        if (n < kOnePass) continue;  // k_expand_short's
+
         // pass 1: the total of the n + 1 spacings; q_0 .. q_{n-1} parked in
         // the output (lane l draws block l of every 256 spacings)
         unsigned long long part = 0;
@@ -176,6 +249,7 @@ extern "C" snn_status snn_expand_jobs(const snn_job* jobs, uint64_t n_jobs, uint
     const uint64_t warps_needed = n_jobs;
     const uint64_t blocks = (warps_needed * 32 + kJobThreads - 1) / kJobThreads;
     const uint32_t grid = (uint32_t)(blocks < (uint64_t)sms * 16 ? blocks : (uint64_t)sms * 16);
+    k_expand_short<<<grid, kJobThreads, 0, s>>>(jobs, n_jobs, seed, out, out_len);
     k_expand_jobs<<<grid, kJobThreads, 0, s>>>(jobs, n_jobs, seed, out, out_len);
     if (cudaGetLastError() != cudaSuccess) return SNN_E_CUDA;
     unsigned int h = 0;

@@ -39,9 +39,12 @@ def test_random_jobs_match_the_oracle(gpu, seed):
 
 def test_long_jobs_and_edges(gpu):
     """Jobs longer than one pass of the warp (256 spacings) and several of
-    them, full ranges, an empty job and the largest scale (2^24)."""
+    them, full ranges, an empty job, the largest scale (2^24), and the sizes
+    around the lanes' 32 spacings and the one-pass limit (1,024 spacings)."""
     specs = [(0, 0, 10), (1, 0, 1), (50, 100, 150), (255, 0, 300), (256, 7, 10000), (257, 0, 1 << 20),
-             (100000, 5, 5 + 100000 + (1 << 24)), (70000, 0, 70000), (3, 0, 3), (1000, 123, 2000)]
+             (100000, 5, 5 + 100000 + (1 << 24)), (70000, 0, 70000), (3, 0, 3), (1000, 123, 2000),
+             (31, 0, 40), (32, 9, 100), (33, 0, 33), (1022, 0, 5000), (1023, 17, 1 << 24), (1024, 0, 1024),
+             (1025, 3, 9000)]
     jobs = np.zeros(len(specs), dtype=oracle.JOB_DTYPE)
     o = 0
     for i, (n, a, b) in enumerate(specs):
@@ -51,6 +54,8 @@ def test_long_jobs_and_edges(gpu):
     g = _gpu(gpu, jobs, 7, o)
     assert np.array_equal(g, ref)
     full = 1 + 50 + 255 + 256 + 257 + 100000  # offset of the 70,000-of-70,000 job
+    one = sum(n for n, _, _ in specs[:15])  # offset of the 1,024-of-1,024 job
+    assert g[one:one + 1024].tolist() == list(range(1024))
     assert g[full:full + 70000].tolist() == list(range(70000))
 
 
