@@ -91,11 +91,17 @@ def peaks():
         return 6400.0, "fallback"
 
 
+def replica_seed(rank: int) -> int:
+    """Graph seed base of the replica on `rank` (each rank simulates its own
+    networks: weak scaling, no data-path collective)."""
+    return 1 + 1000 * rank
+
+
 def workload(name: str, rank: int):
     if name == "batched_sweep_256":
-        return si.batched_sweep(256, base_seed=1 + 1000 * rank, n_steps=0)
+        return si.batched_sweep(256, base_seed=replica_seed(rank), n_steps=0)
     if name.startswith("batched_sweep_"):  # a smaller sweep of the same recipe (profiling)
-        return si.batched_sweep(int(name.rsplit("_", 1)[1]), base_seed=1 + 1000 * rank, n_steps=0)
+        return si.batched_sweep(int(name.rsplit("_", 1)[1]), base_seed=replica_seed(rank), n_steps=0)
     if name == "vogels_1m":
         return si.vogels_1m(seed=1 + rank, n_steps=0)
     if name == "brunel_12k5":
@@ -257,6 +263,24 @@ def step_bytes(prob, edge_bytes: int, events: int, delivered: int, emitted: int,
             emitted * B_SPIKE_EMITTED + per_neuron * prob.n * steps)
 
 
+def reduce_over_ranks(x: float, op: str, dist, device) -> float:
+    """x combined over the ranks ("max": the slowest rank's time, "sum": the
+    job's events); dist is torch.distributed or None (one rank), device the
+    tensor device of the process group's backend (cuda for NCCL, cpu for gloo)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_value(events: float, seconds: float, dist, device) -> float:
+    """Whole-job throughput of weakly scaled replicas: the events of all ranks
+    over the slowest rank's time."""
+    return reduce_over_ranks(events, "sum", dist, device) / reduce_over_ranks(seconds, "max", dist, device)
+
+
 def run_ours(args, rank, world, dist):
     import torch
     import paper_1912_07423_b300 as snn
@@ -274,18 +298,10 @@ def run_ours(args, rank, world, dist):
             dist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_over_ranks(x, "max", dist, dev)
 
     def sum_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return reduce_over_ranks(x, "sum", dist, dev)
 
     def timed(net, steps):
         stream = net.stream
