@@ -534,12 +534,13 @@ snn_status download(snn_ctx* c, void* dst, const void* src, size_t bytes, cudaSt
 // receive pays per edge for an L2 atomic.  Tiled is taken for graphs of at
 // least kAutoMinEdges synapses whose rows reach each tile with
 // kAutoMinSegment edges or more on average (edge-weighted over instances,
-// targets taken as uniform over the instance).  Measured: Vogels 1M (rows of
-// 1,000 over 70 tiles) 38 us tiled vs 20 us global per step; Vogels 4k
-// (320k synapses) 12.4 vs 6.8 us; Brunel 12.5k (12.5M synapses, one tile)
-// 11.4 vs 14.7 us; the 256-network sweep 65 vs 188 us.
+// targets taken as uniform over the instance).  Measured per step, tiled vs
+// global: Vogels 1M (rows of 1,000 over 70 tiles: 14 edges each) 38 vs
+// 20 us; Brunel+ 100k (4 tiles, 250 each) 42.6 vs 33.4 us; Vogels 4k (320k
+// synapses) 12.4 vs 6.8 us; Brunel 12.5k (one tile, 1,250) 11.6 vs 13.9 us;
+// the 256-network sweep (714 on average) 65 vs 188 us.
 constexpr uint64_t kAutoMinEdges = 4000000;
-constexpr double kAutoMinSegment = 64.0;
+constexpr double kAutoMinSegment = 400.0;
 
 bool auto_tiled(const snn_ctx* c)
 {
