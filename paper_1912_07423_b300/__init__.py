@@ -195,7 +195,16 @@ class _TorchMemory:
 class Network:
     """One simulator context: many network instances stepped together.
 
-    problem: an ``snn_inputs.Problem`` (model, instances, delay, seed, graph).
+    problem: an ``snn_inputs.Problem`` (model, instances, delay, seed, graph);
+    its model may be VOGELS, BRUNEL or a generic-update model (MODEL_RELAY,
+    MODEL_BRUNEL_LIF), whose state records ``read("model")`` returns.
+    w16: 16-bit weight codes (else binary32).  receive: RECV_*.
+    packed: let the tiled receive read 4-byte packed edges where it can.
+    lazy, lazy_fifo: with STDP, the lazy Update Synapses and its history
+    length in steps (0: 64).  stats: keep spike counts and ISI moments.
+    steps_per_graph, tune_steps: CUDA-graph length and bulk re-plan step.
+    build_graph: upload problem's graph now (else call build_graph).
+    Every call goes through the C ABI; there is no CPU path.
     """
 
     def __init__(self, problem, *, w16: bool = True, receive: int = RECV_AUTO, log_capacity: int | None = None,
