@@ -455,7 +455,9 @@ def run_reference(args, rank):
     import oracle
     prob = workload(args.workload, rank)
     sub, desc = oracle_sample(prob)
-    sub.n_steps = args.warmup + args.steps
+    # the run starts at step 0, where the delay FIFO delivers nothing for d
+    # steps: at least 100 steps, so that a short run still measures events
+    sub.n_steps = max(args.warmup + args.steps, 100)
     t0 = time.perf_counter()
     r = oracle.run(sub)
     dt = time.perf_counter() - t0
