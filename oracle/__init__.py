@@ -20,6 +20,9 @@ Parity status of the functions (what pins each one, see tests/test_oracle_*):
   relay_raster -- a hand-worked raster of a four-neuron graph, breadth-first
                  search over the CSR, and the binary32 run of the same graph
                  in its LIF relay form
+  expand_jobs -- Fig. 2's printed spacings, running sums and normalised
+                 values, the binary64 library logarithm, the exact law of
+                 each rounded order statistic, full and empty ranges
 """
 from __future__ import annotations
 
