@@ -45,6 +45,7 @@ struct snn_ctx {
     bool vogels = false, stdp = false, w16 = false, stats = false;
     bool lazy = false;             // lazy Update Synapses (SNN_F_LAZY)
     bool generic = false;          // a model of the generic update (snn_models.cuh)
+    int npt = kUpdateNeurons;      // neurons per thread of the fixed models' update
     void* mstate = nullptr;        // generic models: one state record per neuron slot
     size_t mbytes = 0;             // bytes of one record
     bool graph_loaded = false;
@@ -215,6 +216,25 @@ int sm_count()
     return sms;
 }
 
+// k_update<MODEL, SYN, STATS, npt> on Np slots
+template <int MODEL, int SYN>
+void launch_update(const Net& n, bool stats, int npt, uint32_t Np, cudaStream_t s)
+{
+    if (npt == kUpdateNeuronsSmall) {
+        const uint32_t blocks = grid_for(Np / kUpdateNeuronsSmall, 256);
+        if (stats)
+            k_update<MODEL, SYN, true, kUpdateNeuronsSmall><<<blocks, 256, 0, s>>>(n);
+        else
+            k_update<MODEL, SYN, false, kUpdateNeuronsSmall><<<blocks, 256, 0, s>>>(n);
+    } else {
+        const uint32_t blocks = grid_for(Np / kUpdateNeurons, 256);
+        if (stats)
+            k_update<MODEL, SYN, true, kUpdateNeurons><<<blocks, 256, 0, s>>>(n);
+        else
+            k_update<MODEL, SYN, false, kUpdateNeurons><<<blocks, 256, 0, s>>>(n);
+    }
+}
+
 // The kernels of one timestep, in pipeline order (Fig. 1).  ev, if given,
 // holds kPhases + 1 events recorded between the phases.
 constexpr int kPhases = 6;
@@ -247,29 +267,16 @@ snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr, u
             k_stdp_depress<false><<<wblocks, 256, 0, s>>>(n);
     }
     if (ev) cudaEventRecord(ev[1], s);
-    if (c->generic) {
+    if (c->generic)
         launch_update_model(c->cfg.model, n, c->mstate, c->stats, ublocks, s);
-    } else if (c->vogels) {
-        if (c->stats)
-            k_update<0, 0, true><<<ublocks, 256, 0, s>>>(n);
-        else
-            k_update<0, 0, false><<<ublocks, 256, 0, s>>>(n);
-    } else if (c->lazy) {
-        if (c->stats)
-            k_update<1, 2, true><<<ublocks, 256, 0, s>>>(n);
-        else
-            k_update<1, 2, false><<<ublocks, 256, 0, s>>>(n);
-    } else if (c->stdp) {
-        if (c->stats)
-            k_update<1, 1, true><<<ublocks, 256, 0, s>>>(n);
-        else
-            k_update<1, 1, false><<<ublocks, 256, 0, s>>>(n);
-    } else {
-        if (c->stats)
-            k_update<1, 0, true><<<ublocks, 256, 0, s>>>(n);
-        else
-            k_update<1, 0, false><<<ublocks, 256, 0, s>>>(n);
-    }
+    else if (c->vogels)
+        launch_update<0, 0>(n, c->stats, c->npt, c->Np, s);
+    else if (c->lazy)
+        launch_update<1, 2>(n, c->stats, c->npt, c->Np, s);
+    else if (c->stdp)
+        launch_update<1, 1>(n, c->stats, c->npt, c->Np, s);
+    else
+        launch_update<1, 0>(n, c->stats, c->npt, c->Np, s);
     if (ev) cudaEventRecord(ev[2], s);
     if (c->lazy) {
         if (c->w16)
@@ -675,6 +682,10 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     c->stream = (cudaStream_t)c->dev.stream;
     c->vogels = cfg->model == SNN_VOGELS_CUBA;
     c->generic = is_generic_model(cfg->model);
+    // 4 neurons per thread when 8 would give fewer 256-thread blocks than
+    // SMs (a 100k-neuron network: 49 blocks; 4 per thread measured 4 %
+    // faster there, 8 % slower on the 3.2M-neuron sweep)
+    c->npt = (uint64_t)Np / kUpdateNeurons / 256 < (uint64_t)sm_count() ? kUpdateNeuronsSmall : kUpdateNeurons;
     c->mbytes = model_state_bytes(cfg->model);
     c->stdp = (cfg->flags & SNN_F_STDP) != 0;
     c->lazy = c->stdp && (cfg->flags & SNN_F_LAZY) != 0;

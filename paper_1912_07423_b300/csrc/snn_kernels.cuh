@@ -15,18 +15,20 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // ---------------------------------------------------------------------------
 // Update Neurons (Section III-A-1): N_t -> N'_{t+1}, spikers -> S_t.
-// One thread advances kUpdateNeurons consecutive neurons (128-bit loads per
+// One thread advances NPT (8, or 4 for small networks) consecutive neurons (128-bit loads per
 // float field) and computes one Philox block, whose 8 words are the Poisson
 // draws of an aligned group of 8 neurons.  Spiking ids are
 // compacted per warp with a shuffle scan and one atomicAdd on the queue
 // index (Section III-A-2: queues are arrays with an atomic index).
 // ---------------------------------------------------------------------------
 
-constexpr int kUpdateNeurons = 8;  // neurons per thread of the update (4 or 8)
-// a warp of the update covers 32 * kUpdateNeurons neurons and must never
-// cross an instance (instances are padded to 256 slots): its spikes go to
-// one instance's queue region with one atomicAdd
+constexpr int kUpdateNeurons = 8;       // neurons per thread of the update
+constexpr int kUpdateNeuronsSmall = 4;  // ... when 8 per thread would leave SMs without a block
+// a warp of the update covers 32 * NPT neurons and must never cross an
+// instance (instances are padded to 256 slots): its spikes go to one
+// instance's queue region with one atomicAdd
 static_assert(256 % (32 * kUpdateNeurons) == 0, "a warp of the update must stay inside one 256-slot block");
+static_assert(256 % (32 * kUpdateNeuronsSmall) == 0, "a warp of the update must stay inside one 256-slot block");
 
 // Number of Poisson thresholds <= u (thresholds T[0..nT) ascending): the
 // instance's bucket table S gives the count below the start of u's bucket
@@ -42,10 +44,10 @@ __device__ __forceinline__ uint32_t poisson_count(const uint32_t* __restrict__ T
 
 // SYN: 0 no plasticity, 1 eager traces (x and y every step), 2 lazy (y, the
 // ring of decayed y, the spike history and the expiry queue)
-template <int MODEL, int SYN, bool STATS>
+template <int MODEL, int SYN, bool STATS, int NPT>
 __global__ void __launch_bounds__(256) k_update(Net n)
 {
-    constexpr int NPT = kUpdateNeurons;  // neurons per thread
+    static_assert(NPT == 4 || NPT == 8, "one Philox block serves 8 neurons");
     const unsigned long long t = n.ctl->t + n.k;
     // per-step bookkeeping of the previous step (its kernels have finished):
     // fold its queue indices into the counters, clear the next step's indices
@@ -278,8 +280,8 @@ __global__ void __launch_bounds__(256) k_update(Net n)
     }
     if (SYN != 0) {
         // 32 / NPT lanes cover one 32-neuron bitmask word
-        constexpr uint32_t L = 32 / kUpdateNeurons;
-        uint32_t word = spk << (kUpdateNeurons * (lane & (L - 1u)));
+        constexpr uint32_t L = 32 / NPT;
+        uint32_t word = spk << (NPT * (lane & (L - 1u)));
 #pragma unroll
         for (uint32_t o = 1; o < L; o <<= 1) word |= __shfl_xor_sync(kFull, word, o);
         if (active && (lane & (L - 1u)) == 0) n.bits[(size_t)slot_q * (n.Np >> 5) + (id0 >> 5)] = word;
