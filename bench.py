@@ -156,7 +156,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # raw samples (the JSON line carries their summary); SNN_CLOCKS_DIR keeps them elsewhere
+        import tempfile
+        self.path = os.path.join(os.environ.get("SNN_CLOCKS_DIR", tempfile.gettempdir()), f"snn_clocks_rank{index}.csv")
 
     def start(self):
         try:
