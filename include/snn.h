@@ -84,8 +84,8 @@ typedef enum {
 
 /* snn_config.receive */
 #define SNN_RECV_AUTO 0u   /* the library picks: tiled when the rows are sorted, the graph has at least
-                              4M synapses and a row reaches each target tile with 400 or more edges on
-                              average; else global */
+                              200M synapses and a row reaches each target tile with 400 or more edges
+                              on average; else global */
 #define SNN_RECV_GLOBAL 1u /* warp per spike, red.global.add into L2-resident accumulators */
 #define SNN_RECV_TILED 2u  /* target-tiled, accumulators in shared memory; needs sorted rows */
 #define SNN_RECV_BULK 3u   /* as TILED, rows staged into shared memory by bulk async copies */

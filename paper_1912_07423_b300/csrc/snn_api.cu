@@ -538,15 +538,17 @@ snn_status download(snn_ctx* c, void* dst, const void* src, size_t bytes, cudaSt
 // SNN_RECV_AUTO: the target-tiled receive pays per step for its plan and its
 // persistent launch, and per spike for every tile its row reaches (a row
 // record, split offsets, partial vectors at both ends); the global-atomic
-// receive pays per edge for an L2 atomic.  Tiled is taken for graphs of at
-// least kAutoMinEdges synapses whose rows reach each tile with
-// kAutoMinSegment edges or more on average (edge-weighted over instances,
-// targets taken as uniform over the instance).  Measured per step, tiled vs
-// global: Vogels 1M (rows of 1,000 over 70 tiles: 14 edges each) 38 vs
-// 20 us; Brunel+ 100k (4 tiles, 250 each) 42.6 vs 33.4 us; Vogels 4k (320k
-// synapses) 12.4 vs 6.8 us; Brunel 12.5k (one tile, 1,250) 11.6 vs 13.9 us;
-// the 256-network sweep (714 on average) 65 vs 188 us.
-constexpr uint64_t kAutoMinEdges = 4000000;
+// receive pays per edge for an L2 atomic and spreads few spikes over the
+// whole grid in row pieces.  Tiled is taken for graphs of at least
+// kAutoMinEdges synapses whose rows reach each tile with kAutoMinSegment
+// edges or more on average (edge-weighted over instances, targets taken as
+// uniform over the instance).  Measured per step, tiled vs global: Vogels
+// 1M (rows of 1,000 over 70 tiles: 14 edges each) 38 vs 16 us; Brunel+ 100k
+// (4 tiles, 250 each) 42.6 vs 31.8 us; Vogels 4k (320k synapses) 12.4 vs
+// 6.4 us; Brunel 12.5k (one tile, 1,250 edges; 15.6M synapses) 11.5 vs
+// 9.2 us with binary32 weights; the 256-network sweep (2.9e9 synapses, 714
+// on average) 65 vs 188 us.
+constexpr uint64_t kAutoMinEdges = 200000000;
 constexpr double kAutoMinSegment = 400.0;
 
 bool auto_tiled(const snn_ctx* c)

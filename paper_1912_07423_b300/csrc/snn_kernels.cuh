@@ -414,42 +414,68 @@ __device__ __forceinline__ void for_each_spike(const Net& n, unsigned long long 
 }
 
 // ---------------------------------------------------------------------------
-// Receive Spikes (Section III-A-2), global-accumulator form: one warp per
-// spike of S_{t-d+1} walks the spiker's row with coalesced target/weight
-// loads and adds the weights with red.global.add into the L2-resident
-// int32 accumulators of the targets (order-independent integer sums).
+// Receive Spikes (Section III-A-2), global-accumulator form: the rows of the
+// spikes of S_{t-d+1} are cut into K pieces, K the largest power of two up
+// to 16 that still leaves every warp of the grid one piece, and a warp walks
+// its piece with coalesced target/weight loads and adds the weights with
+// red.global.add into the L2-resident int32 accumulators of the targets
+// (order-independent integer sums).  With few spikes per step the pieces
+// keep the grid busy; a warp per whole row would walk it alone.
 // ---------------------------------------------------------------------------
 template <bool W16>
 __global__ void __launch_bounds__(256) k_receive_global(Net n)
 {
     const unsigned long long t = n.ctl->t + n.k;
     if (t + 1 < n.d) return;
+    const unsigned long long ts = t + 1 - n.d;
     const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t* qs = n.q + (size_t)(ts % n.D) * n.Np;
+    const unsigned int* ic = n.icount + (size_t)(ts & (n.cr - 1)) * n.n_inst;
+    uint32_t total = 0;
+    for (uint32_t b = 0; b < n.n_inst; ++b) total += ic[b];
+    uint32_t lk = 0;  // K = 2^lk pieces per row
+    while (lk < 4 && ((uint64_t)total << (lk + 1)) <= nwarps) ++lk;
     unsigned long long ev = 0;
-    for_each_spike(n, t + 1 - n.d, [&](uint32_t j) {
-        const uint64_t beg = __ldg(n.roff + j), end = __ldg(n.roff + j + 1);
-        const uint32_t meta = __ldg(n.meta + j);
-        const uint32_t shift = meta & 31u;
-        int32_t* acc = (meta & 0x80u) ? n.acc1 : n.acc0;
-        ev += end - beg;
-        uint64_t e = beg + lane;
-        for (; e + 96 < end; e += 128) {
-            uint32_t tg[4];
-            int32_t wv[4];
+    // units u = (spike u >> lk, piece u & (K - 1)), instance by instance
+    uint64_t u = warp;
+    uint32_t base = 0;  // spikes of the instances before b
+    for (uint32_t b = 0; b < n.n_inst; ++b) {
+        const uint32_t cnt = ic[b];
+        if ((u >> lk) < base + cnt) {
+            const uint32_t* qb = qs + __ldg(&n.inst[b].pbase);
+            for (; (u >> lk) < base + cnt; u += nwarps) {
+                const uint32_t j = qb[(u >> lk) - base];
+                const uint64_t beg = __ldg(n.roff + j), end = __ldg(n.roff + j + 1);
+                const uint64_t len = end - beg, c = u & ((1u << lk) - 1u);
+                const uint64_t pb = beg + ((len * c) >> lk), pe = beg + ((len * (c + 1)) >> lk);
+                const uint32_t meta = __ldg(n.meta + j);
+                const uint32_t shift = meta & 31u;
+                int32_t* acc = (meta & 0x80u) ? n.acc1 : n.acc0;
+                ev += pe - pb;
+                uint64_t e = pb + lane;
+                for (; e + 96 < pe; e += 128) {
+                    uint32_t tg[4];
+                    int32_t wv[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                tg[u] = __ldg(n.tgt + e + 32 * u);
-                wv[u] = W16 ? ((int32_t)__ldg(n.w16 + e + 32 * u) << shift) : __float2int_rz(__ldg(n.w32 + e + 32 * u));
+                    for (int k = 0; k < 4; ++k) {
+                        tg[k] = __ldg(n.tgt + e + 32 * k);
+                        wv[k] = W16 ? ((int32_t)__ldg(n.w16 + e + 32 * k) << shift)
+                                    : __float2int_rz(__ldg(n.w32 + e + 32 * k));
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) atomicAdd(acc + tg[k], wv[k]);
+                }
+                for (; e < pe; e += 32) {
+                    const uint32_t tg = __ldg(n.tgt + e);
+                    const int32_t wv = W16 ? ((int32_t)__ldg(n.w16 + e) << shift) : __float2int_rz(__ldg(n.w32 + e));
+                    atomicAdd(acc + tg, wv);
+                }
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) atomicAdd(acc + tg[u], wv[u]);
         }
-        for (; e < end; e += 32) {
-            const uint32_t tg = __ldg(n.tgt + e);
-            const int32_t wv = W16 ? ((int32_t)__ldg(n.w16 + e) << shift) : __float2int_rz(__ldg(n.w32 + e));
-            atomicAdd(acc + tg, wv);
-        }
-    });
+        base += cnt;
+    }
     if (lane == 0 && ev) atomicAdd(&n.ctl->events, ev);
 }
 

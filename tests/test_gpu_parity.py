@@ -366,12 +366,12 @@ def test_instances_larger_than_one_tile(gpu, model, receive):
     assert_parity(g, o, prob)
 
 
-@pytest.mark.parametrize("name,expect", [("vogels_4k", "global"), ("brunel_12k5", "tiled"),
+@pytest.mark.parametrize("name,expect", [("vogels_4k", "global"), ("brunel_12k5", "global"),
                                          ("brunel_stdp_100k", "global")])
 def test_automatic_receive_choice(gpu, name, expect):
-    """SNN_RECV_AUTO takes the tiled receive for graphs of 4M+ synapses whose
-    rows reach each tile with 400+ edges, else the global-atomic one: Vogels
-    4k is too small, Brunel+ 100k reaches 4 tiles with 250 edges each."""
+    """SNN_RECV_AUTO takes the tiled receive for graphs of 200M+ synapses whose
+    rows reach each tile with 400+ edges (the sweep: tests/test_gpu_fullsize),
+    else the global-atomic one."""
     prob = getattr(si, name)(seed=1, n_steps=0)
     net = gpu.Network(prob, receive=0, log_capacity=1 << 16)
     try:
