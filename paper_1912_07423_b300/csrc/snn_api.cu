@@ -684,10 +684,13 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     c->stream = (cudaStream_t)c->dev.stream;
     c->vogels = cfg->model == SNN_VOGELS_CUBA;
     c->generic = is_generic_model(cfg->model);
-    // 4 neurons per thread when 8 would give fewer 256-thread blocks than
-    // SMs (a 100k-neuron network: 49 blocks; 4 per thread measured 4 %
-    // faster there, 8 % slower on the 3.2M-neuron sweep)
-    c->npt = (uint64_t)Np / kUpdateNeurons / 256 < (uint64_t)sm_count() ? kUpdateNeuronsSmall : kUpdateNeurons;
+    // 4 neurons per thread for Vogels (its state takes 64 registers at 8 per
+    // thread: 4 measured 10 % faster on the 1M-neuron network), and for
+    // Brunel when 8 would give fewer 256-thread blocks than SMs (a
+    // 100k-neuron network: 49 blocks; 4 % faster there, 8 % slower on the
+    // 3.2M-neuron sweep)
+    c->npt = (c->vogels || (uint64_t)Np / kUpdateNeurons / 256 < (uint64_t)sm_count()) ? kUpdateNeuronsSmall
+                                                                                       : kUpdateNeurons;
     c->mbytes = model_state_bytes(cfg->model);
     c->stdp = (cfg->flags & SNN_F_STDP) != 0;
     c->lazy = c->stdp && (cfg->flags & SNN_F_LAZY) != 0;
