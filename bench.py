@@ -483,8 +483,8 @@ def main():
     ap.add_argument("--workload", default="batched_sweep_256")
     ap.add_argument("--profile-steps", type=int, default=500)
     ap.add_argument("--receive", choices=["auto", "global", "tiled", "bulk"], default="auto")
-    ap.add_argument("--plasticity", choices=["eager", "lazy"], default="lazy",
-                    help="Update Synapses form for plastic workloads (brunel_stdp_100k)")
+    ap.add_argument("--plasticity", choices=["eager", "lazy"], default="eager",
+                    help="Update Synapses form for plastic workloads (brunel_stdp_100k; eager measured faster)")
     ap.add_argument("--lazy-fifo", type=int, default=0, help="lazy plasticity: history length (0: 64)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -392,90 +392,80 @@ __global__ void k_raster_split(const unsigned long long* __restrict__ keys, uint
 // next step's update kernel.
 __global__ void k_advance(Ctl* ctl, uint32_t steps) { ctl->t += steps; }
 
-// Visit the spikes of one queue slot, instance by instance, spreading them
-// over all warps of the grid: f(j) for every spiking padded id j.
+// Visit the spikes of one queue slot cut into K = 2^lk pieces each, K the
+// largest power of two up to 16 that still leaves every warp of the grid
+// one piece: f(j, c, lk) for piece c of spike j, a warp per piece.  With a
+// few hundred spikes per step a warp per whole row would walk it alone.
 template <class F>
-__device__ __forceinline__ void for_each_spike(const Net& n, unsigned long long ts, F f)
+__device__ __forceinline__ void for_each_piece(const Net& n, unsigned long long ts, F f)
 {
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    const uint32_t sc = (uint32_t)(ts & (n.cr - 1));
-    const uint32_t* qs = n.q + (size_t)(ts % n.D) * n.Np;
-    const unsigned int* ic = n.icount + (size_t)sc * n.n_inst;
-    uint32_t next = warp, base = 0;
-    for (uint32_t b = 0; b < n.n_inst; ++b) {
-        const uint32_t cnt = ic[b];
-        if (next < base + cnt) {
-            const uint32_t* qb = qs + __ldg(&n.inst[b].pbase);
-            for (; next < base + cnt; next += nwarps) f(qb[next - base]);
-        }
-        base += cnt;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Receive Spikes (Section III-A-2), global-accumulator form: the rows of the
-// spikes of S_{t-d+1} are cut into K pieces, K the largest power of two up
-// to 16 that still leaves every warp of the grid one piece, and a warp walks
-// its piece with coalesced target/weight loads and adds the weights with
-// red.global.add into the L2-resident int32 accumulators of the targets
-// (order-independent integer sums).  With few spikes per step the pieces
-// keep the grid busy; a warp per whole row would walk it alone.
-// ---------------------------------------------------------------------------
-template <bool W16>
-__global__ void __launch_bounds__(256) k_receive_global(Net n)
-{
-    const unsigned long long t = n.ctl->t + n.k;
-    if (t + 1 < n.d) return;
-    const unsigned long long ts = t + 1 - n.d;
-    const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t* qs = n.q + (size_t)(ts % n.D) * n.Np;
     const unsigned int* ic = n.icount + (size_t)(ts & (n.cr - 1)) * n.n_inst;
     uint32_t total = 0;
     for (uint32_t b = 0; b < n.n_inst; ++b) total += ic[b];
-    uint32_t lk = 0;  // K = 2^lk pieces per row
+    uint32_t lk = 0;
     while (lk < 4 && ((uint64_t)total << (lk + 1)) <= nwarps) ++lk;
-    unsigned long long ev = 0;
-    // units u = (spike u >> lk, piece u & (K - 1)), instance by instance
-    uint64_t u = warp;
-    uint32_t base = 0;  // spikes of the instances before b
+    uint64_t u = warp;  // unit: piece u & (K - 1) of spike u >> lk, instance by instance
+    uint32_t base = 0;
     for (uint32_t b = 0; b < n.n_inst; ++b) {
         const uint32_t cnt = ic[b];
         if ((u >> lk) < base + cnt) {
             const uint32_t* qb = qs + __ldg(&n.inst[b].pbase);
-            for (; (u >> lk) < base + cnt; u += nwarps) {
-                const uint32_t j = qb[(u >> lk) - base];
-                const uint64_t beg = __ldg(n.roff + j), end = __ldg(n.roff + j + 1);
-                const uint64_t len = end - beg, c = u & ((1u << lk) - 1u);
-                const uint64_t pb = beg + ((len * c) >> lk), pe = beg + ((len * (c + 1)) >> lk);
-                const uint32_t meta = __ldg(n.meta + j);
-                const uint32_t shift = meta & 31u;
-                int32_t* acc = (meta & 0x80u) ? n.acc1 : n.acc0;
-                ev += pe - pb;
-                uint64_t e = pb + lane;
-                for (; e + 96 < pe; e += 128) {
-                    uint32_t tg[4];
-                    int32_t wv[4];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        tg[k] = __ldg(n.tgt + e + 32 * k);
-                        wv[k] = W16 ? ((int32_t)__ldg(n.w16 + e + 32 * k) << shift)
-                                    : __float2int_rz(__ldg(n.w32 + e + 32 * k));
-                    }
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) atomicAdd(acc + tg[k], wv[k]);
-                }
-                for (; e < pe; e += 32) {
-                    const uint32_t tg = __ldg(n.tgt + e);
-                    const int32_t wv = W16 ? ((int32_t)__ldg(n.w16 + e) << shift) : __float2int_rz(__ldg(n.w32 + e));
-                    atomicAdd(acc + tg, wv);
-                }
-            }
+            for (; (u >> lk) < base + cnt; u += nwarps) f(qb[(u >> lk) - base], (uint32_t)(u & ((1u << lk) - 1u)), lk);
         }
         base += cnt;
     }
+}
+
+// Piece c of 2^lk of the index range [beg, end).
+__device__ __forceinline__ void piece_of(uint64_t beg, uint64_t end, uint32_t c, uint32_t lk, uint64_t& pb, uint64_t& pe)
+{
+    const uint64_t len = end - beg;
+    pb = beg + ((len * c) >> lk);
+    pe = beg + ((len * (c + 1)) >> lk);
+}
+
+// ---------------------------------------------------------------------------
+// Receive Spikes (Section III-A-2), global-accumulator form: a warp per
+// piece of the rows of S_{t-d+1} (for_each_piece) walks it with coalesced
+// target/weight loads and adds the weights with red.global.add into the
+// L2-resident int32 accumulators of the targets (order-independent integer
+// sums).
+// ---------------------------------------------------------------------------
+template <bool W16>
+__global__ void __launch_bounds__(256) k_receive_global(Net n)
+{
+    const unsigned long long t = n.ctl->t + n.k;
+    if (t + 1 < n.d) return;
+    const uint32_t lane = lane_id();
+    unsigned long long ev = 0;
+    for_each_piece(n, t + 1 - n.d, [&](uint32_t j, uint32_t c, uint32_t lk) {
+        uint64_t pb, pe;
+        piece_of(__ldg(n.roff + j), __ldg(n.roff + j + 1), c, lk, pb, pe);
+        const uint32_t meta = __ldg(n.meta + j);
+        const uint32_t shift = meta & 31u;
+        int32_t* acc = (meta & 0x80u) ? n.acc1 : n.acc0;
+        ev += pe - pb;
+        uint64_t e = pb + lane;
+        for (; e + 96 < pe; e += 128) {
+            uint32_t tg[4];
+            int32_t wv[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                tg[k] = __ldg(n.tgt + e + 32 * k);
+                wv[k] = W16 ? ((int32_t)__ldg(n.w16 + e + 32 * k) << shift) : __float2int_rz(__ldg(n.w32 + e + 32 * k));
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) atomicAdd(acc + tg[k], wv[k]);
+        }
+        for (; e < pe; e += 32) {
+            const uint32_t tg = __ldg(n.tgt + e);
+            const int32_t wv = W16 ? ((int32_t)__ldg(n.w16 + e) << shift) : __float2int_rz(__ldg(n.w32 + e));
+            atomicAdd(acc + tg, wv);
+        }
+    });
     if (lane == 0 && ev) atomicAdd(&n.ctl->events, ev);
 }
 
@@ -491,14 +481,15 @@ __global__ void __launch_bounds__(256) k_stdp_depress(Net n)
     const unsigned long long t = n.ctl->t + n.k;
     if (t < n.d) return;
     const uint32_t lane = lane_id();
-    for_each_spike(n, t - n.d, [&](uint32_t j) {
+    for_each_piece(n, t - n.d, [&](uint32_t j, uint32_t c, uint32_t lk) {
         const uint32_t meta = __ldg(n.meta + j);
         if (!(meta & 0x40u)) return;  // inhibitory source: no plastic synapses
         const InstDev* I = n.inst + __ldg(n.inst_of_w32 + (j >> 5));
         const uint32_t pbase = __ldg(&I->pbase), n_exc = __ldg(&I->n_exc);
         const float Pn = __ldg(&I->Pn), Am = __ldg(&I->Am);
         const int32_t wmax = __ldg(&I->wmax);
-        const uint64_t beg = __ldg(n.roff + j), end = __ldg(n.roff + j + 1);
+        uint64_t beg, end;
+        piece_of(__ldg(n.roff + j), __ldg(n.roff + j + 1), c, lk, beg, end);
         for (uint64_t e = beg + lane; e < end; e += 32) {
             const uint32_t i = __ldg(n.tgt + e);
             if (i - pbase >= n_exc) continue;
@@ -523,11 +514,12 @@ __global__ void __launch_bounds__(256) k_stdp_potentiate(Net n)
 {
     const unsigned long long t = n.ctl->t + n.k;
     const uint32_t lane = lane_id();
-    for_each_spike(n, t, [&](uint32_t i) {
+    for_each_piece(n, t, [&](uint32_t i, uint32_t c, uint32_t lk) {
         const InstDev* I = n.inst + __ldg(n.inst_of_w32 + (i >> 5));
         const float Ap = __ldg(&I->Ap);
         const int32_t wmax = __ldg(&I->wmax);
-        const uint64_t beg = __ldg(n.coff + i), end = __ldg(n.coff + i + 1);
+        uint64_t beg, end;
+        piece_of(__ldg(n.coff + i), __ldg(n.coff + i + 1), c, lk, beg, end);
         for (uint64_t k = beg + lane; k < end; k += 32) {
             const uint32_t e = __ldg(n.cedge + k);
             const uint32_t j = __ldg(n.cpre + k);
