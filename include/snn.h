@@ -80,13 +80,16 @@ typedef enum {
                           synapses of a row are left stale and brought up to date in one pass
                           when the row transmits a spike or when its age reaches the history
                           length lazy_fifo; the weights and traces are the eager rule's, bit for
-                          bit (snn_read_state / snn_write_state bring every row up to date first) */
+                          bit (snn_read_state / snn_write_state bring every row up to date first).
+                          For the pair rule here the eager form, which touches only the rows of the
+                          arriving spikes and the columns of the spiking neurons, measured faster */
 
 /* snn_config.receive */
 #define SNN_RECV_AUTO 0u   /* the library picks: tiled when the rows are sorted, the graph has at least
                               200M synapses and a row reaches each target tile with 400 or more edges
                               on average; else global */
-#define SNN_RECV_GLOBAL 1u /* warp per spike, red.global.add into L2-resident accumulators */
+#define SNN_RECV_GLOBAL 1u /* a warp per row piece (rows cut into up to 16 pieces when a step has few
+                              spikes), red.global.add into L2-resident accumulators */
 #define SNN_RECV_TILED 2u  /* target-tiled, accumulators in shared memory; needs sorted rows */
 #define SNN_RECV_BULK 3u   /* as TILED, rows staged into shared memory by bulk async copies */
 
