@@ -74,6 +74,12 @@ def test_lazy_binary32_weights(gpu):
     assert_parity(run_lazy(gpu, prob, w16=False, receive="global"), o, prob)
 
 
+def test_lazy_with_the_bulk_receive(gpu):
+    prob = small_stdp(n_steps=1500)
+    o = oracle.run(prob)
+    assert_parity(run_lazy(gpu, prob, fifo=40, receive="bulk"), o, prob)
+
+
 @pytest.mark.parametrize("fifo", [2, 50])
 def test_lazy_delay_one(gpu, fifo):
     """d = 1: a row transmits at the step its neuron spikes, and the

@@ -48,7 +48,7 @@ def assert_brunel_parity(g, o):
     assert g["counters"]["spikes"] == len(o["ids"])
 
 
-@pytest.mark.parametrize("receive", ["global", "tiled"])
+@pytest.mark.parametrize("receive", ["global", "tiled", "bulk"])
 def test_brunel_lif_equals_brunel_oracle(gpu, receive):
     """Brunel 12.5k, 15-step delay, 2,000 steps, through the generic update."""
     prob = si.brunel_12k5(seed=1, n_steps=2000)

@@ -161,6 +161,19 @@ def test_forced_spike_arrives_after_d_steps(gpu, d, model):
         assert_parity(g, o, prob)
 
 
+def test_largest_delay(gpu):
+    """d = 1,000 steps, the largest delay the library takes (a ring of 1,000
+    spike queues): a Brunel network driven to spike, 1,300 steps, every
+    receive form."""
+    prob = si.brunel_stdp_100k(seed=8, n_steps=1300, n=1200, k=120)
+    prob.stdp = False
+    prob.delay = 1000
+    o = oracle.run(prob)
+    assert int((o["steps"] >= 1000).sum()) > 100  # spikes after the first deliveries
+    for receive in ("global", "tiled", "bulk"):
+        assert_parity(run_gpu(gpu, prob, receive=receive), o, prob)
+
+
 @pytest.mark.parametrize("d", [1, 3])
 def test_relay_network(gpu, d):
     """Listing 1's ping-pong network: S_{t+d} = out-neighbours(S_t)."""
