@@ -110,6 +110,8 @@ def _load():
             lib.orc_job_from_uniforms.restype = ctypes.c_int
             lib.orc_expand_jobs.argtypes = [_vp, ctypes.c_uint64, ctypes.c_uint64, _vp, ctypes.c_uint64]
             lib.orc_expand_jobs.restype = ctypes.c_int
+            lib.orc_expand_job.argtypes = [_vp, ctypes.c_uint64, ctypes.c_uint64, _vp]
+            lib.orc_expand_job.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -168,6 +170,17 @@ def expand_jobs(jobs: np.ndarray, seed: int, out_len: int) -> np.ndarray:
     if st != 0:
         raise OracleError(f"expand_jobs failed ({st})")
     return out[:out_len]
+
+
+def expand_job(job, index: int, seed: int) -> np.ndarray:
+    """One job (a JOB_DTYPE record) alone, by its index in the job list
+    (which keys its random draws): its n values."""
+    rec = np.ascontiguousarray(np.asarray(job, dtype=JOB_DTYPE).reshape(1))
+    out = np.zeros(max(int(rec["n"][0]), 1), dtype=np.uint32)
+    st = _load().orc_expand_job(_ptr(rec), index, seed, _ptr(out))
+    if st != 0:
+        raise OracleError(f"expand_job failed ({st})")
+    return out[:int(rec["n"][0])]
 
 
 def poisson_table(lam: float) -> np.ndarray:

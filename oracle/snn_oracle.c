@@ -654,20 +654,27 @@ int orc_job_from_uniforms(const float* u, uint32_t n, uint32_t a, uint32_t b, ui
     return ORC_OK;
 }
 
-/* Every job j draws its uniforms from Philox4x64-10 with key (seed, j),
- * counter (k >> 3, 0, 2, 0), word k & 7: u_k = (word >> 8 + 1) 2^-24. */
+/* Job j draws its uniforms from Philox4x64-10 with key (seed, j), counter
+ * (k >> 3, 0, 2, 0), word k & 7: u_k = (word >> 8 + 1) 2^-24; its n values
+ * go to out[0 .. n). */
+int orc_expand_job(const orc_job* J, uint64_t j, uint64_t seed, uint32_t* out)
+{
+    if (J->b < J->a || J->n > J->b - J->a || J->b - J->a - J->n > (1u << 24)) return ORC_E_ARG;
+    float* u = (float*)malloc(((size_t)J->n + 1) * sizeof(float));
+    if (!u) return ORC_E_NOMEM;
+    for (uint32_t k = 0; k <= J->n; ++k)
+        u[k] = (float)((orc_rand_word(seed, j, k, 0, 2) >> 8) + 1u) * (1.0f / 16777216.0f);
+    const int st = orc_job_from_uniforms(u, J->n, J->a, J->b, NULL, NULL, out);
+    free(u);
+    return st;
+}
+
 int orc_expand_jobs(const orc_job* jobs, uint64_t n_jobs, uint64_t seed, uint32_t* out, uint64_t out_len)
 {
     for (uint64_t j = 0; j < n_jobs; ++j) {
         const orc_job J = jobs[j];
-        if (J.b < J.a || J.n > J.b - J.a || J.b - J.a - J.n > (1u << 24) || J.o > out_len || J.n > out_len - J.o)
-            return ORC_E_ARG;
-        float* u = (float*)malloc(((size_t)J.n + 1) * sizeof(float));
-        if (!u) return ORC_E_NOMEM;
-        for (uint32_t k = 0; k <= J.n; ++k)
-            u[k] = (float)((orc_rand_word(seed, j, k, 0, 2) >> 8) + 1u) * (1.0f / 16777216.0f);
-        const int st = orc_job_from_uniforms(u, J.n, J.a, J.b, NULL, NULL, out + J.o);
-        free(u);
+        if (J.o > out_len || J.n > out_len - J.o) return ORC_E_ARG;
+        const int st = orc_expand_job(&J, j, seed, out + J.o);
         if (st != ORC_OK) return st;
     }
     return ORC_OK;

@@ -89,6 +89,8 @@ float orc_neg_ln(float u);
 int orc_job_from_uniforms(const float* u, uint32_t n, uint32_t a, uint32_t b, uint32_t* q, uint64_t* c,
                           uint32_t* out);
 int orc_expand_jobs(const orc_job* jobs, uint64_t n_jobs, uint64_t seed, uint32_t* out, uint64_t out_len);
+/* One job alone, by its index j in the job list (the index keys its random draws). */
+int orc_expand_job(const orc_job* job, uint64_t j, uint64_t seed, uint32_t* out);
 void orc_raster_free(orc_raster* R);
 
 #endif

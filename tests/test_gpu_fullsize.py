@@ -92,3 +92,32 @@ def test_brunel_stdp_100k_whole_network(gpu, lazy):
     assert np.array_equal(g["V"].view(np.uint32), o["V"].view(np.uint32))
     assert np.array_equal(g["w"], o["w"])
     assert not np.array_equal(o["w"], prob.w)
+
+
+def test_sweep_adjacency_construction_sampled_jobs(gpu):
+    """snn_expand_jobs (Fig. 2) on the sweep's full job list, as bench.py times
+    it (one job per neuron: its out-degree of values from its own instance,
+    2.9e9 values), checked job by job against the oracle on a sample: the
+    shortest and longest jobs, the first and last, and random ones."""
+    import torch
+    prob = _sweep()
+    deg = np.diff(prob.row_off.astype(np.int64)).astype(np.uint32)
+    inst_of = np.repeat(np.arange(len(prob.instances)), np.diff(prob.inst_off.astype(np.int64)))
+    jobs = np.zeros(prob.n, dtype=gpu.JOB_DTYPE)
+    jobs["n"] = deg
+    jobs["a"] = prob.inst_off[inst_of]
+    jobs["b"] = prob.inst_off[inst_of + 1]
+    jobs["o"] = prob.row_off[:-1]
+    E = int(prob.row_off[-1])
+    out = torch.empty(E, dtype=torch.int32, device="cuda")
+    gpu.expand_jobs(torch.from_numpy(jobs.view(np.uint8)).cuda(), 1, E, out=out)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    sample = {0, prob.n - 1, int(np.argmin(deg)), int(np.argmax(deg))} | set(rng.integers(0, prob.n, 60).tolist())
+    ojobs = jobs.view(oracle.JOB_DTYPE)
+    for j in sorted(sample):
+        lo, n = int(jobs["o"][j]), int(jobs["n"][j])
+        got = out[lo:lo + n].cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, oracle.expand_job(ojobs[j], j, 1)), j
+    del out
+    torch.cuda.empty_cache()

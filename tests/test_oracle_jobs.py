@@ -163,3 +163,22 @@ def test_job_rejects_bad_jobs():
     bad[0] = (1, 0, 10, 0, 20)  # outside the output
     with pytest.raises(oracle.OracleError):
         oracle.expand_jobs(bad, seed=1, out_len=20)
+
+
+def test_a_job_alone_equals_its_part_of_the_list():
+    """expand_job(job, j, seed) draws job j's uniforms by its index alone: the
+    same values the whole list writes at its offset (what a sampled check of
+    a large job list relies on)."""
+    rng = np.random.default_rng(11)
+    jobs = np.zeros(40, dtype=oracle.JOB_DTYPE)
+    o = 0
+    for j in range(40):
+        a = int(rng.integers(0, 1000))
+        w = int(rng.integers(1, 3000))
+        n = int(rng.integers(0, w + 1))
+        jobs[j] = (n, a, a + w, 0, o)
+        o += n
+    whole = oracle.expand_jobs(jobs, seed=9, out_len=o)
+    for j in range(40):
+        lo, n = int(jobs[j]["o"]), int(jobs[j]["n"])
+        assert np.array_equal(oracle.expand_job(jobs[j], j, 9), whole[lo:lo + n]), j
