@@ -1,5 +1,8 @@
 // snn_kernels.cuh -- the per-step kernels of libsnn (Update Neurons with
-// spike compaction, Update Synapses, Receive Spikes) and the set-up kernels.
+// spike compaction, Update Synapses in its eager and lazy forms, the
+// global-atomic Receive Spikes) and the set-up kernels.  The tiled and
+// bulk-copy receives are in snn_tiled.cuh and snn_bulk.cuh, the generic
+// update in snn_models.cuh.
 //
 // Arithmetic of the neuron update: binary32, one rounding per operation, no
 // contraction (explicit __f*_rn intrinsics; the file is also compiled with
@@ -15,11 +18,12 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // ---------------------------------------------------------------------------
 // Update Neurons (Section III-A-1): N_t -> N'_{t+1}, spikers -> S_t.
-// One thread advances NPT (8, or 4 for small networks) consecutive neurons (128-bit loads per
-// float field) and computes one Philox block, whose 8 words are the Poisson
-// draws of an aligned group of 8 neurons.  Spiking ids are
-// compacted per warp with a shuffle scan and one atomicAdd on the queue
-// index (Section III-A-2: queues are arrays with an atomic index).
+// One thread advances NPT consecutive neurons (8, or 4 where 8 would leave
+// SMs idle or take too many registers; 128-bit loads per float field) and
+// computes one Philox block, whose 8 words are the Poisson draws of an
+// aligned group of 8 neurons.  Spiking ids are compacted per warp with a
+// shuffle scan and one atomicAdd on the queue index (Section III-A-2:
+// queues are arrays with an atomic index).
 // ---------------------------------------------------------------------------
 
 constexpr int kUpdateNeurons = 8;       // neurons per thread of the update
