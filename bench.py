@@ -369,7 +369,7 @@ def run_ours(args, rank, world, dist):
                       "l2": "inputs larger than L2 (edge arrays %.1f GB >> 126 MB)" % (prob.n_edges * 6 / 1e9),
                       "parallelism": f"replicas x{world} (independent networks, no collective)",
                       "graph_gen_s": round(t_gen, 1), "device_bytes": mem,
-                      **({"plasticity": ("lazy, history %d steps" % (args.lazy_fifo or 64)) if lazy else "eager"}
+                      **({"plasticity": ("lazy, history %d steps" % (args.lazy_fifo or 128)) if lazy else "eager"}
                          if prob.stdp else {})},
            "realtime_factor": args.steps * DT_MS * 1e-3 / t_max,
            "spikes": int(sp_main), "events": int(ev_main),
@@ -485,7 +485,7 @@ def main():
     ap.add_argument("--receive", choices=["auto", "global", "tiled", "bulk"], default="auto")
     ap.add_argument("--plasticity", choices=["eager", "lazy"], default="eager",
                     help="Update Synapses form for plastic workloads (brunel_stdp_100k; eager measured faster)")
-    ap.add_argument("--lazy-fifo", type=int, default=0, help="lazy plasticity: history length (0: 64)")
+    ap.add_argument("--lazy-fifo", type=int, default=0, help="lazy plasticity: history length (0: 128)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-generic", action="store_true", help="skip timing the generic-update model")

@@ -108,8 +108,9 @@ typedef struct {
                               never); the tiled receive cuts its items on the device every
                               step.  Results do not depend on the plan */
     uint32_t lazy_fifo;    /* SNN_F_LAZY: steps of spike and trace history kept per neuron, the
-                              longest a row stays stale (0: 64, the most one 64-bit history
-                              word holds; else 2..64.  The paper's queue holds 50 entries) */
+                              longest a row stays stale (0: 128, the most the two 64-bit
+                              history words of a neuron hold; else 2..128.  The paper's queue
+                              holds 50 entries) */
 } snn_config;
 
 /* Model constants of one instance.  Times in ms, potentials in mV, integer
@@ -151,7 +152,7 @@ typedef struct {
  * The instances are concatenated in order: global neuron id = sum of the
  * sizes of the earlier instances + local id.  Returns SNN_E_ARG for an
  * invalid config (delay 0 or > 1000, refractory > 255, STDP without
- * Brunel, SNN_F_LAZY without SNN_F_STDP or lazy_fifo outside 2..64,
+ * Brunel, SNN_F_LAZY without SNN_F_STDP or lazy_fifo outside 2..128,
  * non-positive time constants, lambda < 0 or so large that the Poisson
  * table would exceed 64 entries).  *out is NULL on failure. */
 snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn_device* dev,

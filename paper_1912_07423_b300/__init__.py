@@ -201,7 +201,7 @@ class Network:
     w16: 16-bit weight codes (else binary32).  receive: RECV_*.
     packed: let the tiled receive read 4-byte packed edges where it can.
     lazy, lazy_fifo: with STDP, the lazy Update Synapses and its history
-    length in steps (0: 64).  stats: keep spike counts and ISI moments.
+    length in steps (0: 128).  stats: keep spike counts and ISI moments.
     steps_per_graph, tune_steps: CUDA-graph length and bulk re-plan step.
     build_graph: upload problem's graph now (else call build_graph).
     Every call goes through the C ABI; there is no CPU path.

@@ -394,7 +394,7 @@ snn_status init_state(snn_ctx* c)
     }
     if (c->lazy) {
         CUDA_TRY(c, cudaMemsetAsync(c->net.xcount, 0, 2 * sizeof(unsigned int), c->stream));
-        CUDA_TRY(c, cudaMemsetAsync(c->net.hist, 0, (size_t)c->Np * sizeof(unsigned long long), c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(c->net.hist, 0, (size_t)c->Np * 2 * sizeof(unsigned long long), c->stream));
     }
     // control block: step 0, empty queues and log
     CUDA_TRY(c, cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), c->stream));
@@ -787,7 +787,7 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     }
     if (c->lazy) {
         n.F = cfg->lazy_fifo ? cfg->lazy_fifo : (uint32_t)kLazyMaxF;
-        n.hist = alloc_n<unsigned long long>(c, Npz);
+        n.hist = alloc_n<unsigned long long>(c, 2 * Npz);
         n.yring = alloc_n<float>(c, (size_t)n.F * Npz);
         n.age = alloc_n<uint32_t>(c, Npz);
         n.xq = alloc_n<uint32_t>(c, Npz);

@@ -16,8 +16,9 @@
 //              with its own index icount[t % CR][b], so a consumer can take
 //              one network's spikes alone.  With STDP a ring of D spike
 //              bitmasks uint32[D][Np/32] sits beside it (Section III-A-1).
-//   lazy     : lazy Update Synapses (Section III-A-1): per neuron a 64-bit
-//              spike history hist[Np] (bit k: spiked at step t - k), a ring
+//   lazy     : lazy Update Synapses (Section III-A-1): per neuron a 128-bit
+//              spike history hist[2 Np] (bit k: spiked at step t - k; words
+//              2i and 2i+1 hold bits 0..63 and 64..127 of neuron i), a ring
 //              of F decayed postsynaptic traces yring[F][Np] (slot s % F:
 //              y(s-1) P-, the value a depression at step s reads), the
 //              row's age[Np] (first step whose synaptic events the row has
@@ -70,7 +71,7 @@ struct Net {
     uint32_t Np, D, d, n_inst;
     uint32_t cr;               // count-ring length, a power of two >= D + 2
     uint32_t k;                // this launch's step offset: step = ctl->t + k
-    uint32_t F;                // lazy plasticity: history length in steps (2..64)
+    uint32_t F;                // lazy plasticity: history length in steps (2..128)
     uint64_t seed;
     unsigned int* count;       // |S_t| over all instances at [t % cr]
     unsigned int* icount;      // |S_t| of instance b at [(t % cr) * n_inst + b]
@@ -101,7 +102,7 @@ struct Net {
     const uint32_t* cpre;   // STDP: padded presynaptic id of each plastic in-edge
     uint32_t* q;            // D * Np
     uint32_t* bits;         // D * Np/32
-    unsigned long long* hist;  // lazy: spike history per neuron, bit k = step t - k
+    unsigned long long* hist;  // lazy: 2 words of spike history per neuron, bit k = step t - k
     float* yring;           // lazy: F * Np decayed postsynaptic traces
     uint32_t* age;          // lazy: per row, first step not applied | arrival pending << 31
     uint32_t* xq;           // lazy: rows whose history expires at this step

@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256) k_update(Net n)
                         }
                     }
                     float ys[NPT], yp[NPT];
-                    unsigned long long hs[NPT];
+                    ulonglong2 hs[NPT];  // 128-bit histories: .x bits 0..63, .y bits 64..127
                     uint32_t ag[NPT];
 #pragma unroll
                     for (int h = 0; h < NPT / 4; ++h) {
@@ -232,8 +232,7 @@ __global__ void __launch_bounds__(256) k_update(Net n)
                         *reinterpret_cast<uint4*>(ag + 4 * h) = *reinterpret_cast<const uint4*>(n.age + id0 + 4 * h);
                     }
 #pragma unroll
-                    for (int h = 0; h < NPT / 2; ++h)
-                        *reinterpret_cast<ulonglong2*>(hs + 2 * h) = *reinterpret_cast<const ulonglong2*>(n.hist + id0 + 2 * h);
+                    for (int k = 0; k < NPT; ++k) hs[k] = *reinterpret_cast<const ulonglong2*>(n.hist + 2 * (id0 + k));
                     const uint32_t t31 = (uint32_t)t & 0x7fffffffu;
 #pragma unroll
                     for (int k = 0; k < NPT; ++k) {
@@ -242,7 +241,8 @@ __global__ void __launch_bounds__(256) k_update(Net n)
                         const float yd = __fmul_rn(ys[k], Pn);
                         yp[k] = yd;
                         ys[k] = (spk >> k & 1u) ? __fadd_rn(yd, 1.0f) : yd;
-                        hs[k] = (hs[k] << 1) | (unsigned long long)(spk >> k & 1u);
+                        hs[k].y = (hs[k].y << 1) | (hs[k].x >> 63);
+                        hs[k].x = (hs[k].x << 1) | (unsigned long long)(spk >> k & 1u);
                         const uint32_t lag = (t31 - (ag[k] & 0x7fffffffu)) & 0x7fffffffu;  // t - age
                         if (lag + 1u >= n.F && !(tx >> k & 1u)) xexp |= 1u << k;
                     }
@@ -253,8 +253,7 @@ __global__ void __launch_bounds__(256) k_update(Net n)
                         *reinterpret_cast<float4*>(yr + id0 + 4 * h) = *reinterpret_cast<float4*>(yp + 4 * h);
                     }
 #pragma unroll
-                    for (int h = 0; h < NPT / 2; ++h)
-                        *reinterpret_cast<ulonglong2*>(n.hist + id0 + 2 * h) = *reinterpret_cast<ulonglong2*>(hs + 2 * h);
+                    for (int k = 0; k < NPT; ++k) *reinterpret_cast<ulonglong2*>(n.hist + 2 * (id0 + k)) = hs[k];
                 }
             }
             have = true;
@@ -551,10 +550,10 @@ __global__ void __launch_bounds__(256) k_stdp_potentiate(Net n)
 // (an arrival follows a transmission by one step, and a transmission always
 // brings the row up to date, so only step a can hold one: a flag records
 // it), with y_i(a-1) P- from the ring, then the potentiation of every step
-// s in a..t at which i spiked (bit t - s of i's history), with x_j(s).
+// s in a..t at which i spiked (bit t - s of i's 128-bit history), with x_j(s).
 // The row's x(s) sequence is the eager one, one rounded multiply per step.
 // ---------------------------------------------------------------------------
-constexpr int kLazyMaxF = 64;    // longest history (steps): the bits of one 64-bit word
+constexpr int kLazyMaxF = 128;   // longest history (steps): the bits of the two history words
 constexpr int kLazyThreads = 256;
 constexpr int kLazyBatch = 4;    // edges per thread with their loads in flight together
 
@@ -565,7 +564,7 @@ struct LazyRow {
     float Ap, Am;
     int32_t wmax;
     bool arrived;
-    unsigned long long win;   // history bits of steps a..t (bits 0 .. L-1)
+    unsigned long long win_lo, win_hi;  // history bits of steps a..t (bits 0 .. L-1 of the 128)
     const float* yr;          // ring slot of step a (when arrived)
 };
 
@@ -585,7 +584,8 @@ __device__ __forceinline__ LazyRow lazy_row(const Net& n, uint32_t j, uint32_t a
         L = n.F;
     }
     r.L = L;
-    r.win = L >= 64u ? ~0ull : (1ull << L) - 1ull;
+    r.win_lo = L >= 64u ? ~0ull : (1ull << L) - 1ull;
+    r.win_hi = L <= 64u ? 0ull : (L >= 128u ? ~0ull : (1ull << (L - 64u)) - 1ull);
     // the ring slot of step a = t - (L - 1): an arrival implies a >= 1
     r.yr = r.arrived ? n.yring + (size_t)((t - (L - 1u)) % n.F) * n.Np : nullptr;
     return r;
@@ -628,17 +628,19 @@ __device__ __forceinline__ void lazy_apply(const Net& n, const LazyRow& r, const
 {
     int32_t w0[B];
     float yv[B];
-    unsigned long long hm[B];
+    ulonglong2 hm[B];
 #pragma unroll
     for (int u = 0; u < B; ++u) {
         w0[u] = 0;
         yv[u] = 0.0f;
-        hm[u] = 0ull;
+        hm[u] = make_ulonglong2(0ull, 0ull);
         if (ii[u] - r.pbase < r.n_exc) {  // excitatory target: plastic
             const uint64_t e = e0 + (uint64_t)u * stride;
             w0[u] = W16 ? (int32_t)n.w16[e] : __float2int_rz(n.w32[e]);
             if (r.arrived) yv[u] = r.yr[ii[u]];
-            hm[u] = n.hist[ii[u]] & r.win;
+            hm[u] = *reinterpret_cast<const ulonglong2*>(n.hist + 2 * (size_t)ii[u]);
+            hm[u].x &= r.win_lo;
+            hm[u].y &= r.win_hi;
         }
     }
     if (sync) __syncthreads();
@@ -647,9 +649,16 @@ __device__ __forceinline__ void lazy_apply(const Net& n, const LazyRow& r, const
         if (ii[u] - r.pbase >= r.n_exc) continue;
         int32_t w = w0[u];
         if (r.arrived) w = min(max(w + __float2int_rn(__fmul_rn(r.Am, yv[u])), 0), r.wmax);
-        unsigned long long m = hm[u];
+        // the older word first; in each, the earliest remaining step (t - k) first
+        unsigned long long m = hm[u].y;
         while (m) {
-            const int k = 63 - __clzll((long long)m);  // the earliest remaining step, t - k
+            const int k = 63 - __clzll((long long)m);
+            m ^= 1ull << k;
+            w = min(max(w + __float2int_rn(__fmul_rn(r.Ap, xs[r.L - 65u - (uint32_t)k])), 0), r.wmax);
+        }
+        m = hm[u].x;
+        while (m) {
+            const int k = 63 - __clzll((long long)m);
             m ^= 1ull << k;
             w = min(max(w + __float2int_rn(__fmul_rn(r.Ap, xs[r.L - 1u - (uint32_t)k])), 0), r.wmax);
         }

@@ -47,7 +47,7 @@ def test_argument_errors_without_device():
     assert lib.snn_create(ctypes.byref(cfg), ctypes.addressof(p), None, ctypes.byref(ctx)) == -1
     cfg = snn.Config(1, snn.F_LAZY, 1, 1, 1, 0, 0, 0, 0, 0)  # lazy plasticity needs STDP
     assert lib.snn_create(ctypes.byref(cfg), ctypes.addressof(p), None, ctypes.byref(ctx)) == -1
-    for fifo in (1, 65):  # the history is 2..64 steps
+    for fifo in (1, 129):  # the history is 2..128 steps
         cfg = snn.Config(1, snn.F_STDP | snn.F_LAZY, 1, 1, 1, 0, 0, 0, 0, fifo)
         assert lib.snn_create(ctypes.byref(cfg), ctypes.addressof(p), None, ctypes.byref(ctx)) == -1
     cfg = snn.Config(1, 0, 1, 1, 1, 0, 0, 0, 0, 0)

@@ -83,7 +83,7 @@ def _stdp_100k():
 
 @pytest.mark.parametrize("lazy", [False, True])
 def test_brunel_stdp_100k_whole_network(gpu, lazy):
-    """Eager Update Synapses, and the lazy form bench.py times (64-step history)."""
+    """Eager Update Synapses, and the lazy form bench.py times (128-step history)."""
     prob, o = _stdp_100k()
     g = _gpu_run(gpu, prob, 300, lazy=lazy)
     gs, gi = g["steps_ids"]

@@ -53,13 +53,14 @@ def small_stdp(n_steps=3000):
     return si.brunel_stdp_100k(seed=2, n_steps=n_steps, n=4000, k=400)
 
 
-@pytest.mark.parametrize("fifo", [0, 2, 17, 50, 63])
+@pytest.mark.parametrize("fifo", [0, 2, 17, 50, 63, 64, 65, 127])
 @pytest.mark.parametrize("receive", ["global", "tiled"])
 def test_lazy_equals_eager_oracle(gpu, fifo, receive):
     """Brunel+ at 4,000 neurons (in-degree 400), 15-step delay, 3,000 steps:
-    the default history (64 steps, the most the history word holds), the
-    shortest (every row replayed every other step), an odd length, the
-    paper's 50 and one step below the longest."""
+    the default history (128 steps, the most the two history words hold),
+    the shortest (every row replayed every other step), an odd length, the
+    paper's 50, the lengths around the boundary of the two words and one
+    step below the longest."""
     prob = small_stdp()
     o = oracle_run("bstdp4k", prob)
     g = run_lazy(gpu, prob, fifo=fifo, receive=receive)
