@@ -82,7 +82,7 @@ typedef enum {
                           length lazy_fifo; the weights and traces are the eager rule's, bit for
                           bit (snn_read_state / snn_write_state bring every row up to date first).
                           For the pair rule here the eager form, which touches only the rows of the
-                          arriving spikes and the columns of the spiking neurons, measured faster */
+                          arriving spikes and the columns of the spiking neurons, measured as fast */
 
 /* snn_config.receive */
 #define SNN_RECV_AUTO 0u   /* the library picks: tiled when the rows are sorted, the graph has at least

@@ -747,7 +747,7 @@ struct LazyRows {
 // row is replayed once.  The next row's record is loaded while the current
 // one is replayed.
 template <bool W16>
-__global__ void __launch_bounds__(kLazyThreads) k_stdp_lazy(Net n)
+__global__ void __launch_bounds__(kLazyThreads, 4) k_stdp_lazy(Net n)
 {
     __shared__ float xs[kLazyMaxF];
     const unsigned long long t = n.ctl->t + n.k;
