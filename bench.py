@@ -131,8 +131,96 @@ def oracle_sample(prob, max_neurons=170_000, max_inst=12):
     return sub, f"instances 0-{b - 1} of the sweep ({n} neurons, {e1} synapses)"
 
 
-def cpu_baseline(prob, steps: int, target_s: float = 15.0):
+def sweep_size(name: str) -> int:
+    """Networks of a batched-sweep workload (0 for the single networks)."""
+    return int(name.rsplit("_", 1)[1]) if name.startswith("batched_sweep_") else 0
+
+
+def _oracle_process(base_seed, n_nets, b, steps, target_s, barrier, out):
+    """One process of the parallel oracle sample: network b of the sweep,
+    rebuilt alone (same graph and Philox keys as inside the batch) and
+    stepped from step 0.  With target_s, a 200-step calibration run sets
+    the step count to about target_s seconds (at most `steps`)."""
+    try:
+        import oracle
+        inst = si.batched_sweep_params(n_nets, base_seed)[b]
+        p = si.problem(si.BRUNEL, [inst], delay=15, n_steps=min(200, steps), seed=base_seed, threads=1,
+                       inst_index0=b)
+        if target_s:
+            t0 = time.monotonic()
+            oracle.run(p, inst_key0=b)
+            dt = time.monotonic() - t0
+            p.n_steps = int(min(steps, max(200, 200 * target_s / max(dt, 1e-3))))
+        else:
+            p.n_steps = steps
+        barrier.wait(timeout=900)
+        t0 = time.monotonic()  # system-wide clock: comparable between the processes
+        r = oracle.run(p, inst_key0=b)
+        out.put((b, p.n_steps, int(r["events"]), t0, time.monotonic(), p.n_edges))
+    except Exception as e:  # reported to the parent, which falls back to one process
+        barrier.abort()
+        out.put((b, -1, 0, 0.0, 0.0, repr(e)))
+
+
+def oracle_parallel(name: str, rank: int, steps: int, target_s: float | None, timeout_s: float = 1800.0):
+    """The oracle on the first networks of a batched sweep, one process per
+    host core (as many as the free host memory holds, each network's graph
+    in its generator and in the oracle), all started together behind a
+    barrier.  Returns (events/s over the wall time of the slowest, cores,
+    description) or None if a process failed."""
+    import multiprocessing as mp
+    import queue
+    n_nets = sweep_size(name)
+    base = replica_seed(rank)
+    params = si.batched_sweep_params(n_nets, base)
+    cores = len(os.sched_getaffinity(0))
+    free = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    k, need = 0, 0
+    while k < min(cores, n_nets):
+        e = params[k].n * (params[k].k_exc + params[k].k_inh)
+        cost = 32 * e + 512 * params[k].n + (256 << 20)  # graph copies (about 13 B per edge measured), state, interpreter
+        if k > 0 and need + cost > free // 2:
+            break
+        need += cost
+        k += 1
+    ctx = mp.get_context("spawn")  # a fresh interpreter per process: safe beside a CUDA context
+    barrier, out = ctx.Barrier(k), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_process, args=(base, n_nets, b, steps, target_s, barrier, out), daemon=True)
+             for b in range(k)]
+    for pr in procs:
+        pr.start()
+    res, deadline = [], time.monotonic() + timeout_s
+    while len(res) < k and time.monotonic() < deadline:
+        try:
+            res.append(out.get(timeout=5.0))
+        except queue.Empty:  # a process that died without reporting ends the sample
+            if any(pr.exitcode not in (None, 0) for pr in procs):
+                barrier.abort()
+                break
+    for pr in procs:
+        pr.join(timeout=10)
+        if pr.is_alive():
+            pr.kill()
+    if len(res) != k or any(r[1] < 0 for r in res):
+        return None
+    events = sum(r[2] for r in res)
+    wall = max(r[4] for r in res) - min(r[3] for r in res)
+    n_steps = sorted(r[1] for r in res)
+    desc = (f"networks 0-{k - 1} of the sweep, one process each on {k} host cores "
+            f"({sum(p.n for p in params[:k])} neurons, {sum(r[5] for r in res)} synapses), "
+            + (f"{n_steps[0]}-{n_steps[-1]} steps from step 0 (about {target_s:.0f} s per process)" if target_s
+               else f"{n_steps[0]} steps from step 0"))
+    return events / wall, k, desc, wall
+
+
+def cpu_baseline(prob, steps: int, target_s: float = 15.0, name: str = "", rank: int = 0):
     import oracle
+    if sweep_size(name):
+        r = oracle_parallel(name, rank, steps, target_s)
+        if r is not None:
+            value, cores, desc, wall = r
+            return {"value": value, "unit": "synaptic events/s", "cores": cores, "kind": "oracle",
+                    "sample": desc + ", single-threaded C oracle per process", "seconds": round(wall, 3)}
     sub, desc = oracle_sample(prob)
     sub.n_steps = 200
     t0 = time.perf_counter()
@@ -447,7 +535,7 @@ def run_ours(args, rank, world, dist):
         out["graph_construction"] = graph_construction(prob, dev, hbm)
 
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(prob, args.steps)
+        out["cpu_baseline"] = cpu_baseline(prob, args.steps, name=args.workload, rank=rank)
     return out
 
 
@@ -455,22 +543,28 @@ def run_reference(args, rank):
     """The oracle, as it stands, on a bounded sample of the same workload,
     on the host cores."""
     import oracle
-    prob = workload(args.workload, rank)
-    sub, desc = oracle_sample(prob)
     # the run starts at step 0, where the delay FIFO delivers nothing for d
     # steps: at least 100 steps, so that a short run still measures events
-    sub.n_steps = max(args.warmup + args.steps, 100)
-    t0 = time.perf_counter()
-    r = oracle.run(sub)
-    dt = time.perf_counter() - t0
-    value = r["events"] / dt
+    n_steps = max(args.warmup + args.steps, 100)
+    r = oracle_parallel(args.workload, rank, n_steps, None) if sweep_size(args.workload) else None
+    if r is not None:
+        value, cores, desc, dt = r
+    else:
+        prob = workload(args.workload, rank)
+        sub, desc = oracle_sample(prob)
+        sub.n_steps = n_steps
+        t0 = time.perf_counter()
+        res = oracle.run(sub)
+        dt = time.perf_counter() - t0
+        value, cores = res["events"] / dt, 1
+        desc = f"{desc}, {n_steps} steps"
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "synaptic events/s", "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / sub.n_steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / n_steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 state, int32 input",
             "data": "synthetic (seeded graphs, no dataset)",
             "config": {"workload": args.workload, "sample": desc},
-            "cpu_baseline": {"value": value, "unit": "synaptic events/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{desc}, {sub.n_steps} steps"},
+            "cpu_baseline": {"value": value, "unit": "synaptic events/s", "cores": cores, "kind": "oracle",
+                             "sample": desc},
             "e2e": {"value": value, "unit": "synaptic events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -145,8 +145,10 @@ class Problem:
         return out
 
 
-def build_graph(prob: Problem, threads: int | None = None) -> Problem:
-    """Draw the connectivity of every instance and fill weights."""
+def build_graph(prob: Problem, threads: int | None = None, inst_index0: int = 0) -> Problem:
+    """Draw the connectivity of every instance and fill weights.  Instance b
+    is drawn as instance inst_index0 + b of a batch (the index is part of
+    its stream key), so network b of a batch can be rebuilt alone."""
     lib = _load()
     if threads is None:
         threads = max(1, len(os.sched_getaffinity(0)))
@@ -156,7 +158,7 @@ def build_graph(prob: Problem, threads: int | None = None) -> Problem:
     counts = []
     for b, inst in enumerate(prob.instances):
         if inst.p_conn > 0:
-            counts.append(int(lib.gen_bernoulli_count(inst.graph_seed, b, inst.n, inst.p_conn)))
+            counts.append(int(lib.gen_bernoulli_count(inst.graph_seed, inst_index0 + b, inst.n, inst.p_conn)))
         else:
             counts.append(inst.n * (inst.k_exc + inst.k_inh))
     E = int(sum(counts))
@@ -170,9 +172,9 @@ def build_graph(prob: Problem, threads: int | None = None) -> Problem:
         ro_ptr = row_off.ctypes.data + 8 * lo
         tg_ptr = tgt.ctypes.data + 4 * ebase
         if inst.p_conn > 0:
-            lib.gen_bernoulli_fill(inst.graph_seed, b, inst.n, inst.p_conn, lo, ebase, ro_ptr, tg_ptr)
+            lib.gen_bernoulli_fill(inst.graph_seed, inst_index0 + b, inst.n, inst.p_conn, lo, ebase, ro_ptr, tg_ptr)
         else:
-            rc = lib.gen_fixed_indegree(inst.graph_seed, b, inst.n, inst.n_exc, inst.k_exc, inst.k_inh, lo,
+            rc = lib.gen_fixed_indegree(inst.graph_seed, inst_index0 + b, inst.n, inst.n_exc, inst.k_exc, inst.k_inh, lo,
                                         ebase, ro_ptr, tg_ptr, threads)
             if rc != 0:
                 raise ValueError(f"bad fixed in-degree recipe for instance {b}")
@@ -228,9 +230,9 @@ def brunel_instance(n: int = 12500, *, k: int = 1250, g: float = 5.0, nu_ratio: 
 
 
 def problem(model: int, instances: list, *, delay: int, n_steps: int, seed: int = 1, stdp: bool = False,
-            threads: int | None = None) -> Problem:
+            threads: int | None = None, inst_index0: int = 0) -> Problem:
     return build_graph(Problem(model=model, instances=instances, delay=delay, seed=seed, n_steps=n_steps,
-                               stdp=stdp), threads=threads)
+                               stdp=stdp), threads=threads, inst_index0=inst_index0)
 
 
 def vogels_4k(seed: int = 1, n_steps: int = 1000) -> Problem:

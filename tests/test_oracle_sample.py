@@ -1,0 +1,57 @@
+"""The CPU baseline's parallel sample: network b of a batched sweep, rebuilt
+alone, is the same network as inside the batch (graph and Philox keys), so
+the processes of the sample step exactly the sweep's first networks."""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+import snn_inputs as si  # noqa: E402
+
+
+def test_network_rebuilt_alone_equals_its_part_of_the_batch():
+    kw = dict(n_lo=300, n_hi=2000)
+    full = si.batched_sweep(5, base_seed=3, n_steps=0, **kw)
+    params = si.batched_sweep_params(5, 3, **kw)
+    for b in range(5):
+        part = si.sub_problem(full, b)
+        alone = si.problem(si.BRUNEL, [params[b]], delay=15, n_steps=0, seed=3, threads=1, inst_index0=b)
+        assert np.array_equal(part.row_off, alone.row_off)
+        assert np.array_equal(part.tgt, alone.tgt)
+        assert np.array_equal(part.w, alone.w)
+    # and the oracle steps it as it steps that network inside the batch
+    b = 2
+    part = si.sub_problem(full, b, n_steps=150)
+    alone = si.problem(si.BRUNEL, [params[b]], delay=15, n_steps=150, seed=3, threads=1, inst_index0=b)
+    o_part, o_alone = oracle.run(part, inst_key0=b), oracle.run(alone, inst_key0=b)
+    assert o_part["events"] == o_alone["events"] > 0
+    assert np.array_equal(o_part["ids"], o_alone["ids"])
+    whole = oracle.run(si.batched_sweep(5, base_seed=3, n_steps=150, **kw))
+    lo, hi = int(full.inst_off[b]), int(full.inst_off[b + 1])
+    sel = (whole["ids"] >= lo) & (whole["ids"] < hi)
+    assert np.array_equal(whole["ids"][sel] - lo, o_alone["ids"])
+    assert np.array_equal(whole["steps"][sel], o_alone["steps"])
+
+
+def test_parallel_sample_counts_the_serial_events():
+    """oracle_parallel over the first networks of a 3-network sweep (one
+    process each) delivers the events the oracle counts network by network."""
+    import bench
+    steps = 120
+    r = bench.oracle_parallel("batched_sweep_3", 0, steps, None, timeout_s=600)
+    assert r is not None
+    value, cores, desc, wall = r
+    k = min(3, len(os.sched_getaffinity(0)))
+    assert cores == k and wall > 0
+    params = si.batched_sweep_params(3, bench.replica_seed(0))
+    events = 0
+    for b in range(k):
+        p = si.problem(si.BRUNEL, [params[b]], delay=15, n_steps=steps, seed=bench.replica_seed(0), threads=1,
+                       inst_index0=b)
+        events += oracle.run(p, inst_key0=b)["events"]
+    assert abs(value * wall - events) <= 1e-6 * events
+    assert f"networks 0-{k - 1}" in desc and f"{steps} steps" in desc
