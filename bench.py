@@ -208,7 +208,8 @@ def oracle_parallel(name: str, rank: int, steps: int, target_s: float | None, ti
     n_steps = sorted(r[1] for r in res)
     desc = (f"networks 0-{k - 1} of the sweep, one process each on {k} host cores "
             f"({sum(p.n for p in params[:k])} neurons, {sum(r[5] for r in res)} synapses), "
-            + (f"{n_steps[0]}-{n_steps[-1]} steps from step 0 (about {target_s:.0f} s per process)" if target_s
+            + (f"{n_steps[0]}-{n_steps[-1]} steps from step 0 (set for about {target_s:.0f} s per process, "
+               f"at most {steps})" if target_s
                else f"{n_steps[0]} steps from step 0"))
     return events / wall, k, desc, wall
 
