@@ -17,8 +17,8 @@
  *       accumulators of the postsynaptic neurons.
  * It is written as that definition, eagerly, one neuron and one edge at a
  * time, with no blocking, fusion or reordering.  The lazy synapse update of
- * Section III-A-1 reaches the same values ("the amortized number of updates
- * remains identical to the eager version"), so the eager form is the oracle.
+ * Section III-A-1 replays the same per-step updates later, in a batch, so it
+ * reaches the eager values and the eager form is the oracle.
  *
  * Precision.  The neuron update is an IEEE binary32 op sequence, one rounding
  * per written operation (compile with -ffp-contract=off and SSE2 math, no

@@ -1,7 +1,7 @@
 """Lazy Update Synapses (Section III-A-1) against the eager oracle.
 
 The lazy form leaves the plastic synapses of a row stale until the row
-transmits a spike or its history of F steps is about to expire, then
+transmits a spike or its history of F steps would otherwise run out, then
 replays the missed steps in one pass.  The paper states that this reaches
 the eager rule's result; here every weight, trace, spike and pending input
 must equal the oracle's (which applies the rule eagerly, every step) bit for
