@@ -535,7 +535,7 @@ def run_ours(args, rank, world, dist):
     if not args.no_graph:
         out["graph_construction"] = graph_construction(prob, dev, hbm)
 
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:  # the baseline is a one-GPU figure
         out["cpu_baseline"] = cpu_baseline(prob, args.steps, name=args.workload, rank=rank)
     return out
 
