@@ -55,3 +55,28 @@ def test_parallel_sample_counts_the_serial_events():
         events += oracle.run(p, inst_key0=b)["events"]
     assert abs(value * wall - events) <= 1e-6 * events
     assert f"networks 0-{k - 1}" in desc and f"{steps} steps" in desc
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference` prints one JSON line with the reference
+    arm's keys: the oracle's rate on the parallel sample, its cores and
+    sample, and an end-to-end entry that moves no bytes."""
+    import json
+    import subprocess
+    env = dict(os.environ)
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        env.pop(k, None)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "batched_sweep_4", "--steps", "20", "--warmup", "3"], capture_output=True, text=True,
+                       env=env, timeout=600)
+    assert r.returncode == 0, r.stderr
+    lines = [x for x in r.stdout.splitlines() if x.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "synaptic events/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["steps"] == 20 and d["warmup"] == 3
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"]
+    assert cb["cores"] == min(4, len(os.sched_getaffinity(0)))
+    assert "100 steps from step 0" in cb["sample"]  # at least 100 steps: the delay FIFO starts empty
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
