@@ -467,9 +467,14 @@ def run_ours(args, rank, world, dist):
                         "traffic": (traffic_ratio() * recv_bytes if traffic_ratio() and recv_kind == "tiled" else None),
                         "launch_ms": recv_ms,
                         "bytes_per_launch": recv_bytes, "launches": n_prof,
-                        "bytes_each": bytes_each[:16]},
+                        "bytes_each": bytes_each[:16],
+                        # effective bytes per delivered event (edges + per-spike records) and the
+                        # events/s the measured HBM rate allows for the edges alone
+                        "bytes_per_event": recv_bytes * n_prof / max(ev_p, 1),
+                        "edge_only_ceiling_events_per_s": hbm * 1e9 / info["edge_bytes"]},
            "step_roofline": {"bytes_per_step": step_b / args.steps, "frac": step_frac, "peak": hbm,
-                             "unit": "GB/s", "achieved": step_b / t_main / 1e9},
+                             "unit": "GB/s", "achieved": step_b / t_main / 1e9,
+                             "bytes_per_event": step_b / max(ev_main, 1)},
            "phase_ms_per_step": {k: v / n_prof for k, v in phases.items()},
            "gpu_launches": gpu_launches(args.steps, recv_kind, prob.stdp, lazy),
            "clocks": clk}
