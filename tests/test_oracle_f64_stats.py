@@ -2,8 +2,8 @@
 
 Both variants see the same graph and the same Poisson draws; they differ in
 state precision and in weight quantisation.  The runs are chaotic, so their
-rasters part ways; what must agree is the statistics the paper's models are
-judged by (population rate, ISI irregularity): pooled over seeds, the rate
+rasters part ways; what must agree is the statistics that characterise the
+paper's models (population rate, ISI irregularity): pooled over seeds, the rate
 within 2 % and the mean ISI CV within 5 %.
 """
 import numpy as np
