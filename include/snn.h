@@ -293,7 +293,7 @@ snn_status snn_expand_jobs(const snn_job* jobs, uint64_t n_jobs, uint64_t seed, 
 
 /* What the context chose and holds. */
 typedef struct {
-    uint32_t receive;      /* SNN_RECV_GLOBAL or SNN_RECV_TILED (after snn_build_graph) */
+    uint32_t receive;      /* the receive form in use: SNN_RECV_GLOBAL, _TILED or _BULK (after snn_build_graph) */
     uint32_t n_tiles;      /* target tiles of the tiled receive (0: global) */
     uint32_t n_padded;     /* neuron slots on the device (instances padded to 256) */
     uint32_t rows_sorted;  /* 1 if every row's targets ascend */
