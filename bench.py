@@ -202,6 +202,8 @@ def oracle_parallel(name: str, rank: int, steps: int, target_s: float | None, ti
         if pr.is_alive():
             pr.kill()
     if len(res) != k or any(r[1] < 0 for r in res):
+        why = [r[5] for r in res if r[1] < 0] or [f"{k - len(res)} of {k} processes did not report"]
+        print(f"parallel oracle sample failed ({why[0]}); timing one process instead", file=sys.stderr)
         return None
     events = sum(r[2] for r in res)
     wall = max(r[4] for r in res) - min(r[3] for r in res)
