@@ -14,7 +14,10 @@ Parity status of the functions (what pins each one, see tests/test_oracle_*):
   run (f32)   -- LIF closed forms, exact d-step FIFO arrival, the relay
                  (ping-pong) network against breadth-first search, a dense
                  matrix brute force of Receive Spikes, closed-form STDP
-                 weight changes of a single pre/post pair
+                 weight changes of a single pre/post pair, the Init stage's
+                 V0 draw against numpy's Philox words and the uniform law on
+                 [v0_lo, v0_lo + v0_span), the Brunel refractory clamp (period
+                 R + 1 under forced drive; input inside the clamp discarded)
   run_f64     -- agreement with the binary32 run in population rate and
                  ISI CV (statistical; it is a comparison variant)
   relay_raster -- a hand-worked raster of a four-neuron graph, breadth-first

@@ -356,3 +356,103 @@ def test_vogels_run_invariants():
     # delivered events = sum of the out-degrees of the delivered spikes
     deg = np.diff(p.row_off.astype(np.int64))
     assert out["events"] == int(deg[ids].sum())  # d = 1: every spike before the last step is delivered
+
+
+# ---------------------------------------------------------------- Init stage (V0 draw)
+def _numpy_words(seed, inst, local, step, tag):
+    """The 32-bit word of neuron `local` from numpy's own Philox4x64-10: the
+    block at counter (local >> 3, step, tag, 0), key (seed, inst); word
+    local & 7, low half of each 64-bit output first."""
+    # numpy advances its 256-bit counter once before the first block
+    c = ((local >> 3) | step << 64 | tag << 128) - 1
+    c %= 1 << 256
+    g = np.random.Philox(counter=np.array([(c >> (64 * i)) & (2**64 - 1) for i in range(4)], dtype=np.uint64),
+                         key=np.array([seed, inst], dtype=np.uint64))
+    raw = g.random_raw(4)
+    k = local & 7
+    return int(raw[k // 2]) >> (32 * (k % 2)) & 0xffffffff
+
+
+@pytest.mark.parametrize("model", [si.VOGELS, si.BRUNEL])
+def test_initial_potential_draw(model):
+    """The Init stage (Fig. 1: N -> N_0) draws V0 = v0_lo + v0_span u with
+    u = (w >> 8) 2^-24 from the tag-0, step-0 Philox word of each neuron,
+    keyed by (seed, instance).  The words come from numpy's Philox, not the
+    oracle's; the uniform law of V0 over [v0_lo, v0_lo + v0_span) is checked
+    against the configured range (a wrong span, offset, word, step, tag or
+    instance key fails one of the two checks).  Zero steps: N_0 itself."""
+    n = 600
+    if model == si.VOGELS:
+        insts = [si.vogels_instance(n, k=0) for _ in range(3)]
+    else:
+        insts = [si.brunel_instance(n, k=0) for _ in range(3)]
+    seed = 12345
+    lo, span = insts[0].v0_lo, insts[0].v0_span
+    assert (lo, span) == ((-60.0, 10.0) if model == si.VOGELS else (0.0, 20.0))
+    p = si.Problem(model=model, instances=insts, delay=1, seed=seed, n_steps=0, stdp=False,
+                   inst_off=np.arange(4, dtype=np.uint32) * n, row_off=np.zeros(3 * n + 1, np.uint64),
+                   tgt=np.zeros(0, np.uint32), w=np.zeros(0, np.int32))
+    for key0 in (0, 7):  # the instance key may start at another index (one network of a batch re-run alone)
+        out = oracle.run(p, inst_key0=key0)
+        V = out["V"]
+        for b in range(3):
+            for local in list(range(0, 40)) + list(range(n - 24, n)):
+                w = _numpy_words(seed, key0 + b, local, 0, 0)
+                u = np.float32(w >> 8) * np.float32(2.0 ** -24)
+                expect = np.float32(lo) + np.float32(span) * u
+                assert V[b * n + local] == expect, (b, local)
+        assert np.all(V >= lo) and np.all(V < lo + span)
+        # uniform on the range: mean and variance within 5 standard errors
+        x = (V.astype(np.float64) - lo) / span
+        assert abs(x.mean() - 0.5) < 5 * math.sqrt(1 / 12 / V.size)
+        assert abs(x.var() - 1 / 12) < 5 * math.sqrt(1 / 180 / V.size)
+        assert scipy.stats.kstest(x, "uniform").pvalue > 1e-4
+        # instances draw independently: different keys, different potentials
+        assert not np.array_equal(V[:n], V[n:2 * n])
+    assert np.all(out["r"] == 0) and np.all(out["acc0"] == 0) and np.all(out["ge"] == 0)
+
+
+# ---------------------------------------------------------------- Brunel refractory clamp
+def test_brunel_refractory_period_and_discarded_input():
+    """Brunel neuron (Section IV), R = 20 steps: held far above threshold
+    before every update it fires every R + 1 steps -- the clamp covers the R
+    updates after a spike, at which V = V_reset and the input is discarded.
+    A synaptic input delivered inside the clamp is dropped: after the clamp
+    ends the neuron starts again from V_reset and does not fire on it, while
+    the same input arriving after the clamp makes it fire."""
+    inst = si.brunel_instance(3, k=0)
+    inst.lam = 0.0
+    inst.n_exc = 3
+    R = inst.refractory_steps
+    assert R == 20
+    # (a) period under a constant forced supra-threshold drive
+    T = 200
+    p = _problem(si.BRUNEL, inst, n_steps=T, delay=1)
+    out = oracle.run(p, overrides=[(t, 0, 1000.0) for t in range(T)], state=_state(3))
+    got = list(out["steps"][out["ids"] == 0])
+    assert got == list(range(0, T, R + 1))
+    # V at the end of each clamped step is V_reset exactly
+    for Tend in (1, 5, R, R + 1):
+        o = oracle.run(_problem(si.BRUNEL, inst, n_steps=Tend, delay=1), overrides=[(0, 0, 1000.0)],
+                       state=_state(3))
+        assert o["V"][0] == np.float32(inst.v_reset)
+        assert o["r"][0] == (R - (Tend - 1) if Tend <= R + 1 else 0)
+    # (b) input inside the clamp is discarded.  Neuron 1 -> 0 with a weight
+    # that alone crosses threshold from V_reset; neuron 1 is forced to fire
+    # at step s, its spike reaches neuron 0's update at step s + 1 (d = 1).
+    w = quantize = int(round(30.0 * 65536))  # 30 mV: V_reset * Pm + 30 > theta
+    assert quantize == w
+    for s, fires in ((3, False), (R - 1, False), (R, True), (R + 5, True)):
+        p = _problem(si.BRUNEL, inst, n_steps=R + 10, delay=1, edges=[(1, 0)], w=[w])
+        o = oracle.run(p, overrides=[(0, 0, 1000.0), (s, 1, 1000.0)], state=_state(3, w=[w]))
+        s0 = list(o["steps"][o["ids"] == 0])
+        # neuron 0 fires at 0; the arrival at update s + 1 is inside the
+        # clamp (updates 1..R) exactly when s + 1 <= R
+        assert s0 == ([0, s + 1] if fires else [0]), (s, s0)
+        if not fires:
+            # V after the clamp: V_reset decayed by the free updates since
+            Pm = np.float32(math.exp(-inst.dt / inst.tau_m))
+            v = np.float32(inst.v_reset)
+            for _ in range(R + 10 - (R + 1)):
+                v = np.float32(v * Pm) + np.float32(0.0)
+            assert o["V"][0] == v
