@@ -111,6 +111,11 @@ typedef struct {
                               longest a row stays stale (0: 128, the most the two 64-bit
                               history words of a neuron hold; else 2..128.  The paper's queue
                               holds 50 entries) */
+    uint32_t wait_polls;   /* bulk-copy receive: polls of one bounded wait of its producer or a
+                              consumer on an mbarrier before the kernel gives up with
+                              SNN_E_TIMEOUT (0: 2^20).  The wait for the copies still in flight
+                              before a CTA exits keeps its own bound of 2^26 polls */
+    uint32_t reserved;     /* 0 */
 } snn_config;
 
 /* Model constants of one instance.  Times in ms, potentials in mV, integer
@@ -263,8 +268,10 @@ snn_status snn_stats_clear(snn_ctx* ctx);
  * Scratch: a static device array of 8192 * 3 + 3 doubles (192 KB) inside
  * the library, held by every GPU that loads the library until exit, so n is
  * limited to 16,777,216; larger n returns SNN_E_ARG.  The first call on a
- * device looks the array's address up (cudaGetSymbolAddress); make that first
- * call before any stream capture begins.  All calls share the array: calls
+ * device looks the array's address up (cudaGetSymbolAddress) and keeps it for
+ * the device's current CUDA context; the first call after a cudaDeviceReset
+ * looks it up again.  Make the first call on a device before any stream
+ * capture begins.  All calls share the array: calls
  * that overlap on the GPU (other streams, other host threads) race and must
  * be serialised by the caller. */
 snn_status snn_rate_cv_static(const uint32_t* count, const unsigned long long* isi_sum,
@@ -287,7 +294,10 @@ typedef struct {
  * stream (NULL: the legacy default stream).  Waits for the stream.  Errors:
  * SNN_E_ARG for n_jobs >= 2^32 or a job with b < a, n > b - a,
  * b - a - n > 2^24 or o + n > out_len (that job writes nothing; the others
- * are written); SNN_E_CUDA.  Allocates nothing. */
+ * are written); SNN_E_CUDA.  Allocates nothing: the invalid-job flag is one
+ * static device word that every call clears and reads, so calls that
+ * overlap on the GPU (other streams, other host threads) race on it and must
+ * be serialised by the caller. */
 snn_status snn_expand_jobs(const snn_job* jobs, uint64_t n_jobs, uint64_t seed, uint32_t* out, uint64_t out_len,
                            void* stream);
 

@@ -292,7 +292,7 @@ snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr, u
     if (ev) cudaEventRecord(ev[3], s);
     cudaEvent_t mid = ev ? ev[4] : nullptr;  // between the receive and the merge
     if (c->use_tiled && c->use_bulk) {
-        CUDA_TRY(c, enqueue_bulk_receive(c->tiled, n, c->w16, s, mid));
+        CUDA_TRY(c, enqueue_bulk_receive(c->tiled, n, c->w16, s, c->cfg.wait_polls ? c->cfg.wait_polls : kBulkSpin, mid));
     } else if (c->use_tiled) {
         if (fork)
             CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_join, 0));

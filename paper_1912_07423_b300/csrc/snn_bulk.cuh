@@ -40,7 +40,8 @@ __host__ __device__ constexpr uint32_t bulk_slot_bytes(bool w16)
     return kBulkTgtBytes + (kBulkChunk + 16) * (w16 ? 2u : 4u);
 }
 constexpr uint32_t kBulkMark = 0xffffffffu;  // chunk count of an end-of-item marker
-constexpr uint32_t kBulkSpin = 1u << 20;     // bounded waits (polls of try_wait)
+constexpr uint32_t kBulkSpin = 1u << 20;     // default bound of a producer / consumer wait (polls of try_wait)
+constexpr uint32_t kBulkDrainSpin = 1u << 26; // bound of the wait for the copies in flight before exit
 
 struct BulkMeta {
     uint32_t toff, woff, count, info;  // info: shift | channel << 8 (real); chunk total (marker)
@@ -63,11 +64,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// true when the phase of the given parity has completed; false after the bound
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+// true when the phase of the given parity has completed; false after `spin` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t spin)
 {
     const uint32_t a = smem_u32(bar);
-    for (uint32_t i = 0; i < kBulkSpin; ++i) {
+    for (uint32_t i = 0; i < spin; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(kBulkThreads, 1) k_receive_bulk(Net n, const T
                                                                   const uint32_t* __restrict__ items,
                                                                   const uint32_t* __restrict__ split,
                                                                   int32_t* __restrict__ partial, uint32_t n_items,
-                                                                  uint32_t max_len)
+                                                                  uint32_t max_len, uint32_t spin)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     int32_t* acc_s = reinterpret_cast<int32_t*>(smem_raw);
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(kBulkThreads, 1) k_receive_bulk(Net n, const T
                         if (lane == 0) {
                             const uint32_t qn = issued;
                             const uint32_t slot = qn % kBulkSlots, use = qn / kBulkSlots;
-                            if (use > 0 && !mbar_wait(empty + slot, (use - 1) & 1u)) ok = false;
+                            if (use > 0 && !mbar_wait(empty + slot, (use - 1) & 1u, spin)) ok = false;
                             if (ok) {
                                 const uint64_t ta = a & ~3ull, tb = (b + 3) & ~3ull;
                                 const uint64_t wa = W16 ? (a & ~7ull) : ta;
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(kBulkThreads, 1) k_receive_bulk(Net n, const T
                 if (lane == 0) {
                     const uint32_t qn = issued;
                     const uint32_t slot = qn % kBulkSlots, use = qn / kBulkSlots;
-                    if (use > 0 && !mbar_wait(empty + slot, (use - 1) & 1u)) ok = false;
+                    if (use > 0 && !mbar_wait(empty + slot, (use - 1) & 1u, spin)) ok = false;
                     if (ok) {
                         meta[slot] = BulkMeta{0, 0, kBulkMark, K};
                         mbar_arrive(full + slot);
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(kBulkThreads, 1) k_receive_bulk(Net n, const T
             for (;;) {
                 const uint32_t slot = c, use = qn / kBulkSlots;
                 // every lane waits, so every lane acquires the chunk's data
-                bool ok = mbar_wait(full + slot, use & 1u);
+                bool ok = mbar_wait(full + slot, use & 1u, spin);
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) {
                     if (lane == 0) {
@@ -291,10 +292,15 @@ __global__ void __launch_bounds__(kBulkThreads, 1) k_receive_bulk(Net n, const T
         }
         __syncthreads();
     }
-    // leave no copy in flight: wait (bounded) for the last use of every slot
+    // leave no copy in flight: wait for the last use of every slot.  Issued
+    // copies always complete, so this wait ends unless the memory system has
+    // failed; its bound (kBulkDrainSpin, far above any copy's latency) only
+    // keeps the kernel from spinning forever then, and is reported as a timeout
     if (threadIdx.x == 0 && issued > 0) {
         const uint32_t first = issued > kBulkSlots ? issued - kBulkSlots : 0;
-        for (uint32_t qn = first; qn < issued; ++qn) mbar_wait(full + qn % kBulkSlots, (qn / kBulkSlots) & 1u);
+        for (uint32_t qn = first; qn < issued; ++qn)
+            if (!mbar_wait(full + qn % kBulkSlots, (qn / kBulkSlots) & 1u, kBulkDrainSpin))
+                atomicOr(&n.ctl->err, kErrTimeout);
     }
     if (threadIdx.x == 0 && ev) atomicAdd(&n.ctl->events, ev);
     if (bad) atomicOr(&n.ctl->err, kErrBadTarget);
@@ -317,22 +323,22 @@ inline cudaError_t bulk_set_smem(size_t smem)
     return e;
 }
 
-inline cudaError_t enqueue_bulk_receive(const TiledPlan& P, const Net& n, bool w16, cudaStream_t s,
+inline cudaError_t enqueue_bulk_receive(const TiledPlan& P, const Net& n, bool w16, cudaStream_t s, uint32_t spin,
                                         cudaEvent_t mid = nullptr /* recorded between the receive and the merge */)
 {
     const size_t smem = bulk_smem(P.max_len, P.channels, w16);
     if (P.channels == 2) {
         if (w16)
-            k_receive_bulk<true, 2><<<P.grid, kBulkThreads, smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
+            k_receive_bulk<true, 2><<<P.grid, kBulkThreads, smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len, spin);
         else
-            k_receive_bulk<false, 2><<<P.grid, kBulkThreads, smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
+            k_receive_bulk<false, 2><<<P.grid, kBulkThreads, smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len, spin);
         if (mid) cudaEventRecord(mid, s);
         if (P.n_merges) k_merge_parts<2><<<P.n_merges, kMergeChunk / 4, 0, s>>>(n, P.tiles, P.merges, P.partial);
     } else {
         if (w16)
-            k_receive_bulk<true, 1><<<P.grid, kBulkThreads, smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
+            k_receive_bulk<true, 1><<<P.grid, kBulkThreads, smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len, spin);
         else
-            k_receive_bulk<false, 1><<<P.grid, kBulkThreads, smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len);
+            k_receive_bulk<false, 1><<<P.grid, kBulkThreads, smem, s>>>(n, P.tiles, P.items, P.split, P.partial, P.n_items, P.max_len, spin);
         if (mid) cudaEventRecord(mid, s);
         if (P.n_merges) k_merge_parts<1><<<P.n_merges, kMergeChunk / 4, 0, s>>>(n, P.tiles, P.merges, P.partial);
     }

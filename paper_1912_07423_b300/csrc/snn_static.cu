@@ -9,6 +9,7 @@
 // device and stall every other stream.  snn_rate_cv_static serves them: its
 // scratch is the file-scope array below, which every GPU that loads this
 // library holds until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -76,10 +77,43 @@ __global__ void __launch_bounds__(kThreads) k_rate_cv_final(double* scratch, uin
     if (threadIdx.x < 3) scratch[3 * kMaxBlocks + threadIdx.x] = red[threadIdx.x][0];
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up once per device and CUDA
+// context: a cudaDeviceReset destroys the device's primary context and the
+// module with it, so an address cached for the old context would point into
+// freed memory.  The context is told apart by its process-unique id
+// (cuCtxGetId), reached through the runtime's driver entry points so that the
+// library does not link the driver library itself.
 constexpr int kMaxDevices = 64;
+struct ScratchSlot {
+    unsigned long long ctx_id;
+    double* addr;
+};
 std::mutex g_mu;
-double* g_addr[kMaxDevices] = {};
+ScratchSlot g_slot[kMaxDevices] = {};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+cudaError_t current_context_id(unsigned long long* id)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* f0 = nullptr;
+        void* f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0{}, q1{};
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0);
+        if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess) return e;
+        if (q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
+            return cudaErrorNotSupported;
+        get_current = reinterpret_cast<CtxGetCurrentFn>(f0);
+        get_id = reinterpret_cast<CtxGetIdFn>(f1);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
 
 cudaError_t scratch_address(double** out)
 {
@@ -87,14 +121,23 @@ cudaError_t scratch_address(double** out)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    // make the device's primary context current on this thread (the runtime
+    // creates it here if nothing has used the device yet)
+    e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    unsigned long long id = 0;
+    e = current_context_id(&id);
+    if (e != cudaSuccess) return e;
+    ScratchSlot& slot = g_slot[dev];
+    if (!slot.addr || slot.ctx_id != id) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_rate_cv_scratch);
         if (e != cudaSuccess) return e;
-        g_addr[dev] = static_cast<double*>(p);
+        slot.addr = static_cast<double*>(p);
+        slot.ctx_id = id;
     }
-    *out = g_addr[dev];
+    *out = slot.addr;
     return cudaSuccess;
 }
 

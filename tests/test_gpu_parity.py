@@ -391,3 +391,31 @@ def test_automatic_receive_choice(gpu, name, expect):
         assert net.info()["receive"] == expect
     finally:
         net.close()
+
+
+def test_bulk_wait_bound_reports_timeout(gpu):
+    """The bulk receive's producer and consumer waits are bounded: with a
+    bound of one poll a chunk's copy is not yet in shared memory when its
+    consumer first looks, the wait gives up, and the kernel drains the copies
+    it issued (under its own, large bound) before its CTAs exit.  The step
+    reports SNN_E_TIMEOUT through snn_sync, the CUDA context stays usable
+    (reset and stepping again raise no CUDA error), and a context with the
+    default bound on the same device still matches the oracle."""
+    prob = si.batched_sweep(n_nets=3, base_seed=4, n_steps=60, n_lo=2000, n_hi=6000)
+    net = gpu.Network(prob, receive=RECV["bulk"], log_capacity=1 << 20, wait_polls=1)
+    try:
+        net.step(prob.n_steps)
+        with pytest.raises(gpu.SnnError) as e:
+            net.sync()
+        assert e.value.status == -5  # SNN_E_TIMEOUT
+        net.reset()  # clears the error; the device answers
+        net.step(5)
+        with pytest.raises(gpu.SnnError) as e:
+            net.sync()
+        assert e.value.status == -5
+    finally:
+        net.close()
+    ref = oracle.run(prob)
+    out = run_gpu(gpu, prob, receive="bulk")
+    assert np.array_equal(out["steps"], ref["steps"]) and np.array_equal(out["ids"], ref["ids"])
+    assert len(ref["ids"]) > 0
