@@ -136,38 +136,46 @@ def sweep_size(name: str) -> int:
     return int(name.rsplit("_", 1)[1]) if name.startswith("batched_sweep_") else 0
 
 
-def _oracle_process(base_seed, n_nets, b, steps, target_s, barrier, out):
-    """One process of the parallel oracle sample: network b of the sweep,
-    rebuilt alone (same graph and Philox keys as inside the batch) and
-    stepped from step 0.  With target_s, a 200-step calibration run sets
-    the step count to about target_s seconds (at most `steps`)."""
+def _oracle_window_process(base_seed, n_nets, b, t0, k_min, target_s, per_step, barrier, out):
+    """One process of the oracle sample: network b of the sweep, rebuilt alone
+    (same graph and Philox keys as inside the batch), timed on the window of
+    steps [t0, t0 + k) as the difference of two runs from step 0, to t0 + k
+    and to t0 (the oracle always starts at step 0).  With target_s, a
+    200-step calibration run of every process goes to the shared per_step
+    array, and all processes take the same k: the one that gives the slowest
+    network's longer run about target_s seconds (at least k_min)."""
     try:
         import oracle
         inst = si.batched_sweep_params(n_nets, base_seed)[b]
-        p = si.problem(si.BRUNEL, [inst], delay=15, n_steps=min(200, steps), seed=base_seed, threads=1,
-                       inst_index0=b)
+        p = si.problem(si.BRUNEL, [inst], delay=15, n_steps=200, seed=base_seed, threads=1, inst_index0=b)
         if target_s:
-            t0 = time.monotonic()
+            c0 = time.perf_counter()
             oracle.run(p, inst_key0=b)
-            dt = time.monotonic() - t0
-            p.n_steps = int(min(steps, max(200, 200 * target_s / max(dt, 1e-3))))
-        else:
-            p.n_steps = steps
+            per_step[b] = (time.perf_counter() - c0) / 200
         barrier.wait(timeout=900)
-        t0 = time.monotonic()  # system-wide clock: comparable between the processes
-        r = oracle.run(p, inst_key0=b)
-        out.put((b, p.n_steps, int(r["events"]), t0, time.monotonic(), p.n_edges))
+        k = k_min
+        if target_s:
+            k = int(max(k_min, target_s / max(max(per_step[:]), 1e-7) - t0))
+        p.n_steps = t0
+        a0 = time.perf_counter()
+        ra = oracle.run(p, inst_key0=b)
+        a1 = time.perf_counter()
+        p.n_steps = t0 + k
+        rb = oracle.run(p, inst_key0=b)
+        b1 = time.perf_counter()
+        out.put((b, k, int(rb["events"]) - int(ra["events"]), (b1 - a1) - (a1 - a0), p.n_edges, inst.n))
     except Exception as e:  # reported to the parent, which falls back to one process
         barrier.abort()
-        out.put((b, -1, 0, 0.0, 0.0, repr(e)))
+        out.put((b, -1, 0, 0.0, repr(e), 0))
 
 
-def oracle_parallel(name: str, rank: int, steps: int, target_s: float | None, timeout_s: float = 1800.0):
-    """The oracle on the first networks of a batched sweep, one process per
-    host core (as many as the free host memory holds, each network's graph
-    in its generator and in the oracle), all started together behind a
-    barrier.  Returns (events/s over the wall time of the slowest, cores,
-    description) or None if a process failed."""
+def oracle_window(name: str, rank: int, t0: int, k_min: int, target_s: float | None, timeout_s: float = 1800.0):
+    """The oracle on the first networks of a batched sweep, one single-threaded
+    process per host core (as many as the free host memory holds), started
+    together behind a barrier, each timed on steps [t0, t0 + k) of its
+    network.  The value is the sum of the per-process rates (each process has
+    a core of its own).  Returns (events/s, cores, description, seconds, k,
+    per-process (network, k, events, seconds)) or None if a process failed."""
     import multiprocessing as mp
     import queue
     n_nets = sweep_size(name)
@@ -184,8 +192,9 @@ def oracle_parallel(name: str, rank: int, steps: int, target_s: float | None, ti
         need += cost
         k += 1
     ctx = mp.get_context("spawn")  # a fresh interpreter per process: safe beside a CUDA context
-    barrier, out = ctx.Barrier(k), ctx.Queue()
-    procs = [ctx.Process(target=_oracle_process, args=(base, n_nets, b, steps, target_s, barrier, out), daemon=True)
+    barrier, out, per_step = ctx.Barrier(k), ctx.Queue(), ctx.Array("d", k)
+    procs = [ctx.Process(target=_oracle_window_process,
+                         args=(base, n_nets, b, t0, k_min, target_s, per_step, barrier, out), daemon=True)
              for b in range(k)]
     for pr in procs:
         pr.start()
@@ -202,45 +211,69 @@ def oracle_parallel(name: str, rank: int, steps: int, target_s: float | None, ti
         if pr.is_alive():
             pr.kill()
     if len(res) != k or any(r[1] < 0 for r in res):
-        why = [r[5] for r in res if r[1] < 0] or [f"{k - len(res)} of {k} processes did not report"]
+        why = [r[4] for r in res if r[1] < 0] or [f"{k - len(res)} of {k} processes did not report"]
         print(f"parallel oracle sample failed ({why[0]}); timing one process instead", file=sys.stderr)
         return None
-    events = sum(r[2] for r in res)
-    wall = max(r[4] for r in res) - min(r[3] for r in res)
-    n_steps = sorted(r[1] for r in res)
-    desc = (f"networks 0-{k - 1} of the sweep, one process each on {k} host cores "
-            f"({sum(p.n for p in params[:k])} neurons, {sum(r[5] for r in res)} synapses), "
-            + (f"{n_steps[0]}-{n_steps[-1]} steps from step 0 (set for about {target_s:.0f} s per process, "
-               f"at most {steps})" if target_s
-               else f"{n_steps[0]} steps from step 0"))
-    return events / wall, k, desc, wall
+    value = sum(r[2] / r[3] for r in res if r[3] > 0)
+    ks = sorted(r[1] for r in res)
+    secs = max(r[3] for r in res)
+    desc = (f"networks 0-{k - 1} of the sweep, one single-threaded C oracle process each on {k} host cores "
+            f"({sum(r[5] for r in res)} neurons, {sum(r[4] for r in res)} synapses), steps [{t0}, {t0 + ks[0]}) "
+            f"(at least {k_min} steps), each process timed as the difference of two runs from step 0; "
+            f"value = sum of the per-process rates")
+    return value, k, desc, secs, ks[0], sorted((r[0], r[1], r[2], r[3]) for r in res)
 
 
-def cpu_baseline(prob, steps: int, target_s: float = 15.0, name: str = "", rank: int = 0):
+def oracle_window_single(prob, t0: int, k_min: int, target_s: float | None):
+    """The oracle, single-threaded, on a sample of a non-sweep workload
+    (oracle_sample), timed on steps [t0, t0 + k) as the difference of two runs
+    from step 0."""
     import oracle
-    if sweep_size(name):
-        r = oracle_parallel(name, rank, steps, target_s)
-        if r is not None:
-            value, cores, desc, wall = r
-            return {"value": value, "unit": "synaptic events/s", "cores": cores, "kind": "oracle",
-                    "sample": desc + ", single-threaded C oracle per process", "seconds": round(wall, 3)}
     sub, desc = oracle_sample(prob)
-    sub.n_steps = 200
-    t0 = time.perf_counter()
-    r = oracle.run(sub)
-    dt = time.perf_counter() - t0
-    if dt < target_s / 4:
-        sub.n_steps = int(min(steps, 200 * target_s / max(dt, 1e-3)))
-        t0 = time.perf_counter()
-        r = oracle.run(sub)
-        dt = time.perf_counter() - t0
-    return {"value": r["events"] / dt, "unit": "synaptic events/s", "cores": 1, "kind": "oracle",
-            "sample": f"{desc}, {sub.n_steps} steps from step 0, single-threaded C oracle",
-            "seconds": round(dt, 3), "realtime_factor": sub.n_steps * DT_MS * 1e-3 / dt}
+    k = k_min
+    if target_s:
+        sub.n_steps = 200
+        c0 = time.perf_counter()
+        oracle.run(sub)
+        per_step = (time.perf_counter() - c0) / 200
+        k = int(max(k_min, target_s / max(per_step, 1e-7) - t0))
+    sub.n_steps = t0
+    a0 = time.perf_counter()
+    ra = oracle.run(sub)
+    a1 = time.perf_counter()
+    sub.n_steps = t0 + k
+    rb = oracle.run(sub)
+    b1 = time.perf_counter()
+    dt = (b1 - a1) - (a1 - a0)
+    ev = int(rb["events"]) - int(ra["events"])
+    return (ev / dt, 1, f"{desc}, steps [{t0}, {t0 + k}) timed as the difference of two runs from step 0, "
+            "single-threaded C oracle", dt, k, [(0, k, ev, dt)])
+
+
+def cpu_window(name: str, prob, rank: int, t0: int, k_min: int, target_s: float | None):
+    """The oracle timed on the GPU's window: the parallel sweep sample, or one
+    process (also the fallback when the parallel sample fails)."""
+    r = oracle_window(name, rank, t0, k_min, target_s) if sweep_size(name) else None
+    if r is None:
+        if prob is None:
+            prob = workload(name, rank)
+        r = oracle_window_single(prob, t0, k_min, target_s)
+    return r
+
+
+def cpu_baseline(prob, t0: int, steps: int, target_s: float = 15.0, name: str = "", rank: int = 0):
+    """The CPU oracle on the host cores, on the same window of steps as the
+    GPU's timed region (at least 100 steps of it), sized to about target_s
+    seconds per process."""
+    value, cores, desc, secs, k, _ = cpu_window(name, prob, rank, t0, max(steps, 100), target_s)
+    return {"value": value, "unit": "synaptic events/s", "cores": cores, "kind": "oracle", "sample": desc,
+            "seconds": round(secs, 3), "window": [t0, t0 + k]}
 
 
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples of the SM clock and throttle reasons every 50 ms,
+    summarised over a span of host time (the device work of the run)."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -261,33 +294,49 @@ class ClockSampler:
         except Exception:
             self.proc = None
 
-    def stop(self):
+    @staticmethod
+    def _when(stamp: str):
+        import datetime
+        try:
+            return datetime.datetime.strptime(stamp.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def stop(self, t_from: float | None = None, t_to: float | None = None):
+        """Stop sampling; summarise the samples taken between host times
+        t_from and t_to (time.time(); all samples if not given)."""
         if not self.proc:
             return None
+        time.sleep(0.1)  # the sample in flight
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], [], set()
+        sm, mx, reasons, n_all = [], [], set(), 0
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
+                continue
+            n_all += 1
+            w = self._when(parts[0])
+            if t_from is not None and w is not None and not (t_from - 0.05 <= w <= t_to + 0.05):
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                sm.append(float(parts[2]))
+                mx.append(float(parts[3]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
+            for nm, v in zip(names, parts[6:10]):
                 if v.lower() == "active":
                     reasons.add(nm)
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "span_s": None if t_from is None else round(t_to - t_from, 3),
+                "span": "from the network's creation to the end of the profiled steps"}
 
 
 def delivered_spikes(net, prob, t0: int, t1: int) -> int:
@@ -374,17 +423,101 @@ def replica_value(events: float, seconds: float, dist, device) -> float:
     return reduce_over_ranks(events, "sum", dist, device) / reduce_over_ranks(seconds, "max", dist, device)
 
 
+def isi_stats(steps, ids, n: int, t0: int, t1: int, dt_ms: float):
+    """Population rate (Hz) and mean ISI CV of a raster over steps [t0, t1),
+    with the definitions of snn_stats: rate = spikes / n / window; CV per
+    neuron with at least 3 spikes in the window (ISIs between its consecutive
+    spikes there), averaged over those neurons."""
+    m = (steps >= t0) & (steps < t1)
+    st, i = steps[m].astype(np.int64), ids[m].astype(np.int64)
+    rate = len(st) / n / ((t1 - t0) * dt_ms * 1e-3)
+    order = np.lexsort((st, i))
+    st, i = st[order], i[order]
+    cnt = np.bincount(i, minlength=n)
+    same = i[1:] == i[:-1]
+    isi = (st[1:] - st[:-1])[same].astype(np.float64)
+    who = i[1:][same]
+    s1 = np.bincount(who, weights=isi, minlength=n)
+    s2 = np.bincount(who, weights=isi * isi, minlength=n)
+    ok = cnt >= 3
+    if not ok.any():
+        return rate, 0.0
+    mean = s1[ok] / (cnt[ok] - 1)
+    var = s2[ok] / (cnt[ok] - 1) - mean * mean
+    return rate, float((np.sqrt(np.maximum(var, 0.0)) / mean).mean())
+
+
+def _f64_stats(sub, key0: int, t0: int, t1: int, dt_ms: float):
+    import oracle
+    sub.n_steps = t1
+    r = oracle.run_f64(sub, inst_key0=key0)
+    return isi_stats(r["steps"], r["ids"], sub.n, t0, t1, dt_ms)
+
+
+def drift_networks(prob) -> list:
+    """Networks of the workload whose rate and ISI CV are compared with the
+    binary64 oracle: for a batch the ones at the 25/50/75 % size quantiles and
+    the largest; a single network whole if the oracle holds it (<= 200k neurons)."""
+    B = len(prob.instances)
+    if B == 1:
+        return [0] if prob.n <= 200_000 and not prob.stdp else []
+    order = sorted(range(B), key=lambda b: prob.instances[b].n)
+    return sorted({order[int(q * (B - 1))] for q in (0.25, 0.5, 0.75, 1.0)})
+
+
+def rate_cv_drift(prob, t0: int, k: int, device) -> dict | None:
+    """Rate and ISI CV of the binary32 lattice run on the GPU (snn_stats over
+    steps [t0, t0 + k), each sampled network re-run alone in its own context
+    with its batch key, hence bit-identical to its part of the batch) against
+    the binary64, unquantised-weight oracle of the same networks and window
+    (run in host processes while the GPU runs).  Bounds: rate within 2 %,
+    ISI CV within 5 %, of the pooled values."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import paper_1912_07423_b300 as snn
+    nets = drift_networks(prob)
+    if not nets:
+        return None
+    dt_ms = prob.instances[0].dt
+    subs = [si.sub_problem(prob, b, n_steps=0) if len(prob.instances) > 1 else prob for b in nets]
+    keys = nets if len(prob.instances) > 1 else [0]
+    with cf.ProcessPoolExecutor(max_workers=min(len(nets), max(1, len(os.sched_getaffinity(0)))),
+                                mp_context=mp.get_context("spawn")) as ex:
+        futs = [ex.submit(_f64_stats, dataclasses.replace(sub), key, t0, t0 + k, dt_ms) for sub, key in zip(subs, keys)]
+        gpu = []
+        for sub, key in zip(subs, keys):
+            with snn.Network(sub, w16=True, stats=True, inst_key0=key, log_capacity=0) as net:
+                net.step(t0)
+                net.stats_clear()
+                net.step(k)
+                gpu.append(net.stats(0))
+        f64 = [f.result() for f in futs]
+    n = [sub.n for sub in subs]
+    pool = lambda xs: sum(x * w for x, w in zip(xs, n)) / sum(n)  # neuron-weighted
+    r32, r64 = pool([g[0] for g in gpu]), pool([f[0] for f in f64])
+    c32, c64 = sum(g[1] for g in gpu) / len(gpu), sum(f[1] for f in f64) / len(f64)
+    dr, dc = abs(r32 - r64) / r64 if r64 else 0.0, abs(c32 - c64) / c64 if c64 else 0.0
+    return {"networks": nets, "window": [t0, t0 + k],
+            "gpu_rate_hz": r32, "f64_rate_hz": r64, "rate_rel_diff": dr,
+            "gpu_isi_cv": c32, "f64_isi_cv": c64, "isi_cv_rel_diff": dc,
+            "within_bounds": bool(dr <= 0.02 and dc <= 0.05), "bounds": {"rate": 0.02, "isi_cv": 0.05},
+            "per_network": [{"net": b, "gpu": list(g), "f64": list(f)} for b, g, f in zip(nets, gpu, f64)]}
+
+
 def run_ours(args, rank, world, dist):
     import torch
     import paper_1912_07423_b300 as snn
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
+    clocks = ClockSampler(dev.index)
+    clocks.start()  # running before the device work starts: it spans settle, warm-up, timed and profiled steps
     t_gen = time.perf_counter()
     prob = workload(args.workload, rank)
     t_gen = time.perf_counter() - t_gen
     hbm, peak_kind = peaks()
-    cap = int(prob.n * (args.warmup + args.steps + args.profile_steps) * 0.05) + (1 << 20)
+    t0 = args.settle + args.warmup  # first timed step
+    cap = int(prob.n * (t0 + args.steps) * 0.05) + (1 << 20)
 
     def barrier():
         if dist is not None:
@@ -411,30 +544,32 @@ def run_ours(args, rank, world, dist):
         c1 = net.counters()
         return e0.elapsed_time(e1) / 1e3, c1["events"] - c0["events"], c1["spikes"] - c0["spikes"]
 
-    # ---- headline: batched + int16, timed on the device
+    # ---- headline: batched + int16, timed on the device over steps [t0, t0 + K)
     recv_mode = {"auto": snn.RECV_AUTO, "global": snn.RECV_GLOBAL, "tiled": snn.RECV_TILED,
                  "bulk": snn.RECV_BULK}[args.receive]
     lazy = prob.stdp and args.plasticity == "lazy"
+    t_clk0 = time.time()
     net = snn.Network(prob, w16=True, receive=recv_mode, log_capacity=cap, lazy=lazy, lazy_fifo=args.lazy_fifo)
     info = net.info()
     recv_kind = info["receive"]
+    net.step(args.settle)  # the initial transient passes and the delay FIFO fills
     net.step(args.warmup)
     net.sync()
-    clocks = ClockSampler(dev.index)
-    clocks.start()
     t_main, ev_main, sp_main = timed(net, args.steps)
-    clk = clocks.stop()
-    t_a = args.warmup
-    deliv_main = delivered_spikes(net, prob, t_a, t_a + args.steps)
-    # ---- per-kernel times (CUDA events around every kernel, same stream)
+    deliv_main = delivered_spikes(net, prob, t0, t0 + args.steps)
+    # ---- the same window again from a reset, with CUDA events around every
+    # kernel (deterministic: the same spikes and events as the timed steps)
     n_prof = min(args.steps, args.profile_steps)
-    t_p0 = t_a + args.steps
+    net.reset()
+    net.step(t0)
+    net.sync()
     c0 = net.counters()
     phases = net.step_profiled(n_prof)
     c1 = net.counters()
-    bytes_each = launch_bytes(net, prob, t_p0, min(n_prof, 16), info["edge_bytes"])
+    clk = clocks.stop(t_clk0, time.time())
+    bytes_each = launch_bytes(net, prob, t0, min(n_prof, 16), info["edge_bytes"])
     ev_p, sp_p = c1["events"] - c0["events"], c1["spikes"] - c0["spikes"]
-    deliv_p = delivered_spikes(net, prob, t_p0, t_p0 + n_prof)
+    deliv_p = delivered_spikes(net, prob, t0, t0 + n_prof)
     mem = info["device_bytes"]
     net.close()
     del net
@@ -445,6 +580,7 @@ def run_ours(args, rank, world, dist):
     value = ev_total / t_max
     recv_ms = phases["receive"] / n_prof
     recv_bytes = (ev_p * info["edge_bytes"] + deliv_p * B_SPIKE_DELIVERED) / n_prof
+    recv_bytes_6 = (ev_p * 6 + deliv_p * B_SPIKE_DELIVERED) / n_prof  # int16 code + u32 target per event
     achieved = recv_bytes / (recv_ms * 1e-3) / 1e9
     step_b = step_bytes(prob, info["edge_bytes"], ev_main, deliv_main, sp_main, args.steps)
     step_frac = (step_b / (hbm * 1e9)) / t_main
@@ -455,6 +591,7 @@ def run_ours(args, rank, world, dist):
            "data": "synthetic (seeded graphs, no dataset)",
            "config": {"workload": args.workload, "networks": len(prob.instances), "neurons": prob.n,
                       "synapses": prob.n_edges, "delay_steps": prob.delay, "dt_ms": DT_MS,
+                      "window": [t0, t0 + args.steps], "settle_steps": args.settle,
                       "receive": recv_kind, "tiles": info["n_tiles"], "weights": "int16 x 2^shift(row)",
                       "edge_bytes": info["edge_bytes"],
                       "l2": "inputs larger than L2 (edge arrays %.1f GB >> 126 MB)" % (prob.n_edges * 6 / 1e9),
@@ -469,7 +606,11 @@ def run_ours(args, rank, world, dist):
                         "traffic": (traffic_ratio() * recv_bytes if traffic_ratio() and recv_kind == "tiled" else None),
                         "launch_ms": recv_ms,
                         "bytes_per_launch": recv_bytes, "launches": n_prof,
+                        "window": [t0, t0 + n_prof],
+                        "same_events_as_timed": bool(n_prof == args.steps and ev_p == ev_main),
                         "bytes_each": bytes_each[:16],
+                        # the survey's 6 bytes per event (u32 target + int16 code) beside the bytes read
+                        "frac_at_6_bytes_per_event": recv_bytes_6 / (recv_ms * 1e-3) / 1e9 / hbm,
                         # effective bytes per delivered event (edges + per-spike records) and the
                         # events/s the measured HBM rate allows for the edges alone
                         "bytes_per_event": recv_bytes * n_prof / max(ev_p, 1),
@@ -481,18 +622,27 @@ def run_ours(args, rank, world, dist):
            "gpu_launches": gpu_launches(args.steps, recv_kind, prob.stdp, lazy),
            "clocks": clk}
 
-    # ---- plain single-precision weights + global-atomic receive, same networks
+    # ---- plain path: binary32 weights, global-atomic receive, each network in
+    # its own context one after the other (its batch key: the same spikes)
     if not args.no_plain:
-        net = snn.Network(prob, w16=False, receive=snn.RECV_GLOBAL, log_capacity=cap, lazy=lazy,
-                          lazy_fifo=args.lazy_fifo)
-        net.step(args.warmup)
-        net.sync()
-        t_pl, ev_pl, sp_pl = timed(net, args.steps)
-        net.close()
-        del net
+        t_pl, ev_pl, n_ctx = 0.0, 0, 0
+        B = len(prob.instances)
+        for b in range(B):
+            sub = si.sub_problem(prob, b, n_steps=0) if B > 1 else prob
+            with snn.Network(sub, w16=False, receive=snn.RECV_GLOBAL, log_capacity=0, lazy=lazy,
+                             lazy_fifo=args.lazy_fifo, inst_key0=b if B > 1 else 0) as pnet:
+                pnet.step(t0)
+                pnet.sync()
+                t_b, ev_b, _ = timed(pnet, args.steps)
+            t_pl += t_b
+            ev_pl += ev_b
+            n_ctx += 1
         torch.cuda.empty_cache()
         out["plain_fp32"] = {"value": sum_over_ranks(ev_pl) / max_over_ranks(t_pl), "unit": "synaptic events/s",
                              "receive": "global", "weights": "binary32",
+                             "contexts": n_ctx, "how": "each network alone in its own context, one after another; "
+                                                        "time = sum of the per-network CUDA-event times",
+                             "same_events": bool(ev_pl == ev_main),
                              "ms_per_step": t_pl * 1e3 / args.steps,
                              "realtime_factor": args.steps * DT_MS * 1e-3 / t_pl}
         out["speedup_vs_plain_fp32"] = out["value"] / out["plain_fp32"]["value"]
@@ -502,7 +652,7 @@ def run_ours(args, rank, world, dist):
     if not args.no_generic and prob.model == si.BRUNEL and not prob.stdp:
         gprob = dataclasses.replace(prob, model=snn.MODEL_BRUNEL_LIF)
         net = snn.Network(gprob, w16=True, receive=recv_mode, log_capacity=cap)
-        net.step(args.warmup)
+        net.step(t0)
         net.sync()
         t_g, ev_g, sp_g = timed(net, args.steps)
         net.close()
@@ -513,64 +663,60 @@ def run_ours(args, rank, world, dist):
                                  "model": "Brunel from the LIF building block (SNN_MODEL_BRUNEL_LIF)",
                                  "same_events_and_spikes": bool(ev_g == ev_main and sp_g == sp_main)}
 
-    # ---- end to end through the C ABI from host buffers
+    # ---- end to end through the C ABI from host buffers: create + graph
+    # upload, the steps up to the end of the window, raster readout
     if not args.no_e2e:
         barrier()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        t_s = time.perf_counter()
         net = snn.Network(prob, w16=True, receive=recv_mode, log_capacity=cap, lazy=lazy,
                           lazy_fifo=args.lazy_fifo)  # h2d of the graph
         t1 = time.perf_counter()
-        net.step(args.steps)
+        net.step(t0 + args.steps)
         net.sync()
         t2 = time.perf_counter()
         steps_h, ids_h = net.spikes()  # d2h of the raster
-        t_e2e = time.perf_counter() - t0
-        parts = {"create_and_build_s": t1 - t0, "steps_s": t2 - t1, "raster_readout_s": t0 + t_e2e - t2}
+        t_e2e = time.perf_counter() - t_s
+        parts = {"create_and_build_s": t1 - t_s, "steps_s": t2 - t1, "raster_readout_s": t_s + t_e2e - t2}
         c = net.counters()
         net.close()
         del net
         torch.cuda.empty_cache()
+        n_all = t0 + args.steps
         h2d = prob.row_off.nbytes + prob.tgt.nbytes + prob.w.nbytes
         d2h = 8 * int(c["spikes"])
         out["e2e"] = {"value": sum_over_ranks(c["events"]) / max_over_ranks(t_e2e), "unit": "synaptic events/s",
-                      "seconds": t_e2e, "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-                      "includes": "snn_create + snn_build_graph from host arrays + snn_step(K) + snn_read_spikes",
+                      "seconds": t_e2e, "steps": n_all, "h2d_bytes_per_step": h2d / n_all,
+                      "d2h_bytes_per_step": d2h / n_all,
+                      "includes": "snn_create + snn_build_graph from host arrays + snn_step(settle + warm-up + K) "
+                                  "+ snn_read_spikes",
                       "parts": parts}
+
+    # ---- binary32 lattice run against the binary64 float-weight oracle
+    if not args.no_drift and rank == 0:
+        out["rate_cv_drift"] = rate_cv_drift(prob, t0, max(args.steps, args.drift_steps), dev)
 
     # ---- adjacency construction on the GPU (Fig. 2) for the same networks
     if not args.no_graph:
         out["graph_construction"] = graph_construction(prob, dev, hbm)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:  # the baseline is a one-GPU figure
-        out["cpu_baseline"] = cpu_baseline(prob, args.steps, name=args.workload, rank=rank)
+        out["cpu_baseline"] = cpu_baseline(prob, t0, args.steps, name=args.workload, rank=rank)
     return out
 
 
 def run_reference(args, rank):
-    """The oracle, as it stands, on a bounded sample of the same workload,
-    on the host cores."""
-    import oracle
-    # the run starts at step 0, where the delay FIFO delivers nothing for d
-    # steps: at least 100 steps, so that a short run still measures events
-    n_steps = max(args.warmup + args.steps, 100)
-    r = oracle_parallel(args.workload, rank, n_steps, None) if sweep_size(args.workload) else None
-    if r is not None:
-        value, cores, desc, dt = r
-    else:
-        prob = workload(args.workload, rank)
-        sub, desc = oracle_sample(prob)
-        sub.n_steps = n_steps
-        t0 = time.perf_counter()
-        res = oracle.run(sub)
-        dt = time.perf_counter() - t0
-        value, cores = res["events"] / dt, 1
-        desc = f"{desc}, {n_steps} steps"
+    """The oracle, as it stands, on a bounded sample of the same workload, on
+    the host cores, timed on the same window of steps as our arm (at least 100
+    steps of it, from t0 = settle + warm-up)."""
+    t0 = args.settle + args.warmup
+    value, cores, desc, dt, k, _ = cpu_window(args.workload, None, rank, t0, max(args.steps, 100), args.ref_seconds)
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "synaptic events/s", "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / n_steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / k,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 state, int32 input",
             "data": "synthetic (seeded graphs, no dataset)",
-            "config": {"workload": args.workload, "sample": desc},
+            "config": {"workload": args.workload, "window": [t0, t0 + k], "settle_steps": args.settle,
+                       "sample": desc},
             "cpu_baseline": {"value": value, "unit": "synaptic events/s", "cores": cores, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": "synaptic events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -583,7 +729,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="batched_sweep_256")
-    ap.add_argument("--profile-steps", type=int, default=500)
+    ap.add_argument("--profile-steps", type=int, default=2000,
+                    help="steps of the timed window profiled again from a reset (at most --steps)")
+    ap.add_argument("--settle", type=int, default=200,
+                    help="untimed steps before the warm-up: the initial transient passes and the delay FIFO fills")
+    ap.add_argument("--drift-steps", type=int, default=2000, help="window of the rate / ISI CV drift comparison")
+    ap.add_argument("--ref-seconds", type=float, default=15.0,
+                    help="reference arm: about this long per process on the host cores")
     ap.add_argument("--receive", choices=["auto", "global", "tiled", "bulk"], default="auto")
     ap.add_argument("--plasticity", choices=["eager", "lazy"], default="eager",
                     help="Update Synapses form for plastic workloads (brunel_stdp_100k; eager measured faster)")
@@ -593,9 +745,12 @@ def main():
     ap.add_argument("--no-generic", action="store_true", help="skip timing the generic-update model")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="skip timing the GPU adjacency construction")
+    ap.add_argument("--no-drift", action="store_true", help="skip the binary64 rate / ISI CV comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.settle < 0:
+        raise SystemExit("--settle must be >= 0")
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
 

@@ -98,7 +98,7 @@ typedef struct {
     uint32_t flags;        /* SNN_F_* */
     uint32_t delay;        /* d >= 1 steps; a spike of step t reaches the update of step t+d */
     uint32_t n_inst;       /* number of network instances, >= 1 */
-    uint64_t seed;         /* Philox key word 0 (word 1 is the instance index) */
+    uint64_t seed;         /* Philox key word 0 (word 1 is inst_key0 + the instance index) */
     uint64_t log_capacity; /* spikes the raster log keeps (0: no log) */
     uint32_t receive;      /* SNN_RECV_* */
     uint32_t steps_per_graph; /* steps captured per CUDA graph (0: library default) */
@@ -115,7 +115,9 @@ typedef struct {
                               consumer on an mbarrier before the kernel gives up with
                               SNN_E_TIMEOUT (0: 2^20).  The wait for the copies still in flight
                               before a CTA exits keeps its own bound of 2^26 polls */
-    uint32_t reserved;     /* 0 */
+    uint32_t inst_key0;    /* Philox key word 1 of instance 0: instance b draws with key (seed,
+                              inst_key0 + b), so that one network of a batch re-run alone in its
+                              own context gets the same random numbers (0 for a batch) */
 } snn_config;
 
 /* Model constants of one instance.  Times in ms, potentials in mV, integer

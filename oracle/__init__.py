@@ -276,10 +276,11 @@ def run(prob, overrides=None, state=None, inst_key0: int = 0) -> dict:
     return out
 
 
-def run_f64(prob, w_mV: np.ndarray | None = None) -> dict:
-    """The binary64, unquantised-weight comparison variant (no STDP)."""
+def run_f64(prob, w_mV: np.ndarray | None = None, inst_key0: int = 0) -> dict:
+    """The binary64, unquantised-weight comparison variant (no STDP).
+    inst_key0 as for run()."""
     lib = _load()
-    m = _Marshalled(prob)
+    m = _Marshalled(prob, inst_key0=inst_key0)
     wd = np.ascontiguousarray(prob.w_mV() if w_mV is None else w_mV, dtype=np.float64)
     V = np.zeros(prob.n, np.float64)
     R = _Raster()

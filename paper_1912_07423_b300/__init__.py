@@ -48,7 +48,7 @@ class Config(ctypes.Structure):
     _fields_ = [("model", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("delay", ctypes.c_uint32),
                 ("n_inst", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("log_capacity", ctypes.c_uint64),
                 ("receive", ctypes.c_uint32), ("steps_per_graph", ctypes.c_uint32), ("tune_steps", ctypes.c_uint32),
-                ("lazy_fifo", ctypes.c_uint32), ("wait_polls", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("lazy_fifo", ctypes.c_uint32), ("wait_polls", ctypes.c_uint32), ("inst_key0", ctypes.c_uint32)]
 
 
 class Params(ctypes.Structure):
@@ -203,6 +203,8 @@ class Network:
     lazy, lazy_fifo: with STDP, the lazy Update Synapses and its history
     length in steps (0: 128).  stats: keep spike counts and ISI moments.
     wait_polls: bound of the bulk receive's mbarrier waits (0: the default).
+    inst_key0: Philox instance key of the first instance (to re-run network b
+    of a batch alone with its own random numbers, pass b).
     steps_per_graph, tune_steps: CUDA-graph length and bulk re-plan step.
     build_graph: upload problem's graph now (else call build_graph).
     Every call goes through the C ABI; there is no CPU path.
@@ -211,7 +213,7 @@ class Network:
     def __init__(self, problem, *, w16: bool = True, receive: int = RECV_AUTO, log_capacity: int | None = None,
                  stats: bool = False, steps_per_graph: int = 0, tune_steps: int = 0, device: str = "cuda:0",
                  stream=None, build_graph: bool = True, packed: bool = True, lazy: bool = False,
-                 lazy_fifo: int = 0, wait_polls: int = 0):
+                 lazy_fifo: int = 0, wait_polls: int = 0, inst_key0: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise SnnError(-3, "no CUDA device: libsnn has no CPU fallback")
@@ -227,7 +229,7 @@ class Network:
         if log_capacity is None:
             log_capacity = max(1 << 16, int(problem.n) * 64)
         self.cfg = Config(problem.model, flags, problem.delay, len(problem.instances), problem.seed, log_capacity,
-                          receive, steps_per_graph, tune_steps, lazy_fifo, wait_polls, 0)
+                          receive, steps_per_graph, tune_steps, lazy_fifo, wait_polls, inst_key0)
         self.params = _params_array(problem.instances)
         ctx = _vp()
         st = self.lib.snn_create(ctypes.byref(self.cfg), ctypes.addressof(self.params), ctypes.byref(self.dev),

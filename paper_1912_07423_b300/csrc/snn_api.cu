@@ -748,6 +748,7 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     n.Np = c->Np;
     n.D = c->D;
     n.d = cfg->delay;
+    n.key0 = cfg->inst_key0;
     n.n_inst = cfg->n_inst;
     n.seed = cfg->seed;
     c->cr = 4;

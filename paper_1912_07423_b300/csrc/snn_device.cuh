@@ -72,6 +72,8 @@ struct Net {
     uint32_t cr;               // count-ring length, a power of two >= D + 2
     uint32_t k;                // this launch's step offset: step = ctl->t + k
     uint32_t F;                // lazy plasticity: history length in steps (2..128)
+    uint32_t key0;             // Philox key word 1 of instance 0 (instance b uses key0 + b)
+    uint32_t pad0;
     uint64_t seed;
     unsigned int* count;       // |S_t| over all instances at [t % cr]
     unsigned int* icount;      // |S_t| of instance b at [(t % cr) * n_inst + b]

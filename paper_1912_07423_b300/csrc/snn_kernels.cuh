@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256) k_update(Net n)
                 const uint32_t nT = __ldg(&I->pois_n);
                 const uint8_t* S = n.pois_start + (size_t)b * kPoissonBuckets;
                 uint32_t words[8];
-                philox_words8(n.seed, b, local0 >> 3, t, 1, words);
+                philox_words8(n.seed, n.key0 + b, local0 >> 3, t, 1, words);
                 const uint32_t wofs = local0 & 7u & ~(uint32_t)(NPT - 1);  // 0 for 8 per thread
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
@@ -813,7 +813,7 @@ __global__ void k_init_state(Net n, int vogels, int stdp, int lazy)
     const InstDev* I = n.inst + b;
     const uint32_t local0 = id0 - I->pbase;
     uint32_t words[8];
-    philox_words8(n.seed, b, local0 >> 3, 0, 0, words);
+    philox_words8(n.seed, n.key0 + b, local0 >> 3, 0, 0, words);
     for (int k = 0; k < 8; ++k) {
         const uint32_t id = id0 + k;
         float v = 0.0f;

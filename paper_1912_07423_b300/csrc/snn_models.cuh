@@ -142,7 +142,7 @@ __global__ void k_init_model(Net n, typename M::neuron* __restrict__ ms)
     const ModelView mv = model_view(n, b);
     const uint32_t local0 = id0 - mv.I->pbase;
     uint32_t words[8];
-    philox_words8(n.seed, b, local0 >> 3, 0, 0, words);
+    philox_words8(n.seed, n.key0 + b, local0 >> 3, 0, 0, words);
     alignas(16) typename M::neuron st[K];
     for (int k = 0; k < K; ++k) {
         st[k] = typename M::neuron{};
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(256) k_update_model(Net n, typename M::neuron*
         const uint32_t local0 = id0 - pbase;
         if (local0 < nloc) {
             uint32_t words[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            if (M::kRandom) philox_words8(n.seed, b, local0 >> 3, t, 1, words);
+            if (M::kRandom) philox_words8(n.seed, n.key0 + b, local0 >> 3, t, 1, words);
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
                 if (local0 + k >= nloc) continue;

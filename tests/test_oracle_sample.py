@@ -37,24 +37,29 @@ def test_network_rebuilt_alone_equals_its_part_of_the_batch():
     assert np.array_equal(whole["steps"][sel], o_alone["steps"])
 
 
-def test_parallel_sample_counts_the_serial_events():
-    """oracle_parallel over the first networks of a 3-network sweep (one
-    process each) delivers the events the oracle counts network by network."""
+def test_window_sample_counts_the_serial_events():
+    """oracle_window over the first networks of a 3-network sweep (one
+    process each) times steps [t0, t0 + k) of each network as the difference
+    of two runs from step 0: its events per process are the serial oracle's
+    events of that window, and its value the sum of the per-process rates."""
     import bench
-    steps = 120
-    r = bench.oracle_parallel("batched_sweep_3", 0, steps, None, timeout_s=600)
+    t0, k_min = 40, 80
+    r = bench.oracle_window("batched_sweep_3", 0, t0, k_min, None, timeout_s=600)
     assert r is not None
-    value, cores, desc, wall = r
-    k = min(3, len(os.sched_getaffinity(0)))
-    assert cores == k and wall > 0
+    value, cores, desc, secs, k, per = r
+    n = min(3, len(os.sched_getaffinity(0)))
+    assert cores == n and secs > 0 and k == k_min and len(per) == n
     params = si.batched_sweep_params(3, bench.replica_seed(0))
-    events = 0
-    for b in range(k):
-        p = si.problem(si.BRUNEL, [params[b]], delay=15, n_steps=steps, seed=bench.replica_seed(0), threads=1,
+    for b, kb, ev, dt in per:
+        assert kb == k_min and dt > 0
+        p = si.problem(si.BRUNEL, [params[b]], delay=15, n_steps=t0, seed=bench.replica_seed(0), threads=1,
                        inst_index0=b)
-        events += oracle.run(p, inst_key0=b)["events"]
-    assert abs(value * wall - events) <= 1e-6 * events
-    assert f"networks 0-{k - 1}" in desc and f"{steps} steps" in desc
+        e_a = oracle.run(p, inst_key0=b)["events"]
+        p.n_steps = t0 + k_min
+        e_b = oracle.run(p, inst_key0=b)["events"]
+        assert ev == e_b - e_a > 0
+    assert abs(value - sum(ev / dt for _, _, ev, dt in per)) <= 1e-9 * value
+    assert f"networks 0-{n - 1}" in desc and f"steps [{t0}, {t0 + k_min})" in desc
 
 
 def test_reference_arm_line():
@@ -67,7 +72,8 @@ def test_reference_arm_line():
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
         env.pop(k, None)
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
-                        "batched_sweep_4", "--steps", "20", "--warmup", "3"], capture_output=True, text=True,
+                        "batched_sweep_4", "--steps", "20", "--warmup", "3", "--ref-seconds", "2"],
+                       capture_output=True, text=True,
                        env=env, timeout=600)
     assert r.returncode == 0, r.stderr
     lines = [x for x in r.stdout.splitlines() if x.strip()]
@@ -78,5 +84,7 @@ def test_reference_arm_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"]
     assert cb["cores"] == min(4, len(os.sched_getaffinity(0)))
-    assert "100 steps from step 0" in cb["sample"]  # at least 100 steps: the delay FIFO starts empty
+    # the window starts after the settle and warm-up steps and lasts at least 100 steps
+    assert d["config"]["window"][0] == 200 + 3 and d["config"]["window"][1] - d["config"]["window"][0] >= 100
+    assert "timed as the difference of two runs from step 0" in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
