@@ -409,7 +409,7 @@ def test_bulk_wait_bound_reports_timeout(gpu):
             net.sync()
         assert e.value.status == -5  # SNN_E_TIMEOUT
         net.reset()  # clears the error; the device answers
-        net.step(5)
+        net.step(prob.delay + 10)  # past the delay: spikes are delivered again
         with pytest.raises(gpu.SnnError) as e:
             net.sync()
         assert e.value.status == -5
