@@ -45,37 +45,49 @@ B_NEURON = {si.BRUNEL: 18, si.VOGELS: 44}
 B_NEURON_STDP = 16
 
 
-def gpu_launches(steps: int, recv_kind: str, stdp: bool, lazy: bool = False, per_graph: int = 16) -> int:
+def gpu_launches(steps: int, recv_kind: str, stdp: bool, lazy: bool = False, per_graph: int = 16,
+                 fused: bool = False) -> int:
     """Kernels of this library launched by `steps` steps of snn_step: the
     update, the STDP passes (eager: depression and potentiation; lazy: one
     replay pass), the receive (tiled: per-step plan and receive; bulk:
-    receive, merge; global: receive), and one step-counter advance per
-    captured graph (per_graph steps, the rest one by one)."""
-    per_step = 1 + ((1 if lazy else 2) if stdp else 0) + {"tiled": 2, "bulk": 2, "global": 1}[recv_kind]
+    receive, merge; global: receive) -- or the one fused step kernel -- and
+    one step-counter advance per captured graph (per_graph steps, the rest one
+    by one)."""
+    if fused:
+        per_step = 1
+    else:
+        per_step = 1 + ((1 if lazy else 2) if stdp else 0) + {"tiled": 2, "bulk": 2, "global": 1}[recv_kind]
     return steps * per_step + steps // per_graph + steps % per_graph
 
-def kernel_source_hash() -> str:
-    """Hash of the sources of the tiled receive (its ncu traffic figure is
-    only reported while these are unchanged)."""
+
+# the sources each ncu traffic summary depends on (profiles/<file>)
+TRAFFIC_FILES = {"k_receive_tiled": ("receive_traffic.txt", ("snn_tiled.cuh", "snn_device.cuh")),
+                 "k_step_fused": ("fused_step_traffic.txt",
+                                  ("snn_fused.cuh", "snn_tiled.cuh", "snn_kernels.cuh", "snn_device.cuh"))}
+
+
+def kernel_source_hash(kernel: str = "k_receive_tiled") -> str:
+    """Hash of the sources of a kernel (its ncu traffic figure is only
+    reported while these are unchanged)."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("snn_tiled.cuh", "snn_device.cuh"):
+    for f in TRAFFIC_FILES[kernel][1]:
         with open(os.path.join(ROOT, "paper_1912_07423_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def traffic_ratio():
-    """DRAM bytes per algorithmic byte of k_receive_tiled from the committed
-    ncu summary (profiles/receive_traffic.txt), if it matches the sources."""
+def traffic_ratio(kernel: str = "k_receive_tiled"):
+    """DRAM bytes per algorithmic byte of a kernel from its committed ncu
+    summary under profiles/, if that summary matches the sources."""
     try:
         kv = {}
-        with open(os.path.join(ROOT, "profiles", "receive_traffic.txt")) as f:
+        with open(os.path.join(ROOT, "profiles", TRAFFIC_FILES[kernel][0])) as f:
             for line in f:
                 if ":" in line:
                     k, v = line.split(":", 1)
                     kv[k.strip()] = v.strip()
-        if kv.get("source_hash") != kernel_source_hash():
+        if kv.get("source_hash") != kernel_source_hash(kernel):
             return None
         return float(kv["dram_bytes_per_algorithmic_byte"])
     except Exception:
@@ -549,7 +561,8 @@ def run_ours(args, rank, world, dist):
                  "bulk": snn.RECV_BULK}[args.receive]
     lazy = prob.stdp and args.plasticity == "lazy"
     t_clk0 = time.time()
-    net = snn.Network(prob, w16=True, receive=recv_mode, log_capacity=cap, lazy=lazy, lazy_fifo=args.lazy_fifo)
+    net = snn.Network(prob, w16=True, receive=recv_mode, log_capacity=cap, lazy=lazy, lazy_fifo=args.lazy_fifo,
+                      serial=args.serial)
     info = net.info()
     recv_kind = info["receive"]
     net.step(args.settle)  # the initial transient passes and the delay FIFO fills
@@ -578,9 +591,15 @@ def run_ours(args, rank, world, dist):
     t_max = max_over_ranks(t_main)
     ev_total = sum_over_ranks(ev_main)
     value = ev_total / t_max
+    fused = bool(info.get("fused"))
+    # the dominant kernel: the receive, or the fused step kernel, which also
+    # runs the update (its bytes: the receive's plus the update's per-neuron
+    # state and per-emitted-spike queue and log writes)
+    kernel = "k_step_fused" if fused else f"k_receive_{recv_kind}"
     recv_ms = phases["receive"] / n_prof
-    recv_bytes = (ev_p * info["edge_bytes"] + deliv_p * B_SPIKE_DELIVERED) / n_prof
-    recv_bytes_6 = (ev_p * 6 + deliv_p * B_SPIKE_DELIVERED) / n_prof  # int16 code + u32 target per event
+    upd_bytes = (B_NEURON[prob.model] * prob.n * n_prof + B_SPIKE_EMITTED * sp_p) / n_prof if fused else 0.0
+    recv_bytes = (ev_p * info["edge_bytes"] + deliv_p * B_SPIKE_DELIVERED) / n_prof + upd_bytes
+    recv_bytes_6 = (ev_p * 6 + deliv_p * B_SPIKE_DELIVERED) / n_prof + upd_bytes  # int16 code + u32 target per event
     achieved = recv_bytes / (recv_ms * 1e-3) / 1e9
     step_b = step_bytes(prob, info["edge_bytes"], ev_main, deliv_main, sp_main, args.steps)
     step_frac = (step_b / (hbm * 1e9)) / t_main
@@ -593,6 +612,9 @@ def run_ours(args, rank, world, dist):
                       "synapses": prob.n_edges, "delay_steps": prob.delay, "dt_ms": DT_MS,
                       "window": [t0, t0 + args.steps], "settle_steps": args.settle,
                       "receive": recv_kind, "tiles": info["n_tiles"], "weights": "int16 x 2^shift(row)",
+                      "step_kernels": "fused (update + receive in one kernel)" if fused else "separate",
+                      **({"tuned_ms_per_step": {k: v for k, v in info["tune_ms"].items() if v > 0}}
+                         if info.get("tuned") else {}),
                       "edge_bytes": info["edge_bytes"],
                       "l2": "inputs larger than L2 (edge arrays %.1f GB >> 126 MB)" % (prob.n_edges * 6 / 1e9),
                       "parallelism": f"replicas x{world} (independent networks, no collective)",
@@ -601,9 +623,11 @@ def run_ours(args, rank, world, dist):
                          if prob.stdp else {})},
            "realtime_factor": args.steps * DT_MS * 1e-3 / t_max,
            "spikes": int(sp_main), "events": int(ev_main),
-           "roofline": {"kernel": f"k_receive_{recv_kind}", "bound": "hbm", "achieved": achieved, "peak": hbm,
+           "roofline": {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": hbm,
                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
-                        "traffic": (traffic_ratio() * recv_bytes if traffic_ratio() and recv_kind == "tiled" else None),
+                        "traffic": (traffic_ratio(kernel) * recv_bytes
+                                    if kernel in TRAFFIC_FILES and traffic_ratio(kernel) else None),
+                        "update_bytes_per_launch": upd_bytes,
                         "launch_ms": recv_ms,
                         "bytes_per_launch": recv_bytes, "launches": n_prof,
                         "window": [t0, t0 + n_prof],
@@ -619,8 +643,21 @@ def run_ours(args, rank, world, dist):
                              "unit": "GB/s", "achieved": step_b / t_main / 1e9,
                              "bytes_per_event": step_b / max(ev_main, 1)},
            "phase_ms_per_step": {k: v / n_prof for k, v in phases.items()},
-           "gpu_launches": gpu_launches(args.steps, recv_kind, prob.stdp, lazy),
+           "gpu_launches": gpu_launches(args.steps, recv_kind, prob.stdp, lazy, fused=fused),
            "clocks": clk}
+
+    # ---- the same path with Update Neurons and Receive Spikes as separate
+    # kernels (SNN_F_SERIAL), same window: what running them in one kernel gains
+    if fused and not args.no_serial_compare:
+        with snn.Network(prob, w16=True, receive=recv_mode, log_capacity=cap, serial=True) as snet:
+            snet.step(t0)
+            snet.sync()
+            t_s, ev_s, sp_s = timed(snet, args.steps)
+        torch.cuda.empty_cache()
+        out["separate_kernels"] = {"value": sum_over_ranks(ev_s) / max_over_ranks(t_s), "unit": "synaptic events/s",
+                                   "ms_per_step": t_s * 1e3 / args.steps,
+                                   "same_events_and_spikes": bool(ev_s == ev_main and sp_s == sp_main)}
+        out["speedup_fused_vs_separate"] = out["value"] / out["separate_kernels"]["value"]
 
     # ---- plain path: binary32 weights, global-atomic receive, each network in
     # its own context one after the other (its batch key: the same spikes)
@@ -746,6 +783,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="skip timing the GPU adjacency construction")
     ap.add_argument("--no-drift", action="store_true", help="skip the binary64 rate / ISI CV comparison")
+    ap.add_argument("--no-serial-compare", action="store_true",
+                    help="skip timing the separate update and receive kernels beside the fused step")
+    ap.add_argument("--serial", action="store_true",
+                    help="headline with Update Neurons and Receive Spikes as separate kernels (SNN_F_SERIAL)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

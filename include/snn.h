@@ -73,9 +73,13 @@ typedef enum {
 #define SNN_F_STDP 1u  /* pair STDP on exc -> exc synapses (Brunel only; "Brunel+") */
 #define SNN_F_W16 2u   /* weights stored as int16 codes x 2^shift(row); else binary32 */
 #define SNN_F_STATS 4u /* keep per-neuron spike counts and ISI moments for snn_stats */
-#define SNN_F_UNPACKED 8u /* tiled receive: read the u32 target and int16 code arrays even where the
-                             packed layout applies (SNN_F_W16, no STDP, every instance of at most
-                             65,536 neurons: one u32 per edge, target offset << 16 | code) */
+#define SNN_F_UNPACKED 8u /* read the u32 target and int16 code arrays even where a compressed layout
+                             applies.  The compressed layouts (SNN_F_W16, no STDP): the tiled receive's
+                             packed edges where every instance has at most 65,536 neurons (one u32 per
+                             edge, target offset << 16 | code), and the global receive's row weights
+                             where every row carries one weight -- the source population's, as in the
+                             paper's models (Section III-A-2, Table 2) -- so that it reads the 4-byte
+                             targets alone */
 #define SNN_F_LAZY 16u /* with SNN_F_STDP: lazy Update Synapses (Section III-A-1).  The plastic
                           synapses of a row are left stale and brought up to date in one pass
                           when the row transmits a spike or when its age reaches the history
@@ -83,11 +87,20 @@ typedef enum {
                           bit (snn_read_state / snn_write_state bring every row up to date first).
                           For the pair rule here the eager form, which touches only the rows of the
                           arriving spikes and the columns of the spiking neurons, measured as fast */
+#define SNN_F_SERIAL 32u /* run Update Neurons and Receive Spikes as separate kernels, one after the
+                            other.  Without it the library runs both stages of a step in one kernel
+                            where that applies (the Brunel model without plasticity, 16-bit weights,
+                            the tiled receive, delay >= 3): the update of step t and the receive of
+                            step t, which delivers S_{t-d+1}, touch disjoint data once the input is
+                            held in two buffers, one per step parity.  Results are the same */
 
 /* snn_config.receive */
-#define SNN_RECV_AUTO 0u   /* the library picks: tiled when the rows are sorted, the graph has at least
-                              200M synapses and a row reaches each target tile with 400 or more edges
-                              on average; else global */
+#define SNN_RECV_AUTO 0u   /* the library measures: snn_build_graph runs every form that applies to the
+                              graph (global; with sorted rows tiled, and tiled fused with the update --
+                              SNN_F_SERIAL leaves that one out) from the initial state over the same
+                              delay + 150 steps (at most 1,100) and times the last 48 with CUDA events;
+                              the fastest is kept (snn_info.tune_ms) and the state returns to N_0.
+                              Results do not depend on the form.  The bulk form is not a candidate */
 #define SNN_RECV_GLOBAL 1u /* a warp per row piece (rows cut into up to 16 pieces when a step has few
                               spikes), red.global.add into L2-resident accumulators */
 #define SNN_RECV_TILED 2u  /* target-tiled, accumulators in shared memory; needs sorted rows */
@@ -195,7 +208,8 @@ snn_status snn_step(snn_ctx* ctx, uint32_t n_steps);
  * [1] Update Neurons, [2] Update Synapses (potentiation), [3] Receive
  * Spikes (the receive kernel; with the tiled receive also any wait for its
  * per-step plan, which runs beside [0]-[2] when the delay is 2 or more and
- * before [3] otherwise), [4] the merge of the receive's partial
+ * before [3] otherwise; with the fused step the one kernel that runs Update
+ * Neurons and Receive Spikes together, [1] then 0), [4] the merge of the receive's partial
  * accumulators, [5] end-of-step bookkeeping.  Used to measure one kernel's
  * share of the step; the simulation advances exactly as with snn_step. */
 snn_status snn_step_profiled(snn_ctx* ctx, uint32_t n_steps, double* phase_ms);
@@ -311,8 +325,14 @@ typedef struct {
     uint32_t rows_sorted;  /* 1 if every row's targets ascend */
     uint64_t edges;        /* synapses loaded */
     uint64_t device_bytes; /* device memory held */
-    uint32_t edge_bytes;   /* bytes the receive reads per delivered edge: 4 (packed), 6 (int16 codes), 8 */
+    uint32_t edge_bytes;   /* bytes the receive reads per delivered edge: 4 (packed edges, or targets alone
+                              with row weights), 6 (u32 targets + int16 codes), 8 (+ binary32 weights) */
     uint32_t model_state_bytes; /* generic models: bytes of one neuron's state record (else 0) */
+    uint32_t fused;        /* 1: update and receive of a step run in one kernel (see SNN_F_SERIAL) */
+    uint32_t tuned;        /* 1: the receive form was chosen by SNN_RECV_AUTO's timing run */
+    float tune_ms[4];      /* SNN_RECV_AUTO: ms per step each form took in that run, in the order global,
+                              tiled (separate kernels), tiled fused with the update, bulk; 0: not a
+                              candidate for this graph */
 } snn_info;
 snn_status snn_get_info(snn_ctx* ctx, snn_info* info);
 

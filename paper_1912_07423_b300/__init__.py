@@ -18,7 +18,7 @@ from .build import LIB, build as _build
 
 __all__ = ["Network", "SnnError", "load", "VOGELS", "BRUNEL", "MODEL_RELAY", "MODEL_BRUNEL_LIF", "MODEL_STATE_DTYPE",
            "RECV_AUTO", "RECV_GLOBAL", "RECV_TILED", "RECV_BULK", "F_STDP", "F_W16", "F_STATS", "F_UNPACKED", "F_LAZY",
-           "FIELDS"]
+           "F_SERIAL", "FIELDS"]
 
 VOGELS, BRUNEL = 0, 1
 # models of the generic update (snn_models.cuh) and their per-neuron state records
@@ -27,7 +27,7 @@ MODEL_STATE_DTYPE = {
     MODEL_RELAY: np.dtype([("flag", "u1")]),
     MODEL_BRUNEL_LIF: np.dtype({"names": ["V", "r"], "formats": ["<f4", "u1"], "offsets": [0, 4], "itemsize": 8}),
 }
-F_STDP, F_W16, F_STATS, F_UNPACKED, F_LAZY = 1, 2, 4, 8, 16
+F_STDP, F_W16, F_STATS, F_UNPACKED, F_LAZY, F_SERIAL = 1, 2, 4, 8, 16, 32
 RECV_AUTO, RECV_GLOBAL, RECV_TILED, RECV_BULK = 0, 1, 2, 3
 FIELDS = {"V": 0, "ge": 1, "gi": 2, "r": 3, "x": 4, "y": 5, "acc0": 6, "acc1": 7, "w": 8, "model": 9}
 _FIELD_DTYPE = {"V": np.float32, "ge": np.float32, "gi": np.float32, "r": np.int32, "x": np.float32,
@@ -64,7 +64,8 @@ class Params(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("receive", ctypes.c_uint32), ("n_tiles", ctypes.c_uint32), ("n_padded", ctypes.c_uint32),
                 ("rows_sorted", ctypes.c_uint32), ("edges", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
-                ("edge_bytes", ctypes.c_uint32), ("model_state_bytes", ctypes.c_uint32)]
+                ("edge_bytes", ctypes.c_uint32), ("model_state_bytes", ctypes.c_uint32), ("fused", ctypes.c_uint32),
+                ("tuned", ctypes.c_uint32), ("tune_ms", ctypes.c_float * 4)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(_vp, ctypes.c_size_t, _vp, _vp)
@@ -205,6 +206,8 @@ class Network:
     wait_polls: bound of the bulk receive's mbarrier waits (0: the default).
     inst_key0: Philox instance key of the first instance (to re-run network b
     of a batch alone with its own random numbers, pass b).
+    serial: run Update Neurons and Receive Spikes as separate kernels even
+    where the fused step applies.
     steps_per_graph, tune_steps: CUDA-graph length and bulk re-plan step.
     build_graph: upload problem's graph now (else call build_graph).
     Every call goes through the C ABI; there is no CPU path.
@@ -213,7 +216,7 @@ class Network:
     def __init__(self, problem, *, w16: bool = True, receive: int = RECV_AUTO, log_capacity: int | None = None,
                  stats: bool = False, steps_per_graph: int = 0, tune_steps: int = 0, device: str = "cuda:0",
                  stream=None, build_graph: bool = True, packed: bool = True, lazy: bool = False,
-                 lazy_fifo: int = 0, wait_polls: int = 0, inst_key0: int = 0):
+                 lazy_fifo: int = 0, wait_polls: int = 0, inst_key0: int = 0, serial: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise SnnError(-3, "no CUDA device: libsnn has no CPU fallback")
@@ -225,7 +228,7 @@ class Network:
         self.mem = _TorchMemory(self.device)
         self.dev = Device(self.mem.alloc_cb, self.mem.free_cb, None, self.stream.cuda_stream)
         flags = (F_STDP if problem.stdp else 0) | (F_W16 if w16 else 0) | (F_STATS if stats else 0) | \
-            (0 if packed else F_UNPACKED) | (F_LAZY if lazy else 0)
+            (0 if packed else F_UNPACKED) | (F_LAZY if lazy else 0) | (F_SERIAL if serial else 0)
         if log_capacity is None:
             log_capacity = max(1 << 16, int(problem.n) * 64)
         self.cfg = Config(problem.model, flags, problem.delay, len(problem.instances), problem.seed, log_capacity,
@@ -342,4 +345,6 @@ class Network:
         self._check(self.lib.snn_get_info(self.ctx, ctypes.byref(i)), "snn_get_info")
         return {"receive": {RECV_GLOBAL: "global", RECV_TILED: "tiled", RECV_BULK: "bulk"}.get(i.receive, "?"), "n_tiles": i.n_tiles,
                 "n_padded": i.n_padded, "rows_sorted": bool(i.rows_sorted), "edges": i.edges,
-                "device_bytes": i.device_bytes, "edge_bytes": i.edge_bytes, "model_state_bytes": i.model_state_bytes}
+                "device_bytes": i.device_bytes, "edge_bytes": i.edge_bytes, "model_state_bytes": i.model_state_bytes,
+                "fused": bool(i.fused), "tuned": bool(i.tuned),
+                "tune_ms": dict(zip(["global", "tiled", "fused", "bulk"], [float(x) for x in i.tune_ms]))}

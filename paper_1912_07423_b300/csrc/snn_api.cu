@@ -22,6 +22,7 @@
 #include "snn_tiled.cuh"
 #include "snn_bulk.cuh"
 #include "snn_models.cuh"
+#include "snn_fused.cuh"
 
 #include <cub/device/device_radix_sort.cuh>
 
@@ -86,6 +87,19 @@ struct snn_ctx {
     std::vector<unsigned long long> spk_seen;  // instance spike counts at the last re-plan
     std::vector<uint64_t> inst_edges;  // synapses of each instance
     uint4* rinfo = nullptr;            // row records (start, length, meta)
+    int32_t* roww = nullptr;           // row weights (16-bit codes, one per row); net.roww points here when used
+    // receive form in use (RecvForm) and, with SNN_RECV_AUTO, the ms per step
+    // each form took in the tuning run (0: not a candidate)
+    int form = 0;
+    bool tiled_fits = false;           // within the flat stream's 32-bit vector index and 24-bit length
+    float tune_ms[4] = {0.f, 0.f, 0.f, 0.f};
+    bool tuned = false;
+    // fused step (snn_fused.cuh): update and receive of a step in one kernel
+    bool fused = false;
+    StepPlan plan2{};                  // the second per-step plan (odd steps)
+    uint32_t fused_grid = 0;           // CTAs of the fused kernel (all resident)
+    uint32_t fused_lead = 0;           // receive items before update chunks alternate with them
+    size_t fused_smem = 0;
 
     // pinned staging ring of the large host copies (snn_build_graph's upload,
     // snn_read_spikes' readout), allocated at the first one and kept
@@ -239,10 +253,61 @@ void launch_update(const Net& n, bool stats, int npt, uint32_t Np, cudaStream_t 
 // holds kPhases + 1 events recorded between the phases.
 constexpr int kPhases = 6;
 
+FusedDev fused_args(const snn_ctx* c)
+{
+    FusedDev F{};
+    F.tiles = c->tiled.tiles;
+    F.split = c->tiled.split;
+    F.plan[0] = c->tiled.step;
+    F.plan[1] = c->plan2;
+    F.n_tiles = c->tiled.n_tiles;
+    F.max_len = c->tiled.max_len;
+    F.n_ctas = c->fused_grid;
+    F.cap = std::min<uint32_t>(kMaxParts, c->fused_grid);
+    F.items_cap = c->tiled.items_cap;
+    F.n_chunks = (c->Np + kFusedChunk - 1) / kFusedChunk;
+    F.lead = c->fused_lead;
+    uint32_t n_pad = 1;
+    while (n_pad < c->tiled.n_tiles) n_pad <<= 1;
+    F.plan_bytes = (uint32_t)plan_smem(n_pad);
+    return F;
+}
+
+cudaError_t launch_fused(const snn_ctx* c, const Net& n, cudaStream_t s)
+{
+    const FusedDev F = fused_args(c);
+    const dim3 grid(c->fused_grid), block(kTiledThreads);
+    if (c->packed) {
+        if (c->stats)
+            k_step_fused<kWPacked, true><<<grid, block, c->fused_smem, s>>>(n, F);
+        else
+            k_step_fused<kWPacked, false><<<grid, block, c->fused_smem, s>>>(n, F);
+    } else {
+        if (c->stats)
+            k_step_fused<kW16, true><<<grid, block, c->fused_smem, s>>>(n, F);
+        else
+            k_step_fused<kW16, false><<<grid, block, c->fused_smem, s>>>(n, F);
+    }
+    return cudaGetLastError();
+}
+
 snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr, uint32_t k = 0)
 {
     Net n = c->net;
     n.k = k;  // step = ctl->t + k
+    if (c->fused) {  // update and receive of the step in one kernel (phase [3])
+        if (ev)
+            for (int i = 0; i <= 3; ++i) cudaEventRecord(ev[i], s);
+        CUDA_TRY(c, launch_fused(c, n, s));
+        if (ev) {
+            cudaEventRecord(ev[4], s);
+            cudaEventRecord(ev[5], s);
+            k_advance<<<1, 1, 0, s>>>(c->ctl, 1);
+            cudaEventRecord(ev[6], s);
+        }
+        CUDA_TRY(c, cudaGetLastError());
+        return SNN_OK;
+    }
     if (ev) cudaEventRecord(ev[0], s);
     const uint32_t ublocks = grid_for(c->Np / kUpdateNeurons, 256);
     const uint32_t wblocks = (uint32_t)sm_count() * 8;
@@ -304,10 +369,12 @@ snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr, u
                                           fork && !c->stdp && !ev));
         if (mid) cudaEventRecord(mid, s);  // no merge: the parts add into the accumulators
     } else {
-        if (c->w16)
-            k_receive_global<true><<<wblocks, 256, 0, s>>>(n);
+        if (c->w16 && c->net.roww)
+            k_receive_global<true, true><<<wblocks, 256, 0, s>>>(n);
+        else if (c->w16)
+            k_receive_global<true, false><<<wblocks, 256, 0, s>>>(n);
         else
-            k_receive_global<false><<<wblocks, 256, 0, s>>>(n);
+            k_receive_global<false, false><<<wblocks, 256, 0, s>>>(n);
         if (mid) cudaEventRecord(mid, s);
     }
     if (ev) cudaEventRecord(ev[5], s);
@@ -410,6 +477,11 @@ snn_status init_state(snn_ctx* c)
     CUDA_TRY(c, cudaMemsetAsync(c->net.lbase, 0, (size_t)c->cr * 8, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->net.inst_spikes, 0, (size_t)c->cfg.n_inst * 8, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->net.tile_ctr, 0, 2 * sizeof(unsigned int), c->stream));
+    if (c->fused) {  // the input of step 1 and the plans of steps 0 and 1
+        CUDA_TRY(c, cudaMemsetAsync(c->net.accx, 0, (size_t)c->Np * 4, c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(c->tiled.step.hdr, 0, 4 * sizeof(uint32_t), c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(c->plan2.hdr, 0, 4 * sizeof(uint32_t), c->stream));
+    }
     c->host_steps = 0;
     return SNN_OK;
 }
@@ -425,6 +497,40 @@ bool packable(const snn_ctx* c)
 }
 
 // (Re)build the packed edges from the target and code arrays.
+// Row weights for the global receive: with 16-bit codes and no plasticity
+// (and no SNN_F_UNPACKED), a graph whose every row carries one weight -- the
+// source population's, as in the paper's models -- keeps it per row and the
+// receive reads 4 bytes per event.  Recomputed after snn_write_state(W); the
+// CUDA graphs are re-captured when the layout changes.
+snn_status refresh_row_weights(snn_ctx* c, bool* changed)
+{
+    *changed = false;
+    const int32_t* before = c->net.roww;
+    c->net.roww = nullptr;
+    if (c->w16 && !c->stdp && !(c->cfg.flags & SNN_F_UNPACKED)) {
+        if (!c->roww) c->roww = alloc_n<int32_t>(c, c->Np);
+        unsigned int* dmixed = alloc_n<unsigned int>(c, 1);
+        if (!c->roww || !dmixed) {
+            dev_free(c, dmixed);
+            return fail(c, SNN_E_NOMEM, "row weights");
+        }
+        unsigned int mixed = 0;
+        cudaError_t e = cudaMemsetAsync(dmixed, 0, 4, c->stream);
+        if (e == cudaSuccess) {
+            k_row_weights<<<(uint32_t)sm_count() * 16, 256, 0, c->stream>>>(c->roff, c->w16p, c->meta, c->Np, c->roww,
+                                                                             dmixed);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&mixed, dmixed, 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        dev_free(c, dmixed);
+        if (e != cudaSuccess) return fail(c, SNN_E_CUDA, "row weights: %s", cudaGetErrorString(e));
+        if (!mixed) c->net.roww = c->roww;
+    }
+    *changed = (before != nullptr) != (c->net.roww != nullptr);
+    return SNN_OK;
+}
+
 snn_status pack_edges(snn_ctx* c)
 {
     if (!c->packed) return SNN_OK;
@@ -535,38 +641,6 @@ snn_status download(snn_ctx* c, void* dst, const void* src, size_t bytes, cudaSt
     return st;
 }
 
-// SNN_RECV_AUTO: the target-tiled receive pays per step for its plan and its
-// persistent launch, and per spike for every tile its row reaches (a row
-// record, split offsets, partial vectors at both ends); the global-atomic
-// receive pays per edge for an L2 atomic and spreads few spikes over the
-// whole grid in row pieces.  Tiled is taken for graphs of at least
-// kAutoMinEdges synapses whose rows reach each tile with kAutoMinSegment
-// edges or more on average (edge-weighted over instances, targets taken as
-// uniform over the instance).  Measured per step, tiled vs global: Vogels
-// 1M (rows of 1,000 over 70 tiles: 14 edges each) 38 vs 16 us; Brunel+ 100k
-// (4 tiles, 250 each) 42.6 vs 31.8 us; Vogels 4k (320k synapses) 12.4 vs
-// 6.4 us; Brunel 12.5k (one tile, 1,250 edges; 15.6M synapses) 11.5 vs
-// 9.2 us with binary32 weights; the 256-network sweep (2.9e9 synapses, 714
-// on average) 65 vs 188 us.
-constexpr uint64_t kAutoMinEdges = 200000000;
-constexpr double kAutoMinSegment = 400.0;
-
-bool auto_tiled(const snn_ctx* c)
-{
-    if (!c->rows_sorted || c->E < kAutoMinEdges) return false;
-    const double ch = c->vogels ? 2.0 : 1.0;
-    const double words = (double)(kTiledMaxWords / (uint32_t)ch / 256u * 256u);
-    double wsum = 0.0;
-    for (uint32_t b = 0; b < c->cfg.n_inst; ++b) {
-        const uint32_t n = c->params[b].n;
-        if (!n || !c->inst_edges[b]) continue;
-        const double npad = (double)(c->pbase[b + 1] - c->pbase[b]);
-        const double tiles = std::ceil(npad / words);
-        wsum += (double)c->inst_edges[b] * ((double)c->inst_edges[b] / n / tiles);
-    }
-    return wsum / (double)c->E >= kAutoMinSegment;
-}
-
 // Cut the tiles of the tiled receive; work[b] = expected delivered edges of
 // instance b per step (null: proportional to its synapses).
 snn_status plan_tiles(snn_ctx* c, const double* work)
@@ -627,6 +701,176 @@ snn_status retune(snn_ctx* c)
     st = capture(c, 1, &c->g1);
     if (st == SNN_OK && c->k_steps > 1) st = capture(c, c->k_steps, &c->gk);
     return st;
+}
+
+// The fused step (snn_fused.cuh) applies to the fixed Brunel model without
+// plasticity, the tiled receive with its per-step plan, 16-bit weights and a
+// delay of at least 3 steps (the plan of step t+1 made during step t reads
+// the spike counts of step t+2-d).
+bool fused_applies(const snn_ctx* c)
+{
+    return c->use_tiled && !c->use_bulk && !c->vogels && !c->generic && !c->stdp && c->w16 && c->cfg.delay >= 3;
+}
+
+// Turns the fused step on (its second plan sized like the first, which
+// tiled_plan re-allocates with the tiles).  Returns SNN_OK with c->fused
+// false when the kernel does not fit.
+snn_status setup_fused(snn_ctx* c)
+{
+    c->fused = false;
+    if (!fused_applies(c)) return SNN_OK;
+    uint32_t n_pad = 1;
+    while (n_pad < c->tiled.n_tiles) n_pad <<= 1;
+    const size_t smem = std::max<size_t>((size_t)c->tiled.max_len * 4 + (size_t)kFlatRecWords * 4, plan_smem(n_pad));
+    auto set = [&](auto kernel) { return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); };
+    if (set(k_step_fused<kWPacked, false>) != cudaSuccess || set(k_step_fused<kWPacked, true>) != cudaSuccess ||
+        set(k_step_fused<kW16, false>) != cudaSuccess || set(k_step_fused<kW16, true>) != cudaSuccess) {
+        cudaGetLastError();
+        return SNN_OK;  // keep the separate kernels
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_fused<kWPacked, false>, kTiledThreads, smem) !=
+            cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        return SNN_OK;
+    }
+    c->fused_grid = (uint32_t)(sm_count() * per_sm);
+    c->fused_smem = smem;
+    c->fused_lead = c->fused_grid;
+    dev_free(c, c->plan2.hdr);
+    dev_free(c, c->plan2.items);
+    dev_free(c, c->plan2.parts);
+    c->plan2.hdr = alloc_n<uint32_t>(c, 4);
+    c->plan2.items = alloc_n<ItemDev>(c, c->tiled.items_cap);
+    c->plan2.parts = alloc_n<uint32_t>(c, c->tiled.n_tiles);
+    if (!c->net.accx) c->net.accx = alloc_n<int32_t>(c, c->Np);
+    if (!c->plan2.hdr || !c->plan2.items || !c->plan2.parts || !c->net.accx)
+        return fail(c, SNN_E_NOMEM, "fused step buffers");
+    c->fused = true;
+    return SNN_OK;
+}
+
+// The receive forms a context can run.  Results do not depend on the form.
+enum RecvForm : int { kFormGlobal = 0, kFormTiled = 1, kFormFused = 2, kFormBulk = 3, kForms = 4 };
+
+// Switches the context to a receive form: builds what it reads (tiles and
+// split tables, packed edges, the fused step's buffers), frees the packed
+// edges when it does not read them, and captures the step graphs.  The
+// neuron state is not touched.  SNN_E_ARG when the form does not fit the
+// graph (the context then runs the global receive).
+snn_status use_form(snn_ctx* c, int form)
+{
+    drop_graphs(c);
+    c->fused = false;
+    c->use_tiled = form != kFormGlobal;
+    c->use_bulk = form == kFormBulk;
+    snn_status st = SNN_OK;
+    if (c->use_tiled) {
+        st = (c->rows_sorted && c->tiled_fits) ? plan_tiles(c, nullptr) : SNN_E_ARG;
+        if (st == SNN_OK && packable(c) && !c->pk32) {
+            c->pk32 = alloc_n<uint32_t>(c, c->E + 16);
+            if (!c->pk32) return fail(c, SNN_E_NOMEM, "packed edges");
+            CUDA_TRY(c, cudaMemsetAsync(c->pk32, 0, (c->E + 16) * 4, c->stream));
+            c->packed = true;
+            c->net.pk = c->pk32;
+            st = pack_edges(c);
+        }
+        if (st == SNN_OK && form == kFormFused) {
+            st = setup_fused(c);
+            if (st == SNN_OK && !c->fused) st = SNN_E_ARG;
+        }
+    }
+    if (st != SNN_OK || !c->use_tiled) {
+        tiled_free(c->tiled, [c](void* p) { dev_free(c, p); });
+        c->use_tiled = c->use_bulk = c->fused = false;
+    }
+    c->packed = c->use_tiled && c->pk32 && packable(c);
+    if (!c->packed && c->pk32) {
+        dev_free(c, c->pk32);
+        c->pk32 = nullptr;
+    }
+    c->net.pk = c->packed ? c->pk32 : nullptr;
+    c->form = c->fused ? kFormFused : (c->use_bulk ? kFormBulk : (c->use_tiled ? kFormTiled : kFormGlobal));
+    snn_status cs = capture(c, 1, &c->g1);
+    if (cs == SNN_OK && c->k_steps > 1) cs = capture(c, c->k_steps, &c->gk);
+    return st != SNN_OK ? st : cs;
+}
+
+// N_0 again: the weights loaded by snn_build_graph (plasticity changes
+// them) and the initial neuron state.
+snn_status reset_state(snn_ctx* c)
+{
+    if (c->stdp) {
+        k_weights_in<<<(uint32_t)sm_count() * 16, 256, 0, c->stream>>>(c->roff, c->meta, c->w_init, c->w16 ? 1 : 0,
+                                                                        c->Np, c->w16p, c->w32p, &c->ctl->err);
+        CUDA_TRY(c, cudaGetLastError());
+    }
+    return init_state(c);
+}
+
+// Steps of a tuning run before its timed window, and in it.
+uint32_t tune_warm_steps(const snn_ctx* c) { return std::min<uint32_t>(c->cfg.delay + 150u, 1100u); }
+constexpr uint32_t kTuneSteps = 48;
+
+// SNN_RECV_AUTO: every form that applies runs from the initial state N_0
+// over the same steps (past the first deliveries), timed with CUDA events
+// over the last kTuneSteps of them; the fastest is kept.  The simulation is
+// deterministic, so every form meets the same spikes; the caller's run
+// starts from N_0 afterwards (init_state).
+snn_status tune_receive(snn_ctx* c)
+{
+    int cand[kForms];
+    int nc = 0;
+    cand[nc++] = kFormGlobal;
+    if (c->rows_sorted && c->tiled_fits) {
+        cand[nc++] = kFormTiled;
+        c->use_tiled = true;
+        c->use_bulk = false;
+        if (!(c->cfg.flags & SNN_F_SERIAL) && fused_applies(c)) cand[nc++] = kFormFused;
+    }
+    for (float& x : c->tune_ms) x = 0.f;
+    if (nc == 1) return use_form(c, cand[0]);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(c, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(c, SNN_E_CUDA, "cudaEventCreate");
+    }
+    int best = -1;
+    snn_status st = SNN_OK;
+    const uint32_t warm = tune_warm_steps(c);
+    auto launch = [&](uint32_t n) -> snn_status {
+        while (c->gk && n >= c->k_steps) {
+            CUDA_TRY(c, cudaGraphLaunch(c->gk, c->stream));
+            n -= c->k_steps;
+        }
+        while (n--) CUDA_TRY(c, cudaGraphLaunch(c->g1, c->stream));
+        return SNN_OK;
+    };
+    for (int i = 0; i < nc && st == SNN_OK; ++i) {
+        st = use_form(c, cand[i]);
+        if (st == SNN_E_ARG) {  // the form does not fit after all: not a candidate
+            st = SNN_OK;
+            continue;
+        }
+        if (st == SNN_OK) st = reset_state(c);
+        if (st == SNN_OK) st = launch(warm);
+        if (st == SNN_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) st = fail(c, SNN_E_CUDA, "event record");
+        if (st == SNN_OK) st = launch(kTuneSteps);
+        if (st == SNN_OK && cudaEventRecord(e1, c->stream) != cudaSuccess) st = fail(c, SNN_E_CUDA, "event record");
+        if (st == SNN_OK) st = check_device_errors(c);
+        float ms = 0.f;
+        if (st == SNN_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = fail(c, SNN_E_CUDA, "event time");
+        if (st == SNN_OK) {
+            c->tune_ms[cand[i]] = ms / kTuneSteps;
+            if (best < 0 || c->tune_ms[cand[i]] < c->tune_ms[best]) best = cand[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SNN_OK) return st;
+    return use_form(c, best < 0 ? kFormGlobal : best);
 }
 
 }  // namespace
@@ -857,6 +1101,9 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
     for (void* p : {(void*)c->roff, (void*)c->tgt, (void*)c->w16p, (void*)c->w32p, (void*)c->meta, (void*)c->coff,
                     (void*)c->cedge, (void*)c->cpre, (void*)c->w_init, (void*)c->rinfo, (void*)c->pk32})
         dev_free(c, p);
+    dev_free(c, c->roww);
+    c->roww = nullptr;
+    c->net.roww = nullptr;
     c->rinfo = nullptr;
     c->pk32 = nullptr;
     c->packed = false;
@@ -1002,6 +1249,14 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
     Net& n = c->net;
     n.rinfo = c->rinfo;
     n.roff = c->roff;
+    n.meta = c->meta;
+    n.w16 = c->w16p;
+    {
+        bool changed = false;
+        snn_status st = refresh_row_weights(c, &changed);
+        if (st != SNN_OK) return st;
+    }
+    n.roff = c->roff;
     n.tgt = c->tgt;
     n.w16 = c->w16p;
     n.w32 = c->w32p;
@@ -1015,38 +1270,44 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
     for (uint32_t b = 0; b < c->cfg.n_inst; ++b)
         c->inst_edges[b] = row_off[c->g_off[b + 1]] - row_off[c->g_off[b]];
     c->use_tiled = false;
-    c->use_bulk = c->cfg.receive == SNN_RECV_BULK;
+    c->use_bulk = false;
     c->tune_count = 0;
     c->tune_next = c->cfg.tune_steps ? c->cfg.tune_steps : 256;
     c->spk_seen.assign(c->cfg.n_inst, 0);
-    if (c->cfg.receive == SNN_RECV_AUTO && !auto_tiled(c)) {
-        // the global-atomic receive is kept
-    } else if (c->cfg.receive != SNN_RECV_GLOBAL) {
-        snn_status st = c->rows_sorted ? plan_tiles(c, nullptr) : SNN_E_ARG;
-        if (st == SNN_OK) {
-            c->use_tiled = true;
-            if (packable(c)) {
-                c->pk32 = alloc_n<uint32_t>(c, E + 16);
-                if (!c->pk32) return fail(c, SNN_E_NOMEM, "packed edges");
-                CUDA_TRY(c, cudaMemsetAsync(c->pk32, 0, (E + 16) * 4, s));
-                c->packed = true;
-                n.pk = c->pk32;
-                st = pack_edges(c);
-                if (st != SNN_OK) return st;
-            }
-        } else {
-            tiled_free(c->tiled, [c](void* p) { dev_free(c, p); });
-            if (c->cfg.receive == SNN_RECV_TILED || c->cfg.receive == SNN_RECV_BULK)
-                return fail(c, st, c->rows_sorted ? "the tiled receive does not fit this graph"
-                                                  : "the tiled receive needs rows sorted by target");
-        }
+    {
+        // the flat stream holds a segment's first 16-byte vector in 32 bits and
+        // its length in 24
+        uint64_t max_deg = 0;
+        for (uint32_t j = 0; j < N; ++j) max_deg = std::max<uint64_t>(max_deg, row_off[j + 1] - row_off[j]);
+        c->tiled_fits = E < (1ull << 34) && max_deg < (1ull << 24);
     }
-    c->graph_loaded = true;
-    snn_status st = init_state(c);
-    if (st != SNN_OK) return st;
     c->k_steps = c->cfg.steps_per_graph ? c->cfg.steps_per_graph : 16;
-    st = capture(c, 1, &c->g1);
-    if (st == SNN_OK && c->k_steps > 1) st = capture(c, c->k_steps, &c->gk);
+    c->tuned = false;
+    for (float& x : c->tune_ms) x = 0.f;
+    c->graph_loaded = true;
+    snn_status st = SNN_OK;
+    if (c->cfg.receive == SNN_RECV_AUTO) {
+        st = tune_receive(c);
+        c->tuned = st == SNN_OK;
+    } else if (c->cfg.receive == SNN_RECV_GLOBAL) {
+        st = use_form(c, kFormGlobal);
+    } else if (!c->rows_sorted || !c->tiled_fits) {
+        st = fail(c, SNN_E_ARG, c->rows_sorted ? "the tiled receive does not fit this graph"
+                                               : "the tiled receive needs rows sorted by target");
+    } else if (c->cfg.receive == SNN_RECV_BULK) {
+        st = use_form(c, kFormBulk);
+    } else {
+        c->use_tiled = true;
+        c->use_bulk = false;
+        const bool fuse = fused_applies(c) && !(c->cfg.flags & SNN_F_SERIAL);
+        st = use_form(c, fuse ? kFormFused : kFormTiled);
+        if (st == SNN_E_ARG && fuse) st = use_form(c, kFormTiled);  // the fused kernel did not fit
+    }
+    if (st != SNN_OK) {
+        c->graph_loaded = false;
+        return st;
+    }
+    st = reset_state(c);
     if (st != SNN_OK) return st;
     CUDA_TRY(c, cudaStreamSynchronize(s));
     return SNN_OK;
@@ -1056,12 +1317,7 @@ snn_status snn_reset(snn_ctx* c)
 {
     if (!c) return SNN_E_ARG;
     if (!c->graph_loaded) return fail(c, SNN_E_STATE, "no graph loaded");
-    if (c->stdp) {
-        k_weights_in<<<(uint32_t)sm_count() * 16, 256, 0, c->stream>>>(c->roff, c->meta, c->w_init, c->w16 ? 1 : 0,
-                                                                        c->Np, c->w16p, c->w32p, &c->ctl->err);
-        CUDA_TRY(c, cudaGetLastError());
-    }
-    snn_status st = init_state(c);
+    snn_status st = reset_state(c);
     if (st != SNN_OK) return st;
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return SNN_OK;
@@ -1250,7 +1506,15 @@ static snn_status field_ptr(snn_ctx* c, snn_field f, void** p, size_t* elem, boo
     case SNN_FIELD_R: *p = c->net.r; *u8 = true; break;
     case SNN_FIELD_X: *p = c->net.x; break;
     case SNN_FIELD_Y: *p = c->net.y; break;
-    case SNN_FIELD_ACC0: *p = c->net.acc0; break;
+    case SNN_FIELD_ACC0: {  // the input of the next update: with the fused step, buffer t & 1
+        *p = c->net.acc0;
+        if (c->fused) {
+            unsigned long long t = 0;
+            CUDA_TRY(c, cudaMemcpy(&t, &c->ctl->t, 8, cudaMemcpyDeviceToHost));
+            if (t & 1ull) *p = c->net.accx;
+        }
+        break;
+    }
     case SNN_FIELD_ACC1: *p = c->net.acc1; break;
     case SNN_FIELD_MODEL: *p = c->mstate; *elem = c->mbytes; break;
     default: return fail(c, SNN_E_ARG, "unknown field %d", (int)f);
@@ -1326,6 +1590,13 @@ snn_status snn_write_state(snn_ctx* c, snn_field f, const void* host)
         if (err & kErrBadWeight) return fail(c, SNN_E_ARG, "a weight does not fit its row's int16 code and shift");
         snn_status st = pack_edges(c);
         if (st == SNN_OK) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        bool changed = false;
+        if (st == SNN_OK) st = refresh_row_weights(c, &changed);
+        if (st == SNN_OK && changed) {  // the receive reads another layout now
+            drop_graphs(c);
+            st = capture(c, 1, &c->g1);
+            if (st == SNN_OK && c->k_steps > 1) st = capture(c, c->k_steps, &c->gk);
+        }
         return st;
     }
     void* p;
@@ -1413,8 +1684,12 @@ snn_status snn_get_info(snn_ctx* c, snn_info* info)
     info->rows_sorted = c->rows_sorted ? 1 : 0;
     info->edges = c->E;
     info->device_bytes = c->bytes_held;
-    info->edge_bytes = c->use_tiled ? edge_bytes_of(c->packed ? kWPacked : (c->w16 ? kW16 : kWF32)) : (c->w16 ? 6u : 8u);
+    info->edge_bytes = c->use_tiled ? edge_bytes_of(c->packed ? kWPacked : (c->w16 ? kW16 : kWF32))
+                                    : (c->net.roww ? 4u : (c->w16 ? 6u : 8u));
     info->model_state_bytes = (uint32_t)c->mbytes;
+    info->fused = c->fused ? 1u : 0u;
+    info->tuned = c->tuned ? 1u : 0u;
+    for (int f = 0; f < 4; ++f) info->tune_ms[f] = c->tune_ms[f];
     return SNN_OK;
 }
 

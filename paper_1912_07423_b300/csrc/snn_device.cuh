@@ -5,11 +5,16 @@
 //              pbase_b a multiple of 256, so the 256 neurons one warp of the
 //              update kernel advances (8 per thread) never straddle two
 //              instances.
-//              V, ge, gi, x, y: float[Np]; r: uint8[Np]; acc0, acc1: int32[Np].
+//              V, ge, gi, x, y: float[Np]; r: uint8[Np]; acc0, acc1: int32[Np];
+//              with the fused step a second channel-0 buffer accx: int32[Np]
+//              (the input of step t is in acc0 for even t, accx for odd t).
 //   graph    : CSR over padded ids, roff: uint64[Np+1], tgt: uint32[E]
 //              (padded ids, sorted rows), weights int16[E] (code, value =
 //              code << shift(row)) or float[E] (exact lattice integers),
-//              meta: uint8[Np] = shift | exc_source << 6 | channel << 7.
+//              meta: uint8[Np] = shift | exc_source << 6 | channel << 7;
+//              when every row carries one weight (the source population's),
+//              roww: int32[Np] holds it and the global receive reads the
+//              targets alone.
 //   queues   : the delay FIFO is a ring of D spike queues, uint32[D][Np]
 //              (Section III-A-2: arrays with an atomic insertion index).  In
 //              every slot instance b owns the region [pbase_b, pbase_b+n_b)
@@ -92,12 +97,15 @@ struct Net {
     uint8_t* r;
     int32_t* acc0;
     int32_t* acc1;
+    int32_t* accx;          // fused step: the second channel-0 input buffer (the update of step t
+                            // reads buffer t & 1: acc0 for even t, accx for odd t)
     const uint64_t* roff;
     const uint32_t* tgt;
     int16_t* w16;
     float* w32;
     const uint8_t* meta;
     const uint4* rinfo;     // per padded row: start (lo, hi), length, meta -- one load per spike
+    const int32_t* roww;    // row weights (lattice units) when every row carries one (null otherwise)
     const uint32_t* pk;     // packed edges for the tiled receive (null when not used)
     const uint64_t* coff;   // STDP: plastic in-edges per padded post id
     const uint32_t* cedge;  // STDP: edge index of each plastic in-edge

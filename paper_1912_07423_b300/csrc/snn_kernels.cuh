@@ -46,35 +46,41 @@ __device__ __forceinline__ uint32_t poisson_count(const uint32_t* __restrict__ T
     return k;
 }
 
-// SYN: 0 no plasticity, 1 eager traces (x and y every step), 2 lazy (y, the
-// ring of decayed y, the spike history and the expiry queue)
-template <int MODEL, int SYN, bool STATS, int NPT>
-__global__ void __launch_bounds__(256) k_update(Net n)
+// Per-step bookkeeping of the previous step, done once per step by the
+// threads gt (grid-wide index) of the step's update (its kernels have
+// finished): fold its queue indices into the counters, clear the next step's
+// indices and the tile counter of the next receive, and set the log position
+// of this step's first spike (the previous step's base plus its count; 0 at
+// the first step of the log).
+__device__ __forceinline__ void step_bookkeeping(const Net& n, unsigned long long t, uint32_t gt, bool lazy)
 {
-    static_assert(NPT == 4 || NPT == 8, "one Philox block serves 8 neurons");
-    const unsigned long long t = n.ctl->t + n.k;
-    // per-step bookkeeping of the previous step (its kernels have finished):
-    // fold its queue indices into the counters, clear the next step's indices
-    // and the tile counter of the next receive
-    {
-        const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
-        const uint32_t sn = (uint32_t)((t + 1) & (n.cr - 1));
-        if (gt < n.n_inst) {
-            if (t > 0) n.inst_spikes[gt] += n.icount[(size_t)((t - 1) & (n.cr - 1)) * n.n_inst + gt];
-            n.icount[(size_t)sn * n.n_inst + gt] = 0;
-        }
-        if (gt == 0) {
-            if (t > 0) n.ctl->spikes += n.count[(t - 1) & (n.cr - 1)];
-            n.count[sn] = 0;
-            n.tile_ctr[(t + 1) & 1ull] = 0;
-            if (SYN == 2) n.xcount[(t + 1) & 1ull] = 0;
+    const uint32_t sn = (uint32_t)((t + 1) & (n.cr - 1));
+    if (gt < n.n_inst) {
+        if (t > 0) n.inst_spikes[gt] += n.icount[(size_t)((t - 1) & (n.cr - 1)) * n.n_inst + gt];
+        n.icount[(size_t)sn * n.n_inst + gt] = 0;
+    }
+    if (gt == 0) {
+        if (t > 0) n.ctl->spikes += n.count[(t - 1) & (n.cr - 1)];
+        n.count[sn] = 0;
+        n.tile_ctr[(t + 1) & 1ull] = 0;
+        if (lazy) n.xcount[(t + 1) & 1ull] = 0;
+        if (n.log_cap) {
+            const unsigned long long tp = t - 1;
+            n.lbase[t & (n.cr - 1)] = (t > n.ctl->t_log0) ? n.lbase[tp & (n.cr - 1)] + n.count[tp & (n.cr - 1)] : 0ull;
         }
     }
-    // a receive launched as this kernel's programmatic dependent may start
-    // (it waits for this kernel before touching what it writes)
-    if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// SYN: 0 no plasticity, 1 eager traces (x and y every step), 2 lazy (y, the
+// ring of decayed y, the spike history and the expiry queue).  Thread g of
+// the step's update advances neurons g*NPT .. g*NPT+NPT-1 (whole warps: a
+// warp covers 32*NPT slots inside one instance); acc0 is the channel-0 input
+// it reads and clears.
+template <int MODEL, int SYN, bool STATS, int NPT>
+__device__ __forceinline__ void update_neurons(const Net& n, unsigned long long t, uint32_t g, int32_t* acc0)
+{
+    static_assert(NPT == 4 || NPT == 8, "one Philox block serves 8 neurons");
     const uint32_t G = n.Np / NPT;
-    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = g < G;  // whole warps: Np is a multiple of 256
     const uint32_t id0 = g * NPT;
     uint32_t spk = 0;  // bit k: neuron id0 + k spiked
@@ -90,7 +96,7 @@ __global__ void __launch_bounds__(256) k_update(Net n)
         for (int h = 0; h < NPT / 4; ++h) {
             *reinterpret_cast<float4*>(V + 4 * h) = *reinterpret_cast<const float4*>(n.V + id0 + 4 * h);
             *reinterpret_cast<uint32_t*>(r + 4 * h) = *reinterpret_cast<const uint32_t*>(n.r + id0 + 4 * h);
-            *reinterpret_cast<int4*>(a0 + 4 * h) = *reinterpret_cast<const int4*>(n.acc0 + id0 + 4 * h);
+            *reinterpret_cast<int4*>(a0 + 4 * h) = *reinterpret_cast<const int4*>(acc0 + id0 + 4 * h);
         }
     }
     const uint32_t b = active ? __ldg(n.inst_of_w32 + (id0 >> 5)) : 0u;  // uniform across the warp
@@ -277,10 +283,6 @@ __global__ void __launch_bounds__(256) k_update(Net n)
     const uint32_t lane = lane_id();
     const uint32_t slot_q = (uint32_t)(t % n.D);
     const uint32_t slot_c = (uint32_t)(t & (n.cr - 1));
-    if (blockIdx.x == 0 && threadIdx.x == 0 && n.log_cap) {
-        const unsigned long long tp = t - 1;
-        n.lbase[slot_c] = (t > n.ctl->t_log0) ? n.lbase[tp & (n.cr - 1)] + n.count[tp & (n.cr - 1)] : 0ull;
-    }
     if (SYN != 0) {
         // 32 / NPT lanes cover one 32-neuron bitmask word
         constexpr uint32_t L = 32 / NPT;
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(256) k_update(Net n)
         for (int h = 0; h < NPT / 4; ++h) {
             *reinterpret_cast<float4*>(n.V + id0 + 4 * h) = *reinterpret_cast<float4*>(V + 4 * h);
             *reinterpret_cast<uint32_t*>(n.r + id0 + 4 * h) = *reinterpret_cast<uint32_t*>(r + 4 * h);
-            *reinterpret_cast<int4*>(n.acc0 + id0 + 4 * h) = make_int4(0, 0, 0, 0);
+            *reinterpret_cast<int4*>(acc0 + id0 + 4 * h) = make_int4(0, 0, 0, 0);
         }
     }
     if (total == 0) return;
@@ -364,6 +366,18 @@ __global__ void __launch_bounds__(256) k_update(Net n)
         }
         ++k;
     }
+}
+
+template <int MODEL, int SYN, bool STATS, int NPT>
+__global__ void __launch_bounds__(256) k_update(Net n)
+{
+    const unsigned long long t = n.ctl->t + n.k;
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    step_bookkeeping(n, t, g, SYN == 2);
+    // a receive launched as this kernel's programmatic dependent may start
+    // (it waits for this kernel before touching what it writes)
+    if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    update_neurons<MODEL, SYN, STATS, NPT>(n, t, g, n.acc0);
 }
 
 // Raster readout: log entries (step << 32 | padded id) -> sortable keys
@@ -437,7 +451,10 @@ __device__ __forceinline__ void piece_of(uint64_t beg, uint64_t end, uint32_t c,
 // L2-resident int32 accumulators of the targets (order-independent integer
 // sums).
 // ---------------------------------------------------------------------------
-template <bool W16>
+// ROWW: every row carries one weight (the source population's, as in the
+// paper's models: Section III-A-2, Table 2), held per row in n.roww, so the
+// walk reads the 4-byte targets alone.
+template <bool W16, bool ROWW>
 __global__ void __launch_bounds__(256) k_receive_global(Net n)
 {
     const unsigned long long t = n.ctl->t + n.k;
@@ -449,6 +466,7 @@ __global__ void __launch_bounds__(256) k_receive_global(Net n)
         piece_of(__ldg(n.roff + j), __ldg(n.roff + j + 1), c, lk, pb, pe);
         const uint32_t meta = __ldg(n.meta + j);
         const uint32_t shift = meta & 31u;
+        const int32_t rw = ROWW ? __ldg(n.roww + j) : 0;
         int32_t* acc = (meta & 0x80u) ? n.acc1 : n.acc0;
         ev += pe - pb;
         uint64_t e = pb + lane;
@@ -458,14 +476,16 @@ __global__ void __launch_bounds__(256) k_receive_global(Net n)
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 tg[k] = __ldg(n.tgt + e + 32 * k);
-                wv[k] = W16 ? ((int32_t)__ldg(n.w16 + e + 32 * k) << shift) : __float2int_rz(__ldg(n.w32 + e + 32 * k));
+                wv[k] = ROWW ? rw
+                             : (W16 ? ((int32_t)__ldg(n.w16 + e + 32 * k) << shift)
+                                    : __float2int_rz(__ldg(n.w32 + e + 32 * k)));
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) atomicAdd(acc + tg[k], wv[k]);
         }
         for (; e < pe; e += 32) {
             const uint32_t tg = __ldg(n.tgt + e);
-            const int32_t wv = W16 ? ((int32_t)__ldg(n.w16 + e) << shift) : __float2int_rz(__ldg(n.w32 + e));
+            const int32_t wv = ROWW ? rw : (W16 ? ((int32_t)__ldg(n.w16 + e) << shift) : __float2int_rz(__ldg(n.w32 + e)));
             atomicAdd(acc + tg, wv);
         }
     });
@@ -842,6 +862,26 @@ __global__ void k_init_state(Net n, int vogels, int stdp, int lazy)
 // they stay inside the source's instance), picks the row's weight shift and
 // writes the stored weights.
 // ---------------------------------------------------------------------------
+// The weight of every row whose edges all carry the same 16-bit code:
+// roww[pj] = code << shift (0 for an empty row); *mixed is set when some row
+// carries two or more codes.  A warp per row.
+__global__ void k_row_weights(const uint64_t* __restrict__ roff, const int16_t* __restrict__ w16,
+                              const uint8_t* __restrict__ meta, uint32_t Np, int32_t* __restrict__ roww,
+                              unsigned int* mixed)
+{
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t pj = warp; pj < Np; pj += nwarps) {
+        const uint64_t beg = roff[pj], end = roff[pj + 1];
+        const int16_t w0 = beg < end ? w16[beg] : (int16_t)0;
+        bool same = true;
+        for (uint64_t e = beg + lane; e < end; e += 32) same = same && w16[e] == w0;
+        if (!__all_sync(kFull, same) && lane == 0) atomicOr(mixed, 1u);
+        if (lane == 0) roww[pj] = (int32_t)w0 << (meta[pj] & 31u);
+    }
+}
+
 struct RowMapArgs {
     const uint64_t* roff;        // padded row offsets (Np+1)
     const uint32_t* row_src;     // padded id -> global id (or ~0u for padding)

@@ -104,7 +104,8 @@ struct TiledPlan {
 // the SM's loads in flight.
 constexpr int kTiledThreads = 512;
 constexpr int kTiledCtasPerSm = 2;
-constexpr uint32_t kTiledMaxWords = 28672;  // int32 accumulators of one CTA (112 KB)
+constexpr uint32_t kTiledMaxWords = 25600;  // int32 accumulators of one CTA (100 KB; with the flat stream's
+                                            // 12 KB of spike records two CTAs fill an SM's shared memory)
 constexpr int kVec = 4;            // 4-edge vectors in flight per lane
 constexpr uint32_t kMaxParts = 255;
 constexpr uint32_t kMergeChunk = 4096;
@@ -331,20 +332,207 @@ __device__ __forceinline__ void deliver_part(const Net& n, const TileDev& T, con
     }
 }
 
+// ---------------------------------------------------------------------------
+// Flat delivery: the row segments of a part's spikes are laid end to end as
+// one stream of 16-byte edge vectors, and the CTA's warps walk that stream
+// in chunks of 32 x FV vectors (FV per lane, all in flight together).  Every
+// lane keeps FV loads outstanding whatever the row lengths are, and the
+// warps of the CTA finish within one chunk of each other.  Per batch of up
+// to kFlatBatch spikes the CTA first loads every spike's row record (and
+// split offsets) in parallel into shared memory -- first vector, vector
+// count (exclusive scan), length, head offset, shift and channel -- then
+// streams; a lane finds the spike of its vector by walking the scan forward
+// from the chunk's first spike (found by a two-level warp ballot).
+// ---------------------------------------------------------------------------
+constexpr uint32_t kFlatBatch = 1024;  // spike records per batch
+constexpr uint32_t kFlatRecWords = 3 * kFlatBatch + 4;  // gv0[], vscan[] (+1), info[]
+__host__ __device__ constexpr int flat_vec_of(int wm) { return wm == kWF32 ? 4 : (wm == kW16 ? 5 : 6); }
+
+// The first spike s of the batch with vscan[s] <= v < vscan[s+1] (whole warp;
+// nb <= kFlatBatch, vscan[0] = 0 <= v < vscan[nb]).
+__device__ __forceinline__ uint32_t flat_first_spike(const uint32_t* vscan, uint32_t nb, uint32_t v, uint32_t lane)
+{
+    const uint32_t p1 = lane * 32u;
+    const uint32_t m1 = __ballot_sync(0xffffffffu, p1 < nb && vscan[p1] <= v);
+    const uint32_t base = (31u - __clz(m1)) * 32u;
+    const uint32_t p2 = base + lane;
+    const uint32_t m2 = __ballot_sync(0xffffffffu, p2 < nb && vscan[p2] <= v);
+    return base + 31u - __clz(m2);
+}
+
+// Delivers the spikes [s_beg, s_end) of the instance's queue q (local ids
+// from pbase) to tile T through the flat stream; rec: kFlatRecWords words of
+// shared memory.  last(): called by thread 0 once the last batch's records
+// are in place (the caller takes its next work item there, while the warps
+// stream).  ev: every lane of a warp adds the warp's delivered edges.
+template <int WM, int CH, class Last>
+__device__ __forceinline__ void deliver_flat(const Net& n, const TileDev& T, const uint32_t* q, const uint32_t* sp,
+                                             int32_t* acc_s, uint32_t* rec, uint32_t s_beg, uint32_t s_end,
+                                             unsigned long long pol, unsigned long long& ev, bool& bad, Last last)
+{
+    constexpr int FV = flat_vec_of(WM);
+    constexpr uint32_t kChunk = 32u * FV;
+    __shared__ uint32_t s_wsum[32];
+    __shared__ uint32_t s_next;  // next chunk of the stream (vectors)
+    uint32_t* gv0 = rec;
+    uint32_t* vscan = rec + kFlatBatch;
+    uint32_t* info = vscan + kFlatBatch + 1;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t nsplit = T.ntiles - 1;
+    const uint32_t x0 = WM == kWPacked ? T.lo - T.pbase : T.lo;
+    constexpr uint32_t per_thread = kFlatBatch / kTiledThreads;  // records per thread (the CTA has kTiledThreads)
+    static_assert(kFlatBatch % kTiledThreads == 0 && per_thread <= 4, "whole records per thread");
+    if (s_end <= s_beg && tid == 0) last();
+    for (uint32_t b0 = s_beg; b0 < s_end; b0 += kFlatBatch) {
+        const uint32_t nb = min(kFlatBatch, s_end - b0);
+        // the records of this batch, per_thread consecutive spikes per thread
+        uint32_t nv_sum = 0, len_sum = 0, nvs[per_thread];
+#pragma unroll
+        for (uint32_t h = 0; h < per_thread; ++h) {
+            nvs[h] = 0;
+            const uint32_t i = per_thread * tid + h;
+            if (i >= nb) continue;
+            const uint32_t j = q[b0 + i];
+            const uint4 r = __ldg(n.rinfo + j);
+            uint64_t sb = ((unsigned long long)r.y << 32) | r.x;
+            uint64_t se = sb + r.z;
+            if (nsplit) {
+                const uint32_t* sj = sp + (size_t)(j - T.pbase) * nsplit;
+                const uint64_t beg = sb;
+                if (T.tau > 0) sb = beg + __ldg(sj + T.tau - 1);
+                if (T.tau < nsplit) se = beg + __ldg(sj + T.tau);
+            }
+            const uint32_t len = (uint32_t)(se - sb), hs = (uint32_t)(sb & 3u);
+            gv0[i] = (uint32_t)(sb >> 2);
+            info[i] = len | hs << 24 | (r.w & 31u) << 26 | ((CH == 2 && (r.w & 0x80u)) ? 1u << 31 : 0u);
+            nvs[h] = len ? (hs + len + 3u) >> 2 : 0u;
+            nv_sum += nvs[h];
+            len_sum += len;
+        }
+        // exclusive scan of the vector counts over the batch
+        uint32_t incl = nv_sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) len_sum += __shfl_xor_sync(0xffffffffu, len_sum, o);
+        ev += len_sum;
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            if (lane == 0) s_next = 0;
+            const uint32_t w = lane < nwarps ? s_wsum[lane] : 0u;
+            uint32_t x = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= (uint32_t)o) x += y;
+            }
+            if (lane < nwarps) s_wsum[lane] = x - w;
+        }
+        __syncthreads();
+        {
+            uint32_t v = s_wsum[warp] + incl - nv_sum;
+#pragma unroll
+            for (uint32_t h = 0; h < per_thread; ++h) {
+                const uint32_t i = per_thread * tid + h;
+                if (i < nb) vscan[i] = v;
+                v += nvs[h];
+            }
+            if (tid == blockDim.x - 1) vscan[nb] = v;  // the batch's vector total (entries past nb count 0)
+        }
+        __syncthreads();
+        if (b0 + kFlatBatch >= s_end && tid == 0) last();
+        const uint32_t V = vscan[nb];
+        // chunks are taken from a shared counter (the next one while the
+        // current one's loads are in flight), so a warp held up elsewhere
+        // takes fewer of them
+        uint32_t c0 = 0;
+        if (lane == 0) c0 = atomicAdd(&s_next, kChunk);
+        c0 = __shfl_sync(0xffffffffu, c0, 0);
+        while (c0 < V) {
+            uint32_t s = flat_first_spike(vscan, nb, c0, lane);
+            uint4 tv[FV];
+            uint2 wh[WM == kW16 ? FV : 1];  // int16 codes (kW16)
+            uint4 wf[WM == kWF32 ? FV : 1]; // binary32 weights (kWF32)
+            uint32_t mk[FV];                // first valid edge | end << 2 | shift << 5 | channel << 10
+#pragma unroll
+            for (int k = 0; k < FV; ++k) {
+                const uint32_t v = c0 + 32u * k + lane;
+                mk[k] = 0;
+                tv[k] = make_uint4(0, 0, 0, 0);
+                if (v < V) {
+                    while (vscan[s + 1] <= v) ++s;
+                    const uint32_t inf = info[s], len = inf & 0xffffffu, hs = (inf >> 24) & 3u;
+                    const uint32_t rel = v - vscan[s];
+                    const int first = (int)(4u * rel) - (int)hs;  // segment edge of lane element 0
+                    const uint32_t lo = first < 0 ? (uint32_t)(-first) : 0u;
+                    const uint32_t hi = (int)len - first < 4 ? (uint32_t)((int)len - first) : 4u;
+                    mk[k] = lo | hi << 2 | ((inf >> 26) & 31u) << 5 | (inf >> 31) << 10;
+                    const uint64_t e = 4ull * ((unsigned long long)gv0[s] + rel);
+                    if constexpr (WM == kWPacked) {
+                        tv[k] = ld_edges4(n.pk + e, pol);
+                    } else {
+                        tv[k] = ld_edges4(n.tgt + e, pol);
+                        if constexpr (WM == kW16) wh[k] = ld_edges2(n.w16 + e, pol);
+                        else wf[k] = ld_edges4(n.w32 + e, pol);
+                    }
+                }
+            }
+            uint32_t cn = 0;
+            if (lane == 0) cn = atomicAdd(&s_next, kChunk);
+#pragma unroll
+            for (int k = 0; k < FV; ++k) {
+                const uint32_t m = mk[k], lo = m & 3u, hi = (m >> 2) & 7u, shift = (m >> 5) & 31u;
+                int32_t* a = acc_s + ((CH == 2 && (m >> 10 & 1u)) ? T.len : 0u);
+                const uint32_t vv[4] = {tv[k].x, tv[k].y, tv[k].z, tv[k].w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if ((uint32_t)i < lo || (uint32_t)i >= hi) continue;
+                    uint32_t x;
+                    int32_t w;
+                    if constexpr (WM == kWPacked) {
+                        x = (vv[i] >> 16) - x0;
+                        w = (int32_t)(int16_t)(vv[i] & 0xffffu) << shift;
+                    } else if constexpr (WM == kW16) {
+                        x = vv[i] - x0;
+                        const uint32_t h2 = i < 2 ? wh[k].x : wh[k].y;
+                        w = (int32_t)(int16_t)((i & 1) ? (h2 >> 16) : (h2 & 0xffffu)) << shift;
+                    } else {
+                        x = vv[i] - x0;
+                        const uint32_t fw = i == 0 ? wf[k].x : i == 1 ? wf[k].y : i == 2 ? wf[k].z : wf[k].w;
+                        w = __float2int_rz(__uint_as_float(fw));
+                    }
+                    if (x < T.len)
+                        atomicAdd(a + x, w);
+                    else
+                        bad = true;
+                }
+            }
+            c0 = __shfl_sync(0xffffffffu, cn, 0);
+        }
+        __syncthreads();  // the next batch rewrites the records
+    }
+}
+
 // Shared memory of k_plan for n_pad (a power of two >= the tiles) entries.
 __host__ __device__ inline size_t plan_smem(uint32_t n_pad) { return (size_t)n_pad * 20; }
 
-// The plan of step t's receive (one block).  Tile k gets P_k parts as the
-// header of this file states; the items are ordered by work per part,
-// heaviest first, ties by tile index: 64-bit keys sorted by rank (each key
-// counts the smaller ones) or, for many tiles, by a bitonic network.
-__global__ void __launch_bounds__(kPlanThreads, 1) k_plan(Net n, const TileDev* __restrict__ tiles, uint32_t n_tiles,
-                                                          StepPlan sp, uint32_t n_ctas, uint32_t cap, uint32_t items_cap)
+// The plan of step t's receive (one block of PT threads; plan_s: plan_smem
+// bytes of shared memory).  Tile k gets P_k parts as the header of this file
+// states; the items are ordered by work per part, heaviest first, ties by
+// tile index: 64-bit keys sorted by rank (each key counts the smaller ones)
+// or, for many tiles, by a bitonic network.
+template <int PT>
+__device__ __forceinline__ void plan_step(const Net& n, unsigned long long t, const TileDev* __restrict__ tiles,
+                                          uint32_t n_tiles, const StepPlan& sp, uint32_t n_ctas, uint32_t cap,
+                                          uint32_t items_cap, unsigned char* plan_s)
 {
-    extern __shared__ __align__(16) unsigned char plan_s[];
-    __shared__ float red[32];
+    static_assert(PT >= 32 && PT % 32 == 0 && kRankSortMax % PT == 0, "whole warps, rank-sort slots per thread");
+    __shared__ float red[PT / 32];
     __shared__ uint32_t s_act, s_items;
-    const unsigned long long t = n.ctl->t + n.k;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     if (t + 1 < n.d) {
         if (threadIdx.x == 0) sp.hdr[0] = 0;
@@ -374,7 +562,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1) k_plan(Net n, const TileDev* 
     if (lane == 0) red[warp] = wsum;
     __syncthreads();
     float W = 0.f;
-    for (uint32_t i = 0; i < blockDim.x / 32; ++i) W += red[i];
+    for (uint32_t i = 0; i < PT / 32; ++i) W += red[i];
     const float target = W / (kItemsPerCta * (float)n_ctas);
     for (uint32_t k = threadIdx.x; k < n_pad; k += blockDim.x) {
         unsigned long long kk = ~0ull;
@@ -415,11 +603,11 @@ __global__ void __launch_bounds__(kPlanThreads, 1) k_plan(Net n, const TileDev* 
             if (c) atomicAdd(&rank[k], c);
         }
         __syncthreads();
-        uint32_t r[kRankSortMax / kPlanThreads];
-        for (uint32_t i = 0, k = threadIdx.x; i < kRankSortMax / kPlanThreads; ++i, k += blockDim.x)
+        uint32_t r[kRankSortMax / PT];
+        for (uint32_t i = 0, k = threadIdx.x; i < kRankSortMax / PT; ++i, k += blockDim.x)
             r[i] = (k < n_pad && key[k] != ~0ull) ? rank[k] : ~0u;
         __syncthreads();
-        for (uint32_t i = 0, k = threadIdx.x; i < kRankSortMax / kPlanThreads; ++i, k += blockDim.x)
+        for (uint32_t i = 0, k = threadIdx.x; i < kRankSortMax / PT; ++i, k += blockDim.x)
             if (r[i] != ~0u) at[r[i]] = k;
     } else {
         for (uint32_t size = 2; size <= n_pad; size <<= 1) {
@@ -479,6 +667,14 @@ __global__ void __launch_bounds__(kPlanThreads, 1) k_plan(Net n, const TileDev* 
     }
 }
 
+// The plan of the launch's step as a kernel of its own (one block).
+__global__ void __launch_bounds__(kPlanThreads, 1) k_plan(Net n, const TileDev* __restrict__ tiles, uint32_t n_tiles,
+                                                          StepPlan sp, uint32_t n_ctas, uint32_t cap, uint32_t items_cap)
+{
+    extern __shared__ __align__(16) unsigned char plan_s[];
+    plan_step<kPlanThreads>(n, n.ctl->t + n.k, tiles, n_tiles, sp, n_ctas, cap, items_cap, plan_s);
+}
+
 // Issues the bulk copy of bytes of shared memory s to global memory g, as a
 // plain copy or an element-wise int32 add into g.  Both addresses 16-byte
 // aligned, bytes a multiple of 16.
@@ -507,10 +703,12 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledCtasPerSm) k_receive_tile
                                                                     const uint32_t* __restrict__ split, uint32_t max_len,
                                                                     uint32_t pdl)
 {
-    extern __shared__ __align__(16) int32_t acc_s[];  // CH * max_len (the current tile uses CH * len)
+    extern __shared__ __align__(16) int32_t acc_s[];  // CH * max_len (the current tile uses CH * len), then the
+                                                      // flat stream's spike records (kFlatRecWords)
     __shared__ TileDev s_T[2];
     __shared__ ItemDev s_I[2];
     __shared__ uint32_t s_ok[2];
+    uint32_t* rec = reinterpret_cast<uint32_t*>(acc_s + CH * max_len);
     const unsigned long long t = n.ctl->t + n.k;
     const uint32_t lane = threadIdx.x & 31u;
     unsigned int* ctr = n.tile_ctr + (t & 1ull);
@@ -544,8 +742,8 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledCtasPerSm) k_receive_tile
     for (uint32_t b = 0; s_ok[b]; b ^= 1u) {
         const ItemDev& I = s_I[b];  // read from shared memory where used
         const TileDev& T = s_T[b];
-        deliver_part<WM, CH>(n, T, qs + T.pbase, T.pbase, split + T.split, acc_s, I.s_beg, I.s_end, pol, ev, bad);
-        if (threadIdx.x == 0) take(atomicAdd(ctr, 1u) + gridDim.x, b ^ 1u);
+        deliver_flat<WM, CH>(n, T, qs + T.pbase, split + T.split, acc_s, rec, I.s_beg, I.s_end, pol, ev, bad,
+                             [&]() { take(atomicAdd(ctr, 1u) + gridDim.x, b ^ 1u); });
         // the tile's pending input for the next update, or this part's share
         // of it: the shared-memory adds are made visible to the copy engine,
         // which reads them out before they are cleared
@@ -741,7 +939,7 @@ inline snn_status tiled_plan(TiledPlan& P, const Net& n, const snn_params* param
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t smem = (size_t)longest * channels * 4;
+    const size_t smem = (size_t)longest * channels * 4 + (dynamic ? (size_t)kFlatRecWords * 4 : 0);
     if (tiles.empty() || smem > (size_t)optin || tiles.size() >= (1u << 24)) return SNN_E_ARG;
     if (dynamic && tiles.size() > kPlanMaxTiles) return SNN_E_ARG;
     if (tiled_set_smem(smem) != cudaSuccess) return SNN_E_CUDA;

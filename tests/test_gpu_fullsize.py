@@ -1,22 +1,72 @@
-"""Parity at the full workload sizes, in the launch configuration bench.py
-times (default receive, 16-bit weights, CUDA-graph steps, re-planned tiles).
+"""Parity at the full workload sizes and run lengths, in the launch
+configuration bench.py times (default receive, 16-bit weights, CUDA-graph
+steps, the fused step where it applies).
 
 The batched sweep of 256 networks is too large for the oracle to run whole,
 but its networks are independent and each one's random draws depend only on
 (seed, instance, neuron, step): sampled networks are re-run alone by the
-oracle and must match bit for bit.  The 1M-neuron Vogels network and the
-100k-neuron Brunel+ network are compared whole over a window of steps.
+oracle, for all 5,000 steps, and must match bit for bit.  The 1M-neuron
+Vogels network (1,000 steps) and the 100k-neuron Brunel+ network (10,000
+steps, raster, potentials and weights at the end) are compared whole.  The
+oracle runs take minutes, so they start together in host processes when the
+module's first test asks for them, while the GPU runs the other tests.
 """
+import concurrent.futures as cf
 import dataclasses
 import functools
+import multiprocessing as mp
+import os
 
 import numpy as np
 import pytest
 
 import oracle
 import snn_inputs as si
+from test_gpu_parity import assert_tuned_fastest
 
 pytestmark = pytest.mark.gpu
+
+SWEEP_STEPS, V1M_STEPS, STDP_STEPS = 5000, 1000, 10000
+
+
+def _sweep_sample(sizes) -> list:
+    """Networks of the sweep re-run alone: the smallest, the largest and
+    random ones (8 in all)."""
+    rng = np.random.default_rng(11)
+    pick = {int(np.argmin(sizes)), int(np.argmax(sizes))}
+    while len(pick) < 8:
+        pick.add(int(rng.integers(0, len(sizes))))
+    return sorted(pick)
+
+
+def _oracle_job(kind: str, arg: int):
+    """One oracle run in a host process (its own graph, built from the seeds)."""
+    import oracle as orc
+    import snn_inputs as sin
+    if kind == "sweep":
+        params = sin.batched_sweep_params(256, 1)
+        p = sin.problem(sin.BRUNEL, [params[arg]], delay=15, n_steps=SWEEP_STEPS, seed=1, threads=1, inst_index0=arg)
+        o = orc.run(p, inst_key0=arg)
+        return {k: o[k] for k in ("steps", "ids", "V", "events")}
+    if kind == "v1m":
+        o = orc.run(sin.vogels_1m(seed=1, n_steps=V1M_STEPS))
+        return {k: o[k] for k in ("steps", "ids", "V", "events")}
+    if kind == "stdp":
+        o = orc.run(sin.brunel_stdp_100k(seed=1, n_steps=STDP_STEPS))
+        return {k: o[k] for k in ("steps", "ids", "V", "w", "events")}
+    raise ValueError(kind)
+
+
+@pytest.fixture(scope="module")
+def oracle_runs():
+    """Futures of every oracle run this module compares with."""
+    sizes = np.array([inst.n for inst in si.batched_sweep_params(256, 1)])
+    jobs = [("stdp", 0), ("v1m", 0)] + [("sweep", b) for b in _sweep_sample(sizes)]
+    ex = cf.ProcessPoolExecutor(max_workers=max(1, min(len(jobs), len(os.sched_getaffinity(0)))),
+                                mp_context=mp.get_context("spawn"))
+    futs = {job: ex.submit(_oracle_job, *job) for job in jobs}
+    yield futs
+    ex.shutdown(wait=True, cancel_futures=True)
 
 
 def _gpu_run(gpu, prob, steps, chunks=(100,), **kw):
@@ -41,19 +91,35 @@ def _sweep():
     return si.batched_sweep(256, base_seed=1, n_steps=0)
 
 
-@pytest.mark.parametrize("model", ["fixed", "generic"])
-def test_batched_sweep_256_sampled_networks(gpu, model):
-    """model: the fixed Brunel kernel, or Brunel from the LIF building block
-    through the generic update (bench.py's generic_update line)."""
+def test_batched_sweep_256_sampled_networks_whole_run(gpu, oracle_runs):
+    """The fixed Brunel kernel (fused step) over the whole 5,000-step run:
+    8 sampled networks re-run alone by the oracle, raster and final V."""
     prob = _sweep()
-    steps = 400  # crosses the first re-plan of the work items (step 256)
-    run = prob if model == "fixed" else dataclasses.replace(prob, model=gpu.MODEL_BRUNEL_LIF)
-    g = _gpu_run(gpu, run, steps, chunks=(100, 200))
-    assert g["info"]["receive"] == "tiled"
+    g = _gpu_run(gpu, prob, SWEEP_STEPS, chunks=(100, 200, 1000))
+    assert_tuned_fastest(g["info"])
     gs, gi = g["steps_ids"]
     sizes = np.array([inst.n for inst in prob.instances])
-    sample = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 37, 200})
-    for b in sample:
+    for b in _sweep_sample(sizes):
+        o = oracle_runs[("sweep", b)].result()
+        lo, hi = int(prob.inst_off[b]), int(prob.inst_off[b + 1])
+        m = (gi >= lo) & (gi < hi)
+        assert len(o["ids"]) > 0
+        assert np.array_equal(gs[m], o["steps"]), b
+        assert np.array_equal(gi[m] - lo, o["ids"]), b
+        assert np.array_equal(g["V"][lo:hi].view(np.uint32), o["V"].view(np.uint32)), b
+
+
+def test_batched_sweep_256_generic_update(gpu):
+    """Brunel from the LIF building block through the generic update (bench.py's
+    generic_update line), 400 steps, sampled networks re-run alone."""
+    prob = _sweep()
+    steps = 400
+    run = dataclasses.replace(prob, model=gpu.MODEL_BRUNEL_LIF)
+    g = _gpu_run(gpu, run, steps, chunks=(100, 200))
+    assert_tuned_fastest(g["info"])
+    gs, gi = g["steps_ids"]
+    sizes = np.array([inst.n for inst in prob.instances])
+    for b in sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 37, 200}):
         sub = si.sub_problem(prob, b, n_steps=steps)
         o = oracle.run(sub, inst_key0=b)
         lo, hi = int(prob.inst_off[b]), int(prob.inst_off[b + 1])
@@ -64,10 +130,16 @@ def test_batched_sweep_256_sampled_networks(gpu, model):
         assert np.array_equal(g["V"][lo:hi].view(np.uint32), o["V"].view(np.uint32)), b
 
 
-def test_vogels_1m_whole_network(gpu):
-    prob = si.vogels_1m(seed=1, n_steps=120)
-    g = _gpu_run(gpu, prob, 120)
-    o = oracle.run(prob)
+def test_vogels_1m_whole_run(gpu, oracle_runs):
+    """Vogels-Abbott 1M neurons, in-degree 1,000, all 1,000 steps, through the
+    global receive with row weights (4 bytes per event)."""
+    prob = si.vogels_1m(seed=1, n_steps=V1M_STEPS)
+    g = _gpu_run(gpu, prob, V1M_STEPS)
+    assert_tuned_fastest(g["info"])
+    if g["info"]["receive"] == "global":
+        assert g["info"]["edge_bytes"] == 4
+    del prob
+    o = oracle_runs[("v1m", 0)].result()
     gs, gi = g["steps_ids"]
     assert len(o["ids"]) > 1000
     assert np.array_equal(gs, o["steps"]) and np.array_equal(gi, o["ids"])
@@ -75,23 +147,21 @@ def test_vogels_1m_whole_network(gpu):
     assert g["counters"]["events"] == o["events"]
 
 
-@functools.lru_cache(maxsize=1)
-def _stdp_100k():
-    prob = si.brunel_stdp_100k(seed=1, n_steps=300)
-    return prob, oracle.run(prob)
-
-
 @pytest.mark.parametrize("lazy", [False, True])
-def test_brunel_stdp_100k_whole_network(gpu, lazy):
-    """Eager Update Synapses, and the lazy form bench.py times (128-step history)."""
-    prob, o = _stdp_100k()
-    g = _gpu_run(gpu, prob, 300, lazy=lazy)
+def test_brunel_stdp_100k_whole_run(gpu, oracle_runs, lazy):
+    """Brunel+ 100k, all 10,000 steps: eager Update Synapses, and the lazy form
+    bench.py times (128-step history); raster, final V and weights."""
+    prob = si.brunel_stdp_100k(seed=1, n_steps=STDP_STEPS)
+    g = _gpu_run(gpu, prob, STDP_STEPS, chunks=(100, 2000), lazy=lazy)
+    assert_tuned_fastest(g["info"])
+    o = oracle_runs[("stdp", 0)].result()
     gs, gi = g["steps_ids"]
     assert len(o["ids"]) > 1000
     assert np.array_equal(gs, o["steps"]) and np.array_equal(gi, o["ids"])
     assert np.array_equal(g["V"].view(np.uint32), o["V"].view(np.uint32))
     assert np.array_equal(g["w"], o["w"])
     assert not np.array_equal(o["w"], prob.w)
+    assert g["counters"]["events"] == o["events"]
 
 
 def test_sweep_adjacency_construction_sampled_jobs(gpu):

@@ -13,7 +13,9 @@ import snn_inputs as si
 
 pytestmark = pytest.mark.gpu
 
-RECV = {"global": 1, "tiled": 2, "bulk": 3}
+RECV = {"global": 1, "tiled": 2, "bulk": 3, "tiled_serial": 2}
+# "tiled_serial": the tiled receive as its own kernel after the update even
+# where the library would run both in one kernel per step (SNN_F_SERIAL)
 
 
 def _fields(prob):
@@ -32,7 +34,11 @@ def run_gpu(snn, prob, n_steps=None, *, w16=True, receive="global", overrides=()
     n_steps = prob.n_steps if n_steps is None else n_steps
     total = prob.n * max(n_steps, 1)
     cap = total + 4096 if total < 10_000_000 else total // 10 + 4096
-    net = snn.Network(prob, w16=w16, receive=RECV[receive], log_capacity=cap, packed=packed)
+    net = snn.Network(prob, w16=w16, receive=RECV[receive], log_capacity=cap, packed=packed,
+                      serial=receive == "tiled_serial")
+    fused_expected = (receive == "tiled" and w16 and prob.model == si.BRUNEL and not prob.stdp
+                      and prob.delay >= 3)
+    assert net.info()["fused"] == fused_expected
     try:
         if state:
             for k, v in state.items():
@@ -92,7 +98,7 @@ def test_vogels_4k_full(gpu, w16, receive):
     assert_parity(g, o, prob)
 
 
-@pytest.mark.parametrize("receive", ["global", "tiled", "bulk"])
+@pytest.mark.parametrize("receive", ["global", "tiled", "bulk", "tiled_serial"])
 def test_brunel_12k5_full(gpu, receive):
     """Brunel, 12,500 neurons, C_E 1,000 / C_I 250, 15-step delay, 10,000 steps."""
     prob = si.brunel_12k5(seed=1, n_steps=10000)
@@ -114,7 +120,7 @@ def test_brunel_stdp_small(gpu, w16, receive):
     assert_parity(g, o, prob)
 
 
-@pytest.mark.parametrize("receive", ["global", "tiled", "bulk"])
+@pytest.mark.parametrize("receive", ["global", "tiled", "bulk", "tiled_serial"])
 def test_batched_uneven_parity(gpu, receive):
     """A batch of uneven Brunel networks in one context equals the oracle
     on the whole batch."""
@@ -156,7 +162,7 @@ def test_forced_spike_arrives_after_d_steps(gpu, d, model):
     prob = si.from_edges(model, inst, edges, w, delay=d, n_steps=40)
     ov = [(7, 0, 1000.0), (9, 250, 1000.0)]
     o = oracle.run(prob, overrides=ov)
-    for receive in ("global", "tiled", "bulk"):
+    for receive in ("global", "tiled", "bulk", "tiled_serial"):
         g = run_gpu(gpu, prob, overrides=ov, receive=receive)
         assert_parity(g, o, prob)
 
@@ -170,7 +176,7 @@ def test_largest_delay(gpu):
     prob.delay = 1000
     o = oracle.run(prob)
     assert int((o["steps"] >= 1000).sum()) > 100  # spikes after the first deliveries
-    for receive in ("global", "tiled", "bulk"):
+    for receive in ("global", "tiled", "bulk", "tiled_serial"):
         assert_parity(run_gpu(gpu, prob, receive=receive), o, prob)
 
 
@@ -190,7 +196,7 @@ def test_relay_network(gpu, d):
               "r": np.zeros(200, np.int32), "x": np.zeros(200, np.float32), "y": np.zeros(200, np.float32),
               "acc0": acc0, "acc1": np.zeros(200, np.int32), "w": prob.w.copy()}
     o = oracle.run(prob, state=ostate)
-    for receive in ("tiled", "bulk"):
+    for receive in ("tiled", "bulk", "tiled_serial"):
         g = run_gpu(gpu, prob, state=state, receive=receive)
         assert_parity(g, o, prob)
     assert len(o["ids"]) > 500
@@ -342,11 +348,12 @@ def test_retuned_tiles_keep_parity(gpu, tune_steps, receive):
 
 
 @pytest.mark.parametrize("packed", [True, False])
-@pytest.mark.parametrize("n_inst,delay", [(1, 1), (2, 2), (3, 1), (33, 2), (1100, 2)])
+@pytest.mark.parametrize("n_inst,delay", [(1, 1), (2, 2), (3, 1), (33, 2), (1100, 2), (1, 3), (33, 3), (1100, 5)])
 def test_per_step_plan_tile_counts(gpu, n_inst, delay, packed):
     """The tiled receive's per-step plan over 1 to 1,100 tiles (its rank sort
     up to 1,024 tiles, its sorting network above), with the plan beside the
-    update (delay 2) and before the receive (delay 1)."""
+    update (delay 2), before the receive (delay 1), and made one step ahead
+    inside the fused step kernel (delays 3 and 5)."""
     insts = [si.brunel_instance(200 + 37 * (b % 7), k=20 + (b % 5), nu_ratio=3.0, graph_seed=b + 1)
              for b in range(n_inst)]
     prob = si.problem(si.BRUNEL, insts, delay=delay, n_steps=80, seed=7)
@@ -379,18 +386,38 @@ def test_instances_larger_than_one_tile(gpu, model, receive):
     assert_parity(g, o, prob)
 
 
-@pytest.mark.parametrize("name,expect", [("vogels_4k", "global"), ("brunel_12k5", "global"),
-                                         ("brunel_stdp_100k", "global")])
-def test_automatic_receive_choice(gpu, name, expect):
-    """SNN_RECV_AUTO takes the tiled receive for graphs of 200M+ synapses whose
-    rows reach each tile with 400+ edges (the sweep: tests/test_gpu_fullsize),
-    else the global-atomic one."""
-    prob = getattr(si, name)(seed=1, n_steps=0)
-    net = gpu.Network(prob, receive=0, log_capacity=1 << 16)
+def form_of(info) -> str:
+    """The receive form a context runs, in snn_info.tune_ms's names."""
+    return "fused" if info["fused"] else info["receive"]
+
+
+def assert_tuned_fastest(info):
+    """SNN_RECV_AUTO kept the form its timing run measured fastest."""
+    assert info["tuned"]
+    ms = {k: v for k, v in info["tune_ms"].items() if v > 0}
+    assert len(ms) >= 1 and form_of(info) in ms
+    assert form_of(info) == min(ms, key=ms.get), (form_of(info), ms)
+
+
+@pytest.mark.parametrize("name,n_steps", [("vogels_4k", 1000), ("brunel_12k5", 2000), ("brunel_stdp_100k", 300)])
+def test_tuned_receive_is_the_measured_fastest(gpu, name, n_steps):
+    """SNN_RECV_AUTO times every form that applies on the graph itself and
+    keeps the fastest (snn_info.tune_ms); the run that follows starts from
+    N_0 and equals the oracle's (the tuning steps leave no trace)."""
+    prob = getattr(si, name)(seed=1, n_steps=n_steps)
+    net = gpu.Network(prob, receive=0, log_capacity=prob.n * n_steps + 4096)
     try:
-        assert net.info()["receive"] == expect
+        info = net.info()
+        assert_tuned_fastest(info)
+        # the generator sorts rows: both the global and the tiled form were timed
+        assert info["tune_ms"]["tiled"] > 0 and info["tune_ms"]["global"] > 0
+        net.step(n_steps)
+        g = {f: net.read(f) for f in _fields(prob)}
+        g["steps"], g["ids"] = net.spikes()
+        g["counters"] = net.counters()
     finally:
         net.close()
+    assert_parity(g, oracle_run(("tuned", name, n_steps), prob), prob)
 
 
 def test_bulk_wait_bound_reports_timeout(gpu):
@@ -419,3 +446,49 @@ def test_bulk_wait_bound_reports_timeout(gpu):
     out = run_gpu(gpu, prob, receive="bulk")
     assert np.array_equal(out["steps"], ref["steps"]) and np.array_equal(out["ids"], ref["ids"])
     assert len(ref["ids"]) > 0
+
+
+def test_row_weight_layout(gpu):
+    """Rows that carry one weight each (the source population's: Vogels and
+    Brunel, Section III-A-2 and Table 2) let the global receive read the
+    4-byte targets alone; SNN_F_UNPACKED keeps the per-edge codes (6 bytes).
+    Writing weights that differ inside a row switches the receive back to the
+    per-edge codes, and the run still equals the oracle's on those weights."""
+    prob = si.vogels_4k(seed=2, n_steps=400)
+    o = oracle_run("v4k_s2", prob)
+    for packed, eb in ((True, 4), (False, 6)):
+        net = gpu.Network(prob, receive=RECV["global"], log_capacity=prob.n * 400, packed=packed)
+        try:
+            assert net.info()["edge_bytes"] == eb
+            net.step(prob.n_steps)
+            g = {f: net.read(f) for f in _fields(prob)}
+            g["steps"], g["ids"] = net.spikes()
+            g["counters"] = net.counters()
+        finally:
+            net.close()
+        assert_parity(g, o, prob)
+    # 200 excitatory rows get a second weight value in their first edge
+    # (same shift: 2^2 x 32767, 2.0 mV against 1.62 mV)
+    w2 = prob.w.copy()
+    for j in range(200):
+        a = int(prob.row_off[j])
+        assert int(prob.row_off[j + 1]) - a >= 2 and w2[a] == 106168
+        w2[a] = 131068
+    prob2 = si.Problem(model=prob.model, instances=prob.instances, delay=prob.delay, seed=prob.seed,
+                       n_steps=prob.n_steps, stdp=False, inst_off=prob.inst_off, row_off=prob.row_off,
+                       tgt=prob.tgt, w=w2)
+    o2 = oracle.run(prob2)
+    net = gpu.Network(prob, receive=RECV["global"], log_capacity=prob.n * 400)
+    try:
+        assert net.info()["edge_bytes"] == 4
+        net.write("w", w2)
+        assert net.info()["edge_bytes"] == 6
+        net.step(prob.n_steps)
+        g = {f: net.read(f) for f in _fields(prob)}
+        g["steps"], g["ids"] = net.spikes()
+        g["counters"] = net.counters()
+        assert np.array_equal(net.read("w"), w2)
+    finally:
+        net.close()
+    assert_parity(g, o2, prob2)
+    assert not np.array_equal(o2["ids"], o["ids"])  # the changed weight matters
