@@ -82,6 +82,8 @@ struct snn_ctx {
     bool use_bulk = false;             // tiled plan, bulk-copy kernel
     bool packed = false;               // the tiled receive reads pk32
     uint32_t* pk32 = nullptr;          // packed edges: (target - instance base) << 16 | int16 code
+    uint16_t* pk16 = nullptr;          // 16-bit target offsets (rows with one weight each)
+    bool off16 = false;                // the tiled receive reads pk16 and the row weights
     uint32_t tune_count = 0;           // re-plans done (at most 2)
     uint64_t tune_next = 0;            // step of the next re-plan
     std::vector<unsigned long long> spk_seen;  // instance spike counts at the last re-plan
@@ -91,7 +93,7 @@ struct snn_ctx {
     // receive form in use (RecvForm) and, with SNN_RECV_AUTO, the ms per step
     // each form took in the tuning run (0: not a candidate)
     int form = 0;
-    bool tiled_fits = false;           // within the flat stream's 32-bit vector index and 24-bit length
+    bool tiled_fits = false;           // every row's length fits its 32-bit row record
     float tune_ms[4] = {0.f, 0.f, 0.f, 0.f};
     bool tuned = false;
     // fused step (snn_fused.cuh): update and receive of a step in one kernel
@@ -253,6 +255,12 @@ void launch_update(const Net& n, bool stats, int npt, uint32_t Np, cudaStream_t 
 // holds kPhases + 1 events recorded between the phases.
 constexpr int kPhases = 6;
 
+// The edge layout the tiled receive reads.
+int recv_wm(const snn_ctx* c)
+{
+    return c->off16 ? kWOff16 : (c->packed ? kWPacked : (c->w16 ? kW16 : kWF32));
+}
+
 FusedDev fused_args(const snn_ctx* c)
 {
     FusedDev F{};
@@ -277,7 +285,12 @@ cudaError_t launch_fused(const snn_ctx* c, const Net& n, cudaStream_t s)
 {
     const FusedDev F = fused_args(c);
     const dim3 grid(c->fused_grid), block(kTiledThreads);
-    if (c->packed) {
+    if (c->off16) {
+        if (c->stats)
+            k_step_fused<kWOff16, true><<<grid, block, c->fused_smem, s>>>(n, F);
+        else
+            k_step_fused<kWOff16, false><<<grid, block, c->fused_smem, s>>>(n, F);
+    } else if (c->packed) {
         if (c->stats)
             k_step_fused<kWPacked, true><<<grid, block, c->fused_smem, s>>>(n, F);
         else
@@ -365,7 +378,7 @@ snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr, u
             CUDA_TRY(c, enqueue_tiled_plan(c->tiled, n, s));
         // with the plan beside the update and no plasticity in between, the
         // receive follows the update as its programmatic dependent
-        CUDA_TRY(c, enqueue_tiled_receive(c->tiled, n, c->packed ? kWPacked : (c->w16 ? kW16 : kWF32), s,
+        CUDA_TRY(c, enqueue_tiled_receive(c->tiled, n, recv_wm(c), s,
                                           fork && !c->stdp && !ev));
         if (mid) cudaEventRecord(mid, s);  // no merge: the parts add into the accumulators
     } else {
@@ -531,6 +544,18 @@ snn_status refresh_row_weights(snn_ctx* c, bool* changed)
     return SNN_OK;
 }
 
+// 16-bit target offsets apply where packed edges do and every row carries
+// one weight (the row weights are in use).
+bool off16able(const snn_ctx* c) { return packable(c) && c->net.roww != nullptr; }
+
+snn_status pack_off16(snn_ctx* c)
+{
+    if (!c->off16) return SNN_OK;
+    k_pack_off16<<<(uint32_t)sm_count() * 16, 256, 0, c->stream>>>(c->net, c->Np, c->pk16);
+    CUDA_TRY(c, cudaGetLastError());
+    return SNN_OK;
+}
+
 snn_status pack_edges(snn_ctx* c)
 {
     if (!c->packed) return SNN_OK;
@@ -650,7 +675,7 @@ snn_status plan_tiles(snn_ctx* c, const double* work)
     const uint32_t ch = c->vogels ? 2u : 1u;
     const uint32_t bulk_len = (uint32_t)((227u * 1024u - 1024u - kBulkSlots * bulk_slot_bytes(c->w16)) / 4u / 256u * 256u);
     const uint32_t max_len = (c->use_bulk ? bulk_len : kTiledMaxWords) / ch / 256u * 256u;
-    const int wm = packable(c) ? kWPacked : (c->w16 ? kW16 : kWF32);
+    const int wm = off16able(c) ? kWOff16 : (packable(c) ? kWPacked : (c->w16 ? kW16 : kWF32));
     snn_status st = tiled_plan(c->tiled, c->net, c->params.data(), c->pbase.data(), c->cfg.n_inst, (int)ch, max_len,
                                work, c->inst_edges.data(), sm_count(), [c](size_t b) { return dev_alloc(c, b); },
                                [c](void* p) { dev_free(c, p); }, c->stream, !c->use_bulk, 128u * vec_of(wm));
@@ -721,10 +746,11 @@ snn_status setup_fused(snn_ctx* c)
     if (!fused_applies(c)) return SNN_OK;
     uint32_t n_pad = 1;
     while (n_pad < c->tiled.n_tiles) n_pad <<= 1;
-    const size_t smem = std::max<size_t>((size_t)c->tiled.max_len * 4 + (size_t)kFlatRecWords * 4, plan_smem(n_pad));
+    const size_t smem = std::max<size_t>((size_t)c->tiled.max_len * 4, plan_smem(n_pad));
     auto set = [&](auto kernel) { return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); };
     if (set(k_step_fused<kWPacked, false>) != cudaSuccess || set(k_step_fused<kWPacked, true>) != cudaSuccess ||
-        set(k_step_fused<kW16, false>) != cudaSuccess || set(k_step_fused<kW16, true>) != cudaSuccess) {
+        set(k_step_fused<kW16, false>) != cudaSuccess || set(k_step_fused<kW16, true>) != cudaSuccess ||
+        set(k_step_fused<kWOff16, false>) != cudaSuccess || set(k_step_fused<kWOff16, true>) != cudaSuccess) {
         cudaGetLastError();
         return SNN_OK;  // keep the separate kernels
     }
@@ -768,7 +794,14 @@ snn_status use_form(snn_ctx* c, int form)
     snn_status st = SNN_OK;
     if (c->use_tiled) {
         st = (c->rows_sorted && c->tiled_fits) ? plan_tiles(c, nullptr) : SNN_E_ARG;
-        if (st == SNN_OK && packable(c) && !c->pk32) {
+        if (st == SNN_OK && off16able(c) && !c->pk16) {  // targets only: 2 bytes per edge
+            c->pk16 = alloc_n<uint16_t>(c, c->E + 32);
+            if (!c->pk16) return fail(c, SNN_E_NOMEM, "16-bit edge offsets");
+            CUDA_TRY(c, cudaMemsetAsync(c->pk16, 0, (c->E + 32) * 2, c->stream));
+            c->off16 = true;
+            c->net.pk16 = c->pk16;
+            st = pack_off16(c);
+        } else if (st == SNN_OK && !off16able(c) && packable(c) && !c->pk32) {
             c->pk32 = alloc_n<uint32_t>(c, c->E + 16);
             if (!c->pk32) return fail(c, SNN_E_NOMEM, "packed edges");
             CUDA_TRY(c, cudaMemsetAsync(c->pk32, 0, (c->E + 16) * 4, c->stream));
@@ -785,7 +818,13 @@ snn_status use_form(snn_ctx* c, int form)
         tiled_free(c->tiled, [c](void* p) { dev_free(c, p); });
         c->use_tiled = c->use_bulk = c->fused = false;
     }
-    c->packed = c->use_tiled && c->pk32 && packable(c);
+    c->off16 = c->use_tiled && c->pk16 && off16able(c);
+    if (!c->off16 && c->pk16) {
+        dev_free(c, c->pk16);
+        c->pk16 = nullptr;
+    }
+    c->net.pk16 = c->off16 ? c->pk16 : nullptr;
+    c->packed = c->use_tiled && !c->off16 && c->pk32 && packable(c);
     if (!c->packed && c->pk32) {
         dev_free(c, c->pk32);
         c->pk32 = nullptr;
@@ -859,7 +898,14 @@ snn_status tune_receive(snn_ctx* c)
         if (st == SNN_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) st = fail(c, SNN_E_CUDA, "event record");
         if (st == SNN_OK) st = launch(kTuneSteps);
         if (st == SNN_OK && cudaEventRecord(e1, c->stream) != cudaSuccess) st = fail(c, SNN_E_CUDA, "event record");
-        if (st == SNN_OK) st = check_device_errors(c);
+        if (st == SNN_OK) {  // a log too small for the tuning steps is no error here: the log starts over
+            unsigned int err = 0;
+            if (cudaMemcpyAsync(&err, &c->ctl->err, sizeof err, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+                cudaStreamSynchronize(c->stream) != cudaSuccess)
+                st = fail(c, SNN_E_CUDA, "tuning run");
+            else if (err & ~kErrLogOverflow)
+                st = check_device_errors(c);
+        }
         float ms = 0.f;
         if (st == SNN_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = fail(c, SNN_E_CUDA, "event time");
         if (st == SNN_OK) {
@@ -1108,6 +1154,10 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
     c->pk32 = nullptr;
     c->packed = false;
     c->net.pk = nullptr;
+    dev_free(c, c->pk16);
+    c->pk16 = nullptr;
+    c->off16 = false;
+    c->net.pk16 = nullptr;
     c->roff = nullptr; c->tgt = nullptr; c->w16p = nullptr; c->w32p = nullptr; c->meta = nullptr;
     c->coff = nullptr; c->cedge = nullptr; c->cpre = nullptr; c->w_init = nullptr;
     c->graph_loaded = false;
@@ -1275,11 +1325,10 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
     c->tune_next = c->cfg.tune_steps ? c->cfg.tune_steps : 256;
     c->spk_seen.assign(c->cfg.n_inst, 0);
     {
-        // the flat stream holds a segment's first 16-byte vector in 32 bits and
-        // its length in 24
+        // row records hold a row's length in 32 bits
         uint64_t max_deg = 0;
         for (uint32_t j = 0; j < N; ++j) max_deg = std::max<uint64_t>(max_deg, row_off[j + 1] - row_off[j]);
-        c->tiled_fits = E < (1ull << 34) && max_deg < (1ull << 24);
+        c->tiled_fits = max_deg < (1ull << 32);
     }
     c->k_steps = c->cfg.steps_per_graph ? c->cfg.steps_per_graph : 16;
     c->tuned = false;
@@ -1592,11 +1641,7 @@ snn_status snn_write_state(snn_ctx* c, snn_field f, const void* host)
         if (st == SNN_OK) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
         bool changed = false;
         if (st == SNN_OK) st = refresh_row_weights(c, &changed);
-        if (st == SNN_OK && changed) {  // the receive reads another layout now
-            drop_graphs(c);
-            st = capture(c, 1, &c->g1);
-            if (st == SNN_OK && c->k_steps > 1) st = capture(c, c->k_steps, &c->gk);
-        }
+        if (st == SNN_OK && changed) st = use_form(c, c->form);  // the receive reads another layout now
         return st;
     }
     void* p;
@@ -1684,8 +1729,7 @@ snn_status snn_get_info(snn_ctx* c, snn_info* info)
     info->rows_sorted = c->rows_sorted ? 1 : 0;
     info->edges = c->E;
     info->device_bytes = c->bytes_held;
-    info->edge_bytes = c->use_tiled ? edge_bytes_of(c->packed ? kWPacked : (c->w16 ? kW16 : kWF32))
-                                    : (c->net.roww ? 4u : (c->w16 ? 6u : 8u));
+    info->edge_bytes = c->use_tiled ? edge_bytes_of(recv_wm(c)) : (c->net.roww ? 4u : (c->w16 ? 6u : 8u));
     info->model_state_bytes = (uint32_t)c->mbytes;
     info->fused = c->fused ? 1u : 0u;
     info->tuned = c->tuned ? 1u : 0u;

@@ -107,6 +107,7 @@ struct Net {
     const uint4* rinfo;     // per padded row: start (lo, hi), length, meta -- one load per spike
     const int32_t* roww;    // row weights (lattice units) when every row carries one (null otherwise)
     const uint32_t* pk;     // packed edges for the tiled receive (null when not used)
+    const uint16_t* pk16;   // 16-bit target offsets for the tiled receive with row weights (null when not used)
     const uint64_t* coff;   // STDP: plastic in-edges per padded post id
     const uint32_t* cedge;  // STDP: edge index of each plastic in-edge
     const uint32_t* cpre;   // STDP: padded presynaptic id of each plastic in-edge

@@ -102,7 +102,7 @@ __device__ __forceinline__ void fused_unit(const FusedDev& F, uint32_t n_items, 
 template <int WM, bool STATS>
 __global__ void __launch_bounds__(kTiledThreads, kTiledCtasPerSm) k_step_fused(Net n, FusedDev F)
 {
-    extern __shared__ __align__(16) int32_t acc_s[];  // max(max_len words + the flat stream's records, the plan's bytes)
+    extern __shared__ __align__(16) int32_t acc_s[];  // max(max_len words, the plan's bytes)
     __shared__ TileDev s_T[2];
     __shared__ ItemDev s_I[2];
     __shared__ uint32_t s_kind[2], s_idx[2];
@@ -152,9 +152,9 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledCtasPerSm) k_step_fused(N
             const ItemDev& I = s_I[b];
             const TileDev& T = s_T[b];
             const unsigned long long ts = t + 1 - n.d;  // a receive item exists only when t + 1 >= d
-            deliver_flat<WM, 1>(n, T, n.q + (size_t)(ts % n.D) * n.Np + T.pbase, F.split + T.split, acc_s,
-                                reinterpret_cast<uint32_t*>(acc_s + F.max_len), I.s_beg, I.s_end, pol, ev, bad,
-                                [&]() { take(atomicAdd(n.tile_ctr + (t & 1ull), 1u) + gridDim.x, b ^ 1u); });
+            deliver_pipe<WM, 1>(n, T, n.q + (size_t)(ts % n.D) * n.Np + T.pbase, T.pbase, F.split + T.split, acc_s,
+                                I.s_beg, I.s_end, pol, ev, bad);
+            if (tid == 0) take(atomicAdd(n.tile_ctr + (t & 1ull), 1u) + gridDim.x, b ^ 1u);
             // the tile's input for the next update, or this part's share of
             // it: the shared-memory adds are made visible to the copy engine,
             // which reads them out before they are cleared

@@ -104,8 +104,7 @@ struct TiledPlan {
 // the SM's loads in flight.
 constexpr int kTiledThreads = 512;
 constexpr int kTiledCtasPerSm = 2;
-constexpr uint32_t kTiledMaxWords = 25600;  // int32 accumulators of one CTA (100 KB; with the flat stream's
-                                            // 12 KB of spike records two CTAs fill an SM's shared memory)
+constexpr uint32_t kTiledMaxWords = 28672;  // int32 accumulators of one CTA (112 KB)
 constexpr int kVec = 4;            // 4-edge vectors in flight per lane
 constexpr uint32_t kMaxParts = 255;
 constexpr uint32_t kMergeChunk = 4096;
@@ -160,360 +159,202 @@ __device__ __forceinline__ uint16_t ld_edge16(const int16_t* ptr, unsigned long 
 // Edge layouts the receive reads: binary32 weights and u32 targets, int16
 // weight codes and u32 targets, or one u32 per edge holding the target's
 // offset in its instance (high half) and the int16 code (low half).
-enum : int { kWF32 = 0, kW16 = 1, kWPacked = 2 };
-__host__ __device__ constexpr int vec_of(int wm) { return wm == kWPacked ? 6 : kVec; }
-__host__ __device__ constexpr uint32_t edge_bytes_of(int wm) { return wm == kWF32 ? 8u : (wm == kW16 ? 6u : 4u); }
-
-// Adds the edges [sb, se) of one row into the tile's accumulators a (one
-// warp, all lanes).  x0 maps a stored target to its accumulator: padded id -
-// x0 (u32 targets: x0 = the tile's first id) or instance offset - x0 (packed:
-// x0 = the tile's first id - the instance's).  Edges [a4, b4) are read 4 per
-// 16-byte load (targets or packed edges; 8- or 16-byte weight loads beside
-// them), vec_of(WM) loads in flight per lane; the unaligned head and tail,
-// one edge per lane, are loaded with the first vectors so that they cost no
-// round trip of their own.
-template <int WM>
-__device__ __forceinline__ void add_segment(const Net& n, int32_t* a, uint64_t sb, uint64_t se, uint32_t shift,
-                                            uint32_t x0, uint32_t len, uint32_t lane, unsigned long long pol,
-                                            bool& bad)
+// kWOff16: every row carries one weight (the source population's, Table 2),
+// held per row, and an edge is its target's 16-bit offset in its instance
+// alone: 8 edges per 16-byte vector.
+enum : int { kWF32 = 0, kW16 = 1, kWPacked = 2, kWOff16 = 3 };
+__host__ __device__ constexpr int vec_of(int wm) { return wm == kWPacked ? 6 : (wm == kWOff16 ? 4 : kVec); }
+__host__ __device__ constexpr uint32_t edge_bytes_of(int wm)
 {
-    constexpr int V = vec_of(WM);
-    const uint64_t up4 = (sb + 3) & ~3ull, dn4 = se & ~3ull;
-    const uint64_t a4 = up4 < se ? up4 : se;
-    const uint64_t b4 = dn4 > a4 ? dn4 : a4;
-    uint32_t hx = 0;
-    int32_t hw = 0;
-    bool head = false;
-    {
-        uint64_t e = ~0ull;
-        if (lane < a4 - sb)
-            e = sb + lane;
-        else if (lane >= 4 && lane - 4 < se - b4)
-            e = b4 + (lane - 4);
-        if (e != ~0ull) {
-            if constexpr (WM == kWPacked) {
-                const uint32_t v = ld_edge(n.pk + e, pol);
-                hx = (v >> 16) - x0;
-                hw = (int32_t)(int16_t)(v & 0xffffu) << shift;
-            } else if constexpr (WM == kW16) {
-                hx = ld_edge(n.tgt + e, pol) - x0;
-                hw = (int32_t)(int16_t)ld_edge16(n.w16 + e, pol) << shift;
-            } else {
-                hx = ld_edge(n.tgt + e, pol) - x0;
-                hw = __float2int_rz(__uint_as_float(ld_edge(reinterpret_cast<const uint32_t*>(n.w32 + e), pol)));
-            }
-            head = true;
-        }
-    }
-    for (uint64_t base = a4; base < b4; base += 128 * V) {
-        uint4 tv[V];
-        uint4 wr[WM == kWPacked ? 1 : V];  // raw weights: 4 x int16 in .x/.y, or 4 x binary32
-#pragma unroll
-        for (int u = 0; u < V; ++u) {
-            const uint64_t e = base + 128 * u + 4 * lane;
-            tv[u] = make_uint4(0, 0, 0, 0);
-            if constexpr (WM != kWPacked) wr[u] = make_uint4(0, 0, 0, 0);
-            if (e < b4) {
-                if constexpr (WM == kWPacked) {
-                    tv[u] = ld_edges4(n.pk + e, pol);
-                } else {
-                    tv[u] = ld_edges4(n.tgt + e, pol);
-                    if constexpr (WM == kW16) {
-                        const uint2 h = ld_edges2(n.w16 + e, pol);
-                        wr[u].x = h.x;
-                        wr[u].y = h.y;
-                    } else {
-                        wr[u] = ld_edges4(n.w32 + e, pol);
-                    }
-                }
-            }
-        }
-        if (head) {
-            if (hx < len)
-                atomicAdd(a + hx, hw);
-            else
-                bad = true;
-            head = false;
-        }
-#pragma unroll
-        for (int u = 0; u < V; ++u) {
-            if (base + 128 * u + 4 * lane >= b4) continue;
-            uint32_t xs[4];
-            int32_t wv[4];
-            if constexpr (WM == kWPacked) {
-                const uint32_t v[4] = {tv[u].x, tv[u].y, tv[u].z, tv[u].w};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    xs[k] = (v[k] >> 16) - x0;
-                    wv[k] = (int32_t)(int16_t)(v[k] & 0xffffu) << shift;
-                }
-            } else {
-                xs[0] = tv[u].x - x0;
-                xs[1] = tv[u].y - x0;
-                xs[2] = tv[u].z - x0;
-                xs[3] = tv[u].w - x0;
-                if constexpr (WM == kW16) {
-                    wv[0] = (int32_t)(int16_t)(wr[u].x & 0xffffu) << shift;
-                    wv[1] = (int32_t)(int16_t)(wr[u].x >> 16) << shift;
-                    wv[2] = (int32_t)(int16_t)(wr[u].y & 0xffffu) << shift;
-                    wv[3] = (int32_t)(int16_t)(wr[u].y >> 16) << shift;
-                } else {
-                    wv[0] = __float2int_rz(__uint_as_float(wr[u].x));
-                    wv[1] = __float2int_rz(__uint_as_float(wr[u].y));
-                    wv[2] = __float2int_rz(__uint_as_float(wr[u].z));
-                    wv[3] = __float2int_rz(__uint_as_float(wr[u].w));
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (xs[k] < len)
-                    atomicAdd(a + xs[k], wv[k]);
-                else
-                    bad = true;
-            }
-        }
-    }
-    if (head) {  // a row with no whole vector
-        if (hx < len)
-            atomicAdd(a + hx, hw);
-        else
-            bad = true;
-    }
+    return wm == kWF32 ? 8u : (wm == kW16 ? 6u : (wm == kWPacked ? 4u : 2u));
 }
 
-// Delivers the spikes [s_beg, s_end) of the instance's queue q (local ids
-// from pbase) to tile T.  The work is cut into units, piece u % K of the row
-// segment of spike s_beg + u / K (K = 2^T.lpieces), strided over the warps;
-// the row record (and split offsets) of a warp's next unit and the spike of
-// the unit after it are fetched while the current unit is delivered, so no
-// load waits on another.
+// ---------------------------------------------------------------------------
+// Pipelined delivery of the spikes [s_beg, s_end) of the instance's queue q
+// (local ids from pbase) to tile T.  The work is cut into units, piece
+// u % K of the row segment of spike s_beg + u / K (K = 2^T.lpieces; the
+// segment of a row inside the tile comes from the split table), strided
+// over the warps.  A warp's units are walked as a stream of rounds -- up to PV 16-byte vectors per lane of one unit, plus
+// its unaligned head and tail edges in its first round -- and the edge loads
+// of the next round (of the same unit or the next one) are issued before the
+// shared-memory atomics of the current round, so the load latency of one
+// round runs under the atomics of the other and consecutive units follow
+// each other without a gap.  The record of the next unit and the spike of
+// the one after are loaded when a unit's first round is formed.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int pipe_vec_of(int wm) { return wm == kWPacked ? 3 : (wm == kWOff16 ? 2 : (wm == kW16 ? 2 : 1)); }
+__host__ __device__ constexpr uint32_t pipe_epv_of(int wm) { return wm == kWOff16 ? 8u : 4u; }  // edges per vector
+
+template <int WM>
+struct PipeRound {
+    static constexpr int PV = pipe_vec_of(WM);
+    uint4 tv[PV];                              // targets, or packed edges
+    uint2 wh[WM == kW16 ? PV : 1];             // int16 codes
+    uint4 wf[WM == kWF32 ? PV : 1];            // binary32 weights
+    uint32_t nv;                               // vectors of this lane in the round
+    uint32_t sc;                               // shift | channel << 5 | head edge present << 6
+    uint32_t hx, hw;                           // head / tail edge: raw target (or packed edge), raw weight
+    int32_t rw;                                // kWOff16: the row's weight
+};
+
 template <int WM, int CH>
-__device__ __forceinline__ void deliver_part(const Net& n, const TileDev& T, const uint32_t* q, uint32_t pbase,
+__device__ __forceinline__ void deliver_pipe(const Net& n, const TileDev& T, const uint32_t* q, uint32_t pbase,
                                              const uint32_t* sp, int32_t* acc_s, uint32_t s_beg, uint32_t s_end,
                                              unsigned long long pol, unsigned long long& ev, bool& bad)
 {
+    constexpr int PV = pipe_vec_of(WM);
+    constexpr uint32_t EPV = pipe_epv_of(WM), RB = 32u * EPV;  // edges per vector, per warp vector row
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const uint32_t nsplit = T.ntiles - 1, lk = T.lpieces;
     const uint32_t u_end = (s_end - s_beg) << lk;
-    // segment of the row of spike j inside the tile, relative to the row's start
-    auto fetch = [&](uint32_t j, uint4& r, uint32_t& ylo, uint32_t& yhi) {
+    const uint32_t x0 = (WM == kWPacked || WM == kWOff16) ? T.lo - T.pbase : T.lo, tlen = T.len, tau = T.tau;
+    // the next unit to form: u, its record (r, ylo, yhi, its weight rwn); the spike of unit u + nwarps: jn
+    uint32_t u = warp, jn = 0, ylo = 0, yhi = 0;
+    int32_t rwn = 0;
+    uint4 r = make_uint4(0, 0, 0, 0);
+    auto fetch = [&](uint32_t j) {
         r = __ldg(n.rinfo + j);
+        if constexpr (WM == kWOff16) rwn = __ldg(n.roww + j);
         ylo = 0;
-        yhi = 0xffffffffu;  // the row's end
+        yhi = 0xffffffffu;
         if (nsplit) {
             const uint32_t* sj = sp + (size_t)(j - pbase) * nsplit;
-            if (T.tau > 0) ylo = __ldg(sj + T.tau - 1);
-            if (T.tau < nsplit) yhi = __ldg(sj + T.tau);
+            if (tau > 0) ylo = __ldg(sj + tau - 1);
+            if (tau < nsplit) yhi = __ldg(sj + tau);
         }
     };
-    uint32_t u = warp;
-    uint4 r0 = make_uint4(0, 0, 0, 0);
-    uint32_t ylo0 = 0, yhi0 = 0, jn = 0;
-    if (u < u_end) fetch(q[s_beg + (u >> lk)], r0, ylo0, yhi0);
+    if (u < u_end) fetch(q[s_beg + (u >> lk)]);
     if (u + nwarps < u_end) jn = q[s_beg + ((u + nwarps) >> lk)];
-    while (u < u_end) {
-        const uint32_t u1 = u + nwarps, u2 = u1 + nwarps;
-        uint4 r1 = make_uint4(0, 0, 0, 0);
-        uint32_t ylo1 = 0, yhi1 = 0, jn2 = 0;
-        if (u1 < u_end) fetch(jn, r1, ylo1, yhi1);
-        if (u2 < u_end) jn2 = q[s_beg + (u2 >> lk)];
-        const uint64_t beg = ((unsigned long long)r0.y << 32) | r0.x;
-        const uint64_t sb = beg + ylo0, se = beg + (yhi0 == 0xffffffffu ? r0.z : yhi0);
-        const uint64_t len = se - sb, c = u & ((1u << lk) - 1u);
-        const uint64_t pb = sb + ((len * c) >> lk), pe = sb + ((len * (c + 1)) >> lk);
-        ev += pe - pb;
-        int32_t* a = acc_s + ((CH == 2 && (r0.w & 0x80u)) ? T.len : 0u);
-        add_segment<WM>(n, a, pb, pe, r0.w & 31u, WM == kWPacked ? T.lo - T.pbase : T.lo, T.len, lane, pol, bad);
-        u = u1;
-        r0 = r1;
-        ylo0 = ylo1;
-        yhi0 = yhi1;
-        jn = jn2;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Flat delivery: the row segments of a part's spikes are laid end to end as
-// one stream of 16-byte edge vectors, and the CTA's warps walk that stream
-// in chunks of 32 x FV vectors (FV per lane, all in flight together).  Every
-// lane keeps FV loads outstanding whatever the row lengths are, and the
-// warps of the CTA finish within one chunk of each other.  Per batch of up
-// to kFlatBatch spikes the CTA first loads every spike's row record (and
-// split offsets) in parallel into shared memory -- first vector, vector
-// count (exclusive scan), length, head offset, shift and channel -- then
-// streams; a lane finds the spike of its vector by walking the scan forward
-// from the chunk's first spike (found by a two-level warp ballot).
-// ---------------------------------------------------------------------------
-constexpr uint32_t kFlatBatch = 1024;  // spike records per batch
-constexpr uint32_t kFlatRecWords = 3 * kFlatBatch + 4;  // gv0[], vscan[] (+1), info[]
-__host__ __device__ constexpr int flat_vec_of(int wm) { return wm == kWF32 ? 4 : (wm == kW16 ? 5 : 6); }
-
-// The first spike s of the batch with vscan[s] <= v < vscan[s+1] (whole warp;
-// nb <= kFlatBatch, vscan[0] = 0 <= v < vscan[nb]).
-__device__ __forceinline__ uint32_t flat_first_spike(const uint32_t* vscan, uint32_t nb, uint32_t v, uint32_t lane)
-{
-    const uint32_t p1 = lane * 32u;
-    const uint32_t m1 = __ballot_sync(0xffffffffu, p1 < nb && vscan[p1] <= v);
-    const uint32_t base = (31u - __clz(m1)) * 32u;
-    const uint32_t p2 = base + lane;
-    const uint32_t m2 = __ballot_sync(0xffffffffu, p2 < nb && vscan[p2] <= v);
-    return base + 31u - __clz(m2);
-}
-
-// Delivers the spikes [s_beg, s_end) of the instance's queue q (local ids
-// from pbase) to tile T through the flat stream; rec: kFlatRecWords words of
-// shared memory.  last(): called by thread 0 once the last batch's records
-// are in place (the caller takes its next work item there, while the warps
-// stream).  ev: every lane of a warp adds the warp's delivered edges.
-template <int WM, int CH, class Last>
-__device__ __forceinline__ void deliver_flat(const Net& n, const TileDev& T, const uint32_t* q, const uint32_t* sp,
-                                             int32_t* acc_s, uint32_t* rec, uint32_t s_beg, uint32_t s_end,
-                                             unsigned long long pol, unsigned long long& ev, bool& bad, Last last)
-{
-    constexpr int FV = flat_vec_of(WM);
-    constexpr uint32_t kChunk = 32u * FV;
-    __shared__ uint32_t s_wsum[32];
-    __shared__ uint32_t s_next;  // next chunk of the stream (vectors)
-    uint32_t* gv0 = rec;
-    uint32_t* vscan = rec + kFlatBatch;
-    uint32_t* info = vscan + kFlatBatch + 1;
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    const uint32_t nsplit = T.ntiles - 1;
-    const uint32_t x0 = WM == kWPacked ? T.lo - T.pbase : T.lo;
-    constexpr uint32_t per_thread = kFlatBatch / kTiledThreads;  // records per thread (the CTA has kTiledThreads)
-    static_assert(kFlatBatch % kTiledThreads == 0 && per_thread <= 4, "whole records per thread");
-    if (s_end <= s_beg && tid == 0) last();
-    for (uint32_t b0 = s_beg; b0 < s_end; b0 += kFlatBatch) {
-        const uint32_t nb = min(kFlatBatch, s_end - b0);
-        // the records of this batch, per_thread consecutive spikes per thread
-        uint32_t nv_sum = 0, len_sum = 0, nvs[per_thread];
-#pragma unroll
-        for (uint32_t h = 0; h < per_thread; ++h) {
-            nvs[h] = 0;
-            const uint32_t i = per_thread * tid + h;
-            if (i >= nb) continue;
-            const uint32_t j = q[b0 + i];
-            const uint4 r = __ldg(n.rinfo + j);
-            uint64_t sb = ((unsigned long long)r.y << 32) | r.x;
-            uint64_t se = sb + r.z;
-            if (nsplit) {
-                const uint32_t* sj = sp + (size_t)(j - T.pbase) * nsplit;
-                const uint64_t beg = sb;
-                if (T.tau > 0) sb = beg + __ldg(sj + T.tau - 1);
-                if (T.tau < nsplit) se = beg + __ldg(sj + T.tau);
-            }
-            const uint32_t len = (uint32_t)(se - sb), hs = (uint32_t)(sb & 3u);
-            gv0[i] = (uint32_t)(sb >> 2);
-            info[i] = len | hs << 24 | (r.w & 31u) << 26 | ((CH == 2 && (r.w & 0x80u)) ? 1u << 31 : 0u);
-            nvs[h] = len ? (hs + len + 3u) >> 2 : 0u;
-            nv_sum += nvs[h];
-            len_sum += len;
+    // the unit whose rounds are being formed: aligned vectors [cb, ce), first
+    // round pending with its head / tail edges [pb, a4) and [b4, pe)
+    uint64_t cb = 0, ce = 0, pb = 0, pe = 0;
+    uint32_t csc = 0;
+    int32_t crw = 0;
+    bool first = false;
+    // forms the next round into R and issues its loads; false when the warp's units are done
+    auto issue = [&](PipeRound<WM>& R) -> bool {
+        while (!first && cb >= ce) {  // the current unit is done: take the next non-empty one
+            if (u >= u_end) return false;
+            const uint64_t beg = ((unsigned long long)r.y << 32) | r.x;
+            const uint64_t sb = beg + ylo, se = beg + (yhi == 0xffffffffu ? r.z : yhi);
+            const uint64_t len = se - sb, c = u & ((1u << lk) - 1u);
+            pb = sb + ((len * c) >> lk);
+            pe = sb + ((len * (c + 1)) >> lk);
+            csc = (r.w & 31u) | ((CH == 2 && (r.w & 0x80u)) ? 32u : 0u);
+            crw = rwn;
+            ev += pe - pb;
+            // prefetch: the record of the unit after this one and the spike of the one after that
+            const uint32_t u1 = u + nwarps;
+            if (u1 < u_end) fetch(jn);
+            if (u1 + nwarps < u_end) jn = q[s_beg + ((u1 + nwarps) >> lk)];
+            u = u1;
+            const uint64_t upa = (pb + EPV - 1) & ~(uint64_t)(EPV - 1), dna = pe & ~(uint64_t)(EPV - 1);
+            cb = upa < pe ? upa : pe;
+            ce = dna > cb ? dna : cb;
+            first = pe > pb;
         }
-        // exclusive scan of the vector counts over the batch
-        uint32_t incl = nv_sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= (uint32_t)o) incl += y;
+        // this lane's vectors of the round: cb + EPV lane + RB i < ce
+        const uint64_t rem = ce - cb;
+        uint32_t nv = 0;
+        if (rem > (uint64_t)EPV * lane) {
+            const uint64_t k = (rem - (uint64_t)EPV * lane + RB - 1) / RB;
+            nv = k < (uint64_t)PV ? (uint32_t)k : (uint32_t)PV;
         }
+        R.nv = nv;
+        R.sc = csc;
+        R.rw = crw;
 #pragma unroll
-        for (int o = 16; o; o >>= 1) len_sum += __shfl_xor_sync(0xffffffffu, len_sum, o);
-        ev += len_sum;
-        if (lane == 31) s_wsum[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            if (lane == 0) s_next = 0;
-            const uint32_t w = lane < nwarps ? s_wsum[lane] : 0u;
-            uint32_t x = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= (uint32_t)o) x += y;
-            }
-            if (lane < nwarps) s_wsum[lane] = x - w;
-        }
-        __syncthreads();
-        {
-            uint32_t v = s_wsum[warp] + incl - nv_sum;
-#pragma unroll
-            for (uint32_t h = 0; h < per_thread; ++h) {
-                const uint32_t i = per_thread * tid + h;
-                if (i < nb) vscan[i] = v;
-                v += nvs[h];
-            }
-            if (tid == blockDim.x - 1) vscan[nb] = v;  // the batch's vector total (entries past nb count 0)
-        }
-        __syncthreads();
-        if (b0 + kFlatBatch >= s_end && tid == 0) last();
-        const uint32_t V = vscan[nb];
-        // chunks are taken from a shared counter (the next one while the
-        // current one's loads are in flight), so a warp held up elsewhere
-        // takes fewer of them
-        uint32_t c0 = 0;
-        if (lane == 0) c0 = atomicAdd(&s_next, kChunk);
-        c0 = __shfl_sync(0xffffffffu, c0, 0);
-        while (c0 < V) {
-            uint32_t s = flat_first_spike(vscan, nb, c0, lane);
-            uint4 tv[FV];
-            uint2 wh[WM == kW16 ? FV : 1];  // int16 codes (kW16)
-            uint4 wf[WM == kWF32 ? FV : 1]; // binary32 weights (kWF32)
-            uint32_t mk[FV];                // first valid edge | end << 2 | shift << 5 | channel << 10
-#pragma unroll
-            for (int k = 0; k < FV; ++k) {
-                const uint32_t v = c0 + 32u * k + lane;
-                mk[k] = 0;
-                tv[k] = make_uint4(0, 0, 0, 0);
-                if (v < V) {
-                    while (vscan[s + 1] <= v) ++s;
-                    const uint32_t inf = info[s], len = inf & 0xffffffu, hs = (inf >> 24) & 3u;
-                    const uint32_t rel = v - vscan[s];
-                    const int first = (int)(4u * rel) - (int)hs;  // segment edge of lane element 0
-                    const uint32_t lo = first < 0 ? (uint32_t)(-first) : 0u;
-                    const uint32_t hi = (int)len - first < 4 ? (uint32_t)((int)len - first) : 4u;
-                    mk[k] = lo | hi << 2 | ((inf >> 26) & 31u) << 5 | (inf >> 31) << 10;
-                    const uint64_t e = 4ull * ((unsigned long long)gv0[s] + rel);
-                    if constexpr (WM == kWPacked) {
-                        tv[k] = ld_edges4(n.pk + e, pol);
-                    } else {
-                        tv[k] = ld_edges4(n.tgt + e, pol);
-                        if constexpr (WM == kW16) wh[k] = ld_edges2(n.w16 + e, pol);
-                        else wf[k] = ld_edges4(n.w32 + e, pol);
-                    }
+        for (int i = 0; i < PV; ++i) {
+            const uint64_t e = cb + (uint64_t)EPV * lane + (uint64_t)RB * i;
+            if ((uint32_t)i < nv) {
+                if constexpr (WM == kWPacked) {
+                    R.tv[i] = ld_edges4(n.pk + e, pol);
+                } else if constexpr (WM == kWOff16) {
+                    R.tv[i] = ld_edges4(n.pk16 + e, pol);
+                } else {
+                    R.tv[i] = ld_edges4(n.tgt + e, pol);
+                    if constexpr (WM == kW16) R.wh[i] = ld_edges2(n.w16 + e, pol);
+                    else R.wf[i] = ld_edges4(n.w32 + e, pol);
                 }
             }
-            uint32_t cn = 0;
-            if (lane == 0) cn = atomicAdd(&s_next, kChunk);
-#pragma unroll
-            for (int k = 0; k < FV; ++k) {
-                const uint32_t m = mk[k], lo = m & 3u, hi = (m >> 2) & 7u, shift = (m >> 5) & 31u;
-                int32_t* a = acc_s + ((CH == 2 && (m >> 10 & 1u)) ? T.len : 0u);
-                const uint32_t vv[4] = {tv[k].x, tv[k].y, tv[k].z, tv[k].w};
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    if ((uint32_t)i < lo || (uint32_t)i >= hi) continue;
-                    uint32_t x;
-                    int32_t w;
-                    if constexpr (WM == kWPacked) {
-                        x = (vv[i] >> 16) - x0;
-                        w = (int32_t)(int16_t)(vv[i] & 0xffffu) << shift;
-                    } else if constexpr (WM == kW16) {
-                        x = vv[i] - x0;
-                        const uint32_t h2 = i < 2 ? wh[k].x : wh[k].y;
-                        w = (int32_t)(int16_t)((i & 1) ? (h2 >> 16) : (h2 & 0xffffu)) << shift;
-                    } else {
-                        x = vv[i] - x0;
-                        const uint32_t fw = i == 0 ? wf[k].x : i == 1 ? wf[k].y : i == 2 ? wf[k].z : wf[k].w;
-                        w = __float2int_rz(__uint_as_float(fw));
-                    }
-                    if (x < T.len)
-                        atomicAdd(a + x, w);
-                    else
-                        bad = true;
+        }
+        if (first) {  // the unaligned head [pb, cb) on lanes 0..EPV-1, tail [ce, pe) on lanes EPV..2 EPV-1
+            uint64_t e = ~0ull;
+            if (lane < cb - pb)
+                e = pb + lane;
+            else if (lane >= EPV && lane - EPV < pe - ce)
+                e = ce + (lane - EPV);
+            if (e != ~0ull) {
+                R.sc |= 64u;
+                if constexpr (WM == kWPacked) {
+                    R.hx = ld_edge(n.pk + e, pol);
+                } else if constexpr (WM == kWOff16) {
+                    R.hx = ld_edge16(reinterpret_cast<const int16_t*>(n.pk16 + e), pol);
+                } else {
+                    R.hx = ld_edge(n.tgt + e, pol);
+                    if constexpr (WM == kW16) R.hw = ld_edge16(n.w16 + e, pol);
+                    else R.hw = ld_edge(reinterpret_cast<const uint32_t*>(n.w32 + e), pol);
                 }
             }
-            c0 = __shfl_sync(0xffffffffu, cn, 0);
+            first = false;
         }
-        __syncthreads();  // the next batch rewrites the records
+        cb += (uint64_t)RB * PV;
+        if (cb > ce) cb = ce;
+        return true;
+    };
+    auto add = [&](int32_t* a, uint32_t x, int32_t w) {
+        if (x < tlen)
+            atomicAdd(a + x, w);
+        else
+            bad = true;
+    };
+    auto process = [&](const PipeRound<WM>& R) {
+        const uint32_t shift = R.sc & 31u;
+        int32_t* a = acc_s + ((CH == 2 && (R.sc & 32u)) ? tlen : 0u);
+#pragma unroll
+        for (int i = 0; i < PV; ++i) {
+            if ((uint32_t)i >= R.nv) continue;
+            const uint32_t v[4] = {R.tv[i].x, R.tv[i].y, R.tv[i].z, R.tv[i].w};
+            if constexpr (WM == kWOff16) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    add(a, (v[k] & 0xffffu) - x0, R.rw);
+                    add(a, (v[k] >> 16) - x0, R.rw);
+                }
+                continue;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if constexpr (WM == kWPacked) {
+                    add(a, (v[k] >> 16) - x0, (int32_t)(int16_t)(v[k] & 0xffffu) << shift);
+                } else if constexpr (WM == kW16) {
+                    const uint32_t h2 = k < 2 ? R.wh[i].x : R.wh[i].y;
+                    add(a, v[k] - x0, (int32_t)(int16_t)((k & 1) ? (h2 >> 16) : (h2 & 0xffffu)) << shift);
+                } else {
+                    const uint32_t f = k == 0 ? R.wf[i].x : k == 1 ? R.wf[i].y : k == 2 ? R.wf[i].z : R.wf[i].w;
+                    add(a, v[k] - x0, __float2int_rz(__uint_as_float(f)));
+                }
+            }
+        }
+        if (R.sc & 64u) {
+            if constexpr (WM == kWOff16)
+                add(a, (R.hx & 0xffffu) - x0, R.rw);
+            else if constexpr (WM == kWPacked)
+                add(a, (R.hx >> 16) - x0, (int32_t)(int16_t)(R.hx & 0xffffu) << shift);
+            else if constexpr (WM == kW16)
+                add(a, R.hx - x0, (int32_t)(int16_t)(R.hw & 0xffffu) << shift);
+            else
+                add(a, R.hx - x0, __float2int_rz(__uint_as_float(R.hw)));
+        }
+    };
+    PipeRound<WM> A, B;
+    bool hA = issue(A);
+    while (hA) {
+        const bool hB = issue(B);
+        process(A);
+        if (!hB) break;
+        hA = issue(A);
+        process(B);
     }
 }
 
@@ -703,12 +544,10 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledCtasPerSm) k_receive_tile
                                                                     const uint32_t* __restrict__ split, uint32_t max_len,
                                                                     uint32_t pdl)
 {
-    extern __shared__ __align__(16) int32_t acc_s[];  // CH * max_len (the current tile uses CH * len), then the
-                                                      // flat stream's spike records (kFlatRecWords)
+    extern __shared__ __align__(16) int32_t acc_s[];  // CH * max_len (the current tile uses CH * len)
     __shared__ TileDev s_T[2];
     __shared__ ItemDev s_I[2];
     __shared__ uint32_t s_ok[2];
-    uint32_t* rec = reinterpret_cast<uint32_t*>(acc_s + CH * max_len);
     const unsigned long long t = n.ctl->t + n.k;
     const uint32_t lane = threadIdx.x & 31u;
     unsigned int* ctr = n.tile_ctr + (t & 1ull);
@@ -742,8 +581,8 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledCtasPerSm) k_receive_tile
     for (uint32_t b = 0; s_ok[b]; b ^= 1u) {
         const ItemDev& I = s_I[b];  // read from shared memory where used
         const TileDev& T = s_T[b];
-        deliver_flat<WM, CH>(n, T, qs + T.pbase, split + T.split, acc_s, rec, I.s_beg, I.s_end, pol, ev, bad,
-                             [&]() { take(atomicAdd(ctr, 1u) + gridDim.x, b ^ 1u); });
+        deliver_pipe<WM, CH>(n, T, qs + T.pbase, T.pbase, split + T.split, acc_s, I.s_beg, I.s_end, pol, ev, bad);
+        if (threadIdx.x == 0) take(atomicAdd(ctr, 1u) + gridDim.x, b ^ 1u);
         // the tile's pending input for the next update, or this part's share
         // of it: the shared-memory adds are made visible to the copy engine,
         // which reads them out before they are cleared
@@ -862,6 +701,8 @@ inline cudaError_t tiled_set_smem(size_t smem)
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_receive_tiled<kWF32, 2>, attr, s);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_receive_tiled<kW16, 2>, attr, s);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_receive_tiled<kWPacked, 2>, attr, s);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_receive_tiled<kWOff16, 1>, attr, s);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_receive_tiled<kWOff16, 2>, attr, s);
     return e;
 }
 
@@ -939,7 +780,7 @@ inline snn_status tiled_plan(TiledPlan& P, const Net& n, const snn_params* param
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t smem = (size_t)longest * channels * 4 + (dynamic ? (size_t)kFlatRecWords * 4 : 0);
+    const size_t smem = (size_t)longest * channels * 4;
     if (tiles.empty() || smem > (size_t)optin || tiles.size() >= (1u << 24)) return SNN_E_ARG;
     if (dynamic && tiles.size() > kPlanMaxTiles) return SNN_E_ARG;
     if (tiled_set_smem(smem) != cudaSuccess) return SNN_E_CUDA;
@@ -1073,10 +914,27 @@ inline cudaError_t enqueue_tiled_receive(const TiledPlan& P, const Net& n, int w
                                   P.max_len, flag);
     };
     if (P.channels == 2)
-        return wm == kWPacked ? go(k_receive_tiled<kWPacked, 2>) : wm == kW16 ? go(k_receive_tiled<kW16, 2>)
-                                                                             : go(k_receive_tiled<kWF32, 2>);
-    return wm == kWPacked ? go(k_receive_tiled<kWPacked, 1>) : wm == kW16 ? go(k_receive_tiled<kW16, 1>)
-                                                                         : go(k_receive_tiled<kWF32, 1>);
+        return wm == kWOff16 ? go(k_receive_tiled<kWOff16, 2>)
+               : wm == kWPacked ? go(k_receive_tiled<kWPacked, 2>)
+               : wm == kW16     ? go(k_receive_tiled<kW16, 2>)
+                                : go(k_receive_tiled<kWF32, 2>);
+    return wm == kWOff16 ? go(k_receive_tiled<kWOff16, 1>)
+           : wm == kWPacked ? go(k_receive_tiled<kWPacked, 1>)
+           : wm == kW16     ? go(k_receive_tiled<kW16, 1>)
+                            : go(k_receive_tiled<kWF32, 1>);
+}
+
+// 16-bit offsets (kWOff16) of every row's targets in their instance.
+__global__ void k_pack_off16(Net n, uint32_t Np, uint16_t* pk16)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t pj = warp; pj < Np; pj += nwarps) {
+        const uint32_t pb = n.inst[n.inst_of_w32[pj >> 5]].pbase;
+        const uint64_t beg = n.roff[pj], end = n.roff[pj + 1];
+        for (uint64_t e = beg + lane; e < end; e += 32) pk16[e] = (uint16_t)(n.tgt[e] - pb);
+    }
 }
 
 // Packed edges (kWPacked) of every row: (target - instance base) << 16 | code.

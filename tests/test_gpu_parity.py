@@ -288,7 +288,10 @@ def test_reset_repeats_the_run(gpu):
 @pytest.mark.parametrize("packed", [True, False])
 def test_weight_write_reaches_the_receive(gpu, packed):
     """Weights written through the ABI are the ones the tiled receive
-    delivers (the packed edges are rebuilt from them)."""
+    delivers: the sweep's rows each carry one weight, so the receive reads
+    16-bit target offsets and the row weights (2 bytes per event); weights
+    that differ inside a row switch it to the packed edges (offset and code,
+    4 bytes), rebuilt from them."""
     import dataclasses
     prob = si.batched_sweep(n_nets=4, base_seed=3, n_steps=300, n_lo=500, n_hi=3000)
     w = prob.w.copy()
@@ -297,8 +300,9 @@ def test_weight_write_reaches_the_receive(gpu, packed):
     changed = dataclasses.replace(prob, w=w)
     o = oracle.run(changed)
     net = gpu.Network(prob, receive=RECV["tiled"], log_capacity=prob.n * 300, packed=packed)
-    assert net.info()["edge_bytes"] == (4 if packed else 6)
+    assert net.info()["edge_bytes"] == (2 if packed else 6)
     net.write("w", w)
+    assert net.info()["edge_bytes"] == (4 if packed else 6)
     net.step(300)
     g = {f: net.read(f) for f in _fields(prob)}
     g["steps"], g["ids"] = net.spikes()
