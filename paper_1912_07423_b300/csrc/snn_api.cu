@@ -284,7 +284,7 @@ FusedDev fused_args(const snn_ctx* c)
 cudaError_t launch_fused(const snn_ctx* c, const Net& n, cudaStream_t s)
 {
     const FusedDev F = fused_args(c);
-    const dim3 grid(c->fused_grid), block(kTiledThreads);
+    const dim3 grid(c->fused_grid), block(kFusedThreads);
     if (c->off16) {
         if (c->stats)
             k_step_fused<kWOff16, true><<<grid, block, c->fused_smem, s>>>(n, F);
@@ -755,7 +755,7 @@ snn_status setup_fused(snn_ctx* c)
         return SNN_OK;  // keep the separate kernels
     }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_fused<kWPacked, false>, kTiledThreads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_fused<kWPacked, false>, kFusedThreads, smem) !=
             cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();

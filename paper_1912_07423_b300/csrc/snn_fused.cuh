@@ -35,7 +35,8 @@
 
 namespace snn {
 
-constexpr uint32_t kFusedChunk = kTiledThreads * kUpdateNeurons;  // neurons of one update unit
+constexpr int kFusedThreads = 512;    // two CTAs per SM, as the tiled receive
+constexpr uint32_t kFusedChunk = kFusedThreads * kUpdateNeurons;  // neurons of one update unit
 
 enum : uint32_t { kUnitPlan = 0, kUnitRecv = 1, kUnitUpdate = 2, kUnitDone = 3 };
 
@@ -100,7 +101,7 @@ __device__ __forceinline__ void fused_unit(const FusedDev& F, uint32_t n_items, 
 // One timestep of the Brunel model without plasticity (delay >= 3), packed or
 // unpacked 16-bit edges (WM), optional spike statistics.
 template <int WM, bool STATS>
-__global__ void __launch_bounds__(kTiledThreads, kTiledCtasPerSm) k_step_fused(Net n, FusedDev F)
+__global__ void __launch_bounds__(kFusedThreads, 2) k_step_fused(Net n, FusedDev F)
 {
     extern __shared__ __align__(16) int32_t acc_s[];  // max(max_len words, the plan's bytes)
     __shared__ TileDev s_T[2];
@@ -160,10 +161,11 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledCtasPerSm) k_step_fused(N
             // which reads them out before they are cleared
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
-            {  // warp w copies out and clears slice w of the len words
+            {  // warp w copies out and clears slice w of the len words (multiples of 16)
                 const uint32_t nwarps = blockDim.x >> 5, warp = tid >> 5;
-                const uint32_t per = T.len / nwarps, w0 = warp * per;
-                if (lane == 0) {
+                const uint32_t chunks = T.len / 16u, cpw = (chunks + nwarps - 1) / nwarps, c0 = warp * cpw;
+                const uint32_t per = c0 < chunks ? 16u * min(cpw, chunks - c0) : 0u, w0 = 16u * c0;
+                if (lane == 0 && per) {
                     bulk_out((odd ? n.acc0 : n.accx) + T.lo + w0, acc_s + w0, per * 4u, I.P > 1);
                     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
                     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledCtasPerSm) k_step_fused(N
             if (tid == 0) take(atomicAdd(n.tile_ctr + (t & 1ull), 1u) + gridDim.x, b ^ 1u);
             __syncthreads();
         } else {  // the plan of the next step, in the accumulators' shared memory
-            plan_step<kTiledThreads>(n, t + 1, F.tiles, F.n_tiles, odd ? F.plan[0] : F.plan[1], F.n_ctas, F.cap,
+            plan_step<kFusedThreads>(n, t + 1, F.tiles, F.n_tiles, odd ? F.plan[0] : F.plan[1], F.n_ctas, F.cap,
                                      F.items_cap, reinterpret_cast<unsigned char*>(acc_s));
             __syncthreads();
             for (uint32_t i = tid; i < (F.plan_bytes + 15u) / 16u; i += blockDim.x)
