@@ -41,18 +41,32 @@ METRIC = "synaptic events/s and realtime factor on 1 B300, batched+int16 vs plai
 # step the state the update reads and writes (Brunel: V 4+4, refractory 1+1,
 # input 4 read + 4 cleared = 18 B; Vogels 44 B; STDP traces +16 B).
 B_SPIKE_DELIVERED, B_SPIKE_EMITTED = 20, 12
+B_ROW_WEIGHT = 4  # per delivered spike, when the receive reads its row's one weight
+
+
+def reads_row_weights(info: dict) -> bool:
+    """The receive takes each row's one weight from a per-row array (16-bit
+    target offsets in the tiled receive, 4-byte targets in the global one)."""
+    return info["edge_bytes"] == 2 or (info["receive"] == "global" and info["edge_bytes"] == 4)
+
+
+def spike_bytes(info: dict) -> int:
+    """Bytes per delivered spike: row offsets 16 + queue entry 4 (+ row weight)."""
+    return B_SPIKE_DELIVERED + (B_ROW_WEIGHT if reads_row_weights(info) else 0)
 B_NEURON = {si.BRUNEL: 18, si.VOGELS: 44}
 B_NEURON_STDP = 16
 
 
 def gpu_launches(steps: int, recv_kind: str, stdp: bool, lazy: bool = False, per_graph: int = 16,
-                 fused: bool = False) -> int:
-    """Kernels of this library launched by `steps` steps of snn_step: the
-    update, the STDP passes (eager: depression and potentiation; lazy: one
+                 fused: bool = False, persistent: bool = False) -> int:
+    """Kernels of this library launched by one snn_step call of `steps` steps:
+    the update, the STDP passes (eager: depression and potentiation; lazy: one
     replay pass), the receive (tiled: per-step plan and receive; bulk:
     receive, merge; global: receive) -- or the one fused step kernel -- and
     one step-counter advance per captured graph (per_graph steps, the rest one
-    by one)."""
+    by one); the persistent form launches once per call."""
+    if persistent:
+        return 1
     if fused:
         per_step = 1
     else:
@@ -396,7 +410,7 @@ def graph_construction(prob, dev, hbm: float, reps: int = 3) -> dict:
             "what": "snn_expand_jobs: one job per neuron (out-degree values from its instance's ids)"}
 
 
-def launch_bytes(net, prob, t0: int, n: int, edge_bytes: int) -> list:
+def launch_bytes(net, prob, t0: int, n: int, edge_bytes: int, per_spike: int = B_SPIKE_DELIVERED) -> list:
     """Algorithmic bytes of the receive launches of steps t0 .. t0+n-1, from
     the spike log and the row lengths: the receive of step t delivers the
     spikes of step t+1-d, each a whole row (an ncu capture of one of these
@@ -407,13 +421,14 @@ def launch_bytes(net, prob, t0: int, n: int, edge_bytes: int) -> list:
     out = []
     for t in range(t0, t0 + n):
         m = steps == t + 1 - prob.delay
-        out.append(int(deg[ids[m]].sum()) * edge_bytes + int(m.sum()) * B_SPIKE_DELIVERED)
+        out.append(int(deg[ids[m]].sum()) * edge_bytes + int(m.sum()) * per_spike)
     return out
 
 
-def step_bytes(prob, edge_bytes: int, events: int, delivered: int, emitted: int, steps: int) -> float:
+def step_bytes(prob, edge_bytes: int, events: int, delivered: int, emitted: int, steps: int,
+               per_spike: int = B_SPIKE_DELIVERED) -> float:
     per_neuron = B_NEURON[prob.model] + (B_NEURON_STDP if prob.stdp else 0)
-    return (events * edge_bytes + delivered * B_SPIKE_DELIVERED +
+    return (events * edge_bytes + delivered * per_spike +
             emitted * B_SPIKE_EMITTED + per_neuron * prob.n * steps)
 
 
@@ -558,7 +573,7 @@ def run_ours(args, rank, world, dist):
 
     # ---- headline: batched + int16, timed on the device over steps [t0, t0 + K)
     recv_mode = {"auto": snn.RECV_AUTO, "global": snn.RECV_GLOBAL, "tiled": snn.RECV_TILED,
-                 "bulk": snn.RECV_BULK}[args.receive]
+                 "bulk": snn.RECV_BULK, "persistent": snn.RECV_PERSISTENT}[args.receive]
     lazy = prob.stdp and args.plasticity == "lazy"
     t_clk0 = time.time()
     net = snn.Network(prob, w16=True, receive=recv_mode, log_capacity=cap, lazy=lazy, lazy_fifo=args.lazy_fifo,
@@ -580,7 +595,7 @@ def run_ours(args, rank, world, dist):
     phases = net.step_profiled(n_prof)
     c1 = net.counters()
     clk = clocks.stop(t_clk0, time.time())
-    bytes_each = launch_bytes(net, prob, t0, min(n_prof, 16), info["edge_bytes"])
+    bytes_each = launch_bytes(net, prob, t0, min(n_prof, 16), info["edge_bytes"], spike_bytes(info))
     ev_p, sp_p = c1["events"] - c0["events"], c1["spikes"] - c0["spikes"]
     deliv_p = delivered_spikes(net, prob, t0, t0 + n_prof)
     mem = info["device_bytes"]
@@ -592,16 +607,25 @@ def run_ours(args, rank, world, dist):
     ev_total = sum_over_ranks(ev_main)
     value = ev_total / t_max
     fused = bool(info.get("fused"))
-    # the dominant kernel: the receive, or the fused step kernel, which also
-    # runs the update (its bytes: the receive's plus the update's per-neuron
-    # state and per-emitted-spike queue and log writes)
-    kernel = "k_step_fused" if fused else f"k_receive_{recv_kind}"
+    persistent = bool(info.get("persistent"))
+    # the dominant kernel: the receive, or the fused step kernel or the
+    # persistent launch, which also run the update (their bytes: the
+    # receive's plus the update's per-neuron state and per-emitted-spike
+    # queue and log writes)
+    kernel = "k_step_fused" if fused else ("k_persistent" if persistent else f"k_receive_{recv_kind}")
     recv_ms = phases["receive"] / n_prof
-    upd_bytes = (B_NEURON[prob.model] * prob.n * n_prof + B_SPIKE_EMITTED * sp_p) / n_prof if fused else 0.0
-    recv_bytes = (ev_p * info["edge_bytes"] + deliv_p * B_SPIKE_DELIVERED) / n_prof + upd_bytes
-    recv_bytes_6 = (ev_p * 6 + deliv_p * B_SPIKE_DELIVERED) / n_prof + upd_bytes  # int16 code + u32 target per event
+    upd_bytes = ((B_NEURON[prob.model] * prob.n * n_prof + B_SPIKE_EMITTED * sp_p) / n_prof
+                 if fused or persistent else 0.0)
+    sb = spike_bytes(info)
+    recv_bytes = (ev_p * info["edge_bytes"] + deliv_p * sb) / n_prof + upd_bytes
     achieved = recv_bytes / (recv_ms * 1e-3) / 1e9
-    step_b = step_bytes(prob, info["edge_bytes"], ev_main, deliv_main, sp_main, args.steps)
+
+    def frac_at(edge_b: int, spike_b: int) -> float:
+        """The kernel's fraction of the measured HBM rate had its events been
+        stored at edge_b bytes each (same time, same events and spikes)."""
+        b = (ev_p * edge_b + deliv_p * spike_b) / n_prof + upd_bytes
+        return b / (recv_ms * 1e-3) / 1e9 / hbm
+    step_b = step_bytes(prob, info["edge_bytes"], ev_main, deliv_main, sp_main, args.steps, sb)
     step_frac = (step_b / (hbm * 1e9)) / t_main
 
     out = {"metric": METRIC, "value": value, "unit": "synaptic events/s", "n_gpus": world, "steps": args.steps,
@@ -612,7 +636,9 @@ def run_ours(args, rank, world, dist):
                       "synapses": prob.n_edges, "delay_steps": prob.delay, "dt_ms": DT_MS,
                       "window": [t0, t0 + args.steps], "settle_steps": args.settle,
                       "receive": recv_kind, "tiles": info["n_tiles"], "weights": "int16 x 2^shift(row)",
-                      "step_kernels": "fused (update + receive in one kernel)" if fused else "separate",
+                      "step_kernels": ("fused (update + receive in one kernel)" if fused else
+                                       ("persistent (one cooperative launch per call, %d CTAs)" % info["persist_ctas"]
+                                        if persistent else "separate")),
                       **({"tuned_ms_per_step": {k: v for k, v in info["tune_ms"].items() if v > 0}}
                          if info.get("tuned") else {}),
                       "edge_bytes": info["edge_bytes"],
@@ -633,8 +659,13 @@ def run_ours(args, rank, world, dist):
                         "window": [t0, t0 + n_prof],
                         "same_events_as_timed": bool(n_prof == args.steps and ev_p == ev_main),
                         "bytes_each": bytes_each[:16],
-                        # the survey's 6 bytes per event (u32 target + int16 code) beside the bytes read
-                        "frac_at_6_bytes_per_event": recv_bytes_6 / (recv_ms * 1e-3) / 1e9 / hbm,
+                        "edge_bytes": info["edge_bytes"], "spike_bytes": sb,
+                        # the same time and events measured against other edge layouts: a 4-byte
+                        # target per synapse (the paper's Table 2 layout for Vogels / Brunel) and a
+                        # 4-byte target + 2-byte weight code
+                        "frac_at_4_bytes_per_event": frac_at(4, B_SPIKE_DELIVERED),
+                        "frac_at_6_bytes_per_event": frac_at(6, B_SPIKE_DELIVERED),
+                        "events_per_s_in_kernel": ev_p / n_prof / (recv_ms * 1e-3),
                         # effective bytes per delivered event (edges + per-spike records) and the
                         # events/s the measured HBM rate allows for the edges alone
                         "bytes_per_event": recv_bytes * n_prof / max(ev_p, 1),
@@ -643,7 +674,7 @@ def run_ours(args, rank, world, dist):
                              "unit": "GB/s", "achieved": step_b / t_main / 1e9,
                              "bytes_per_event": step_b / max(ev_main, 1)},
            "phase_ms_per_step": {k: v / n_prof for k, v in phases.items()},
-           "gpu_launches": gpu_launches(args.steps, recv_kind, prob.stdp, lazy, fused=fused),
+           "gpu_launches": gpu_launches(args.steps, recv_kind, prob.stdp, lazy, fused=fused, persistent=persistent),
            "clocks": clk}
 
     # ---- the same path with Update Neurons and Receive Spikes as separate
@@ -773,7 +804,7 @@ def main():
     ap.add_argument("--drift-steps", type=int, default=2000, help="window of the rate / ISI CV drift comparison")
     ap.add_argument("--ref-seconds", type=float, default=15.0,
                     help="reference arm: about this long per process on the host cores")
-    ap.add_argument("--receive", choices=["auto", "global", "tiled", "bulk"], default="auto")
+    ap.add_argument("--receive", choices=["auto", "global", "tiled", "bulk", "persistent"], default="auto")
     ap.add_argument("--plasticity", choices=["eager", "lazy"], default="eager",
                     help="Update Synapses form for plastic workloads (brunel_stdp_100k; eager measured faster)")
     ap.add_argument("--lazy-fifo", type=int, default=0, help="lazy plasticity: history length (0: 128)")

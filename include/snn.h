@@ -96,8 +96,11 @@ typedef enum {
 
 /* snn_config.receive */
 #define SNN_RECV_AUTO 0u   /* the library measures: snn_build_graph runs every form that applies to the
-                              graph (global; with sorted rows tiled, and tiled fused with the update --
-                              SNN_F_SERIAL leaves that one out) from the initial state over the same
+                              graph (global; with sorted rows tiled, and tiled fused with the update;
+                              for the fixed models without plasticity the persistent launch with the
+                              fewest CTAs that cover the update and with every resident CTA --
+                              SNN_F_SERIAL leaves the fused and persistent forms out) from the initial
+                              state over the same
                               delay + 150 steps (at most 1,100) and times the last 48 with CUDA events;
                               the fastest is kept (snn_info.tune_ms) and the state returns to N_0.
                               Results do not depend on the form.  The bulk form is not a candidate */
@@ -105,6 +108,9 @@ typedef enum {
                               spikes), red.global.add into L2-resident accumulators */
 #define SNN_RECV_TILED 2u  /* target-tiled, accumulators in shared memory; needs sorted rows */
 #define SNN_RECV_BULK 3u   /* as TILED, rows staged into shared memory by bulk async copies */
+#define SNN_RECV_PERSISTENT 4u /* the fixed models without plasticity: each snn_step call is one cooperative
+                                  launch that runs its steps as phases (Update Neurons, then the global
+                                  receive) separated by a bounded grid-wide barrier; no launch per kernel */
 
 typedef struct {
     uint32_t model;        /* snn_model */
@@ -124,10 +130,11 @@ typedef struct {
                               longest a row stays stale (0: 128, the most the two 64-bit
                               history words of a neuron hold; else 2..128.  The paper's queue
                               holds 50 entries) */
-    uint32_t wait_polls;   /* bulk-copy receive: polls of one bounded wait of its producer or a
-                              consumer on an mbarrier before the kernel gives up with
-                              SNN_E_TIMEOUT (0: 2^20).  The wait for the copies still in flight
-                              before a CTA exits keeps its own bound of 2^26 polls */
+    uint32_t wait_polls;   /* polls of one bounded device-side wait before the kernel gives up with
+                              SNN_E_TIMEOUT: a producer or consumer wait on an mbarrier of the bulk-copy
+                              receive (0: 2^20; the wait for the copies still in flight before a CTA
+                              exits keeps its own bound of 2^26 polls), or a grid-barrier wait of the
+                              persistent launch (0: 2^22 polls, 64 ns apart) */
     uint32_t inst_key0;    /* Philox key word 1 of instance 0: instance b draws with key (seed,
                               inst_key0 + b), so that one network of a batch re-run alone in its
                               own context gets the same random numbers (0 for a batch) */
@@ -330,9 +337,11 @@ typedef struct {
     uint32_t model_state_bytes; /* generic models: bytes of one neuron's state record (else 0) */
     uint32_t fused;        /* 1: update and receive of a step run in one kernel (see SNN_F_SERIAL) */
     uint32_t tuned;        /* 1: the receive form was chosen by SNN_RECV_AUTO's timing run */
-    float tune_ms[4];      /* SNN_RECV_AUTO: ms per step each form took in that run, in the order global,
-                              tiled (separate kernels), tiled fused with the update, bulk; 0: not a
-                              candidate for this graph */
+    float tune_ms[5];      /* SNN_RECV_AUTO: ms per step each form took in that run, in the order global,
+                              tiled (separate kernels), tiled fused with the update, bulk, persistent
+                              launch (the better of its two grids); 0: not a candidate for this graph */
+    uint32_t persistent;   /* 1: one cooperative launch per snn_step call (SNN_RECV_PERSISTENT) */
+    uint32_t persist_ctas; /* its CTAs of 256 threads */
 } snn_info;
 snn_status snn_get_info(snn_ctx* ctx, snn_info* info);
 

@@ -17,7 +17,7 @@ import numpy as np
 from .build import LIB, build as _build
 
 __all__ = ["Network", "SnnError", "load", "VOGELS", "BRUNEL", "MODEL_RELAY", "MODEL_BRUNEL_LIF", "MODEL_STATE_DTYPE",
-           "RECV_AUTO", "RECV_GLOBAL", "RECV_TILED", "RECV_BULK", "F_STDP", "F_W16", "F_STATS", "F_UNPACKED", "F_LAZY",
+           "RECV_AUTO", "RECV_GLOBAL", "RECV_TILED", "RECV_BULK", "RECV_PERSISTENT", "F_STDP", "F_W16", "F_STATS", "F_UNPACKED", "F_LAZY",
            "F_SERIAL", "FIELDS"]
 
 VOGELS, BRUNEL = 0, 1
@@ -28,7 +28,7 @@ MODEL_STATE_DTYPE = {
     MODEL_BRUNEL_LIF: np.dtype({"names": ["V", "r"], "formats": ["<f4", "u1"], "offsets": [0, 4], "itemsize": 8}),
 }
 F_STDP, F_W16, F_STATS, F_UNPACKED, F_LAZY, F_SERIAL = 1, 2, 4, 8, 16, 32
-RECV_AUTO, RECV_GLOBAL, RECV_TILED, RECV_BULK = 0, 1, 2, 3
+RECV_AUTO, RECV_GLOBAL, RECV_TILED, RECV_BULK, RECV_PERSISTENT = 0, 1, 2, 3, 4
 FIELDS = {"V": 0, "ge": 1, "gi": 2, "r": 3, "x": 4, "y": 5, "acc0": 6, "acc1": 7, "w": 8, "model": 9}
 _FIELD_DTYPE = {"V": np.float32, "ge": np.float32, "gi": np.float32, "r": np.int32, "x": np.float32,
                 "y": np.float32, "acc0": np.int32, "acc1": np.int32, "w": np.int32}
@@ -65,7 +65,8 @@ class Info(ctypes.Structure):
     _fields_ = [("receive", ctypes.c_uint32), ("n_tiles", ctypes.c_uint32), ("n_padded", ctypes.c_uint32),
                 ("rows_sorted", ctypes.c_uint32), ("edges", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
                 ("edge_bytes", ctypes.c_uint32), ("model_state_bytes", ctypes.c_uint32), ("fused", ctypes.c_uint32),
-                ("tuned", ctypes.c_uint32), ("tune_ms", ctypes.c_float * 4)]
+                ("tuned", ctypes.c_uint32), ("tune_ms", ctypes.c_float * 5), ("persistent", ctypes.c_uint32),
+                ("persist_ctas", ctypes.c_uint32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(_vp, ctypes.c_size_t, _vp, _vp)
@@ -347,4 +348,5 @@ class Network:
                 "n_padded": i.n_padded, "rows_sorted": bool(i.rows_sorted), "edges": i.edges,
                 "device_bytes": i.device_bytes, "edge_bytes": i.edge_bytes, "model_state_bytes": i.model_state_bytes,
                 "fused": bool(i.fused), "tuned": bool(i.tuned),
-                "tune_ms": dict(zip(["global", "tiled", "fused", "bulk"], [float(x) for x in i.tune_ms]))}
+                "tune_ms": dict(zip(["global", "tiled", "fused", "bulk", "persistent"], [float(x) for x in i.tune_ms])),
+                "persistent": bool(i.persistent), "persist_ctas": int(i.persist_ctas)}

@@ -23,6 +23,7 @@
 #include "snn_bulk.cuh"
 #include "snn_models.cuh"
 #include "snn_fused.cuh"
+#include "snn_persistent.cuh"
 
 #include <cub/device/device_radix_sort.cuh>
 
@@ -94,7 +95,12 @@ struct snn_ctx {
     // each form took in the tuning run (0: not a candidate)
     int form = 0;
     bool tiled_fits = false;           // every row's length fits its 32-bit row record
-    float tune_ms[4] = {0.f, 0.f, 0.f, 0.f};
+    float tune_ms[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    // persistent multi-step launch (snn_persistent.cuh)
+    bool persistent = false;
+    uint32_t persist_grid = 0;         // CTAs of 256 threads (all resident)
+    uint32_t persist_max = 0;          // the most that are resident at once
+    unsigned int* persist_bar = nullptr;  // grid barrier: arrivals, generation
     bool tuned = false;
     // fused step (snn_fused.cuh): update and receive of a step in one kernel
     bool fused = false;
@@ -490,6 +496,7 @@ snn_status init_state(snn_ctx* c)
     CUDA_TRY(c, cudaMemsetAsync(c->net.lbase, 0, (size_t)c->cr * 8, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->net.inst_spikes, 0, (size_t)c->cfg.n_inst * 8, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->net.tile_ctr, 0, 2 * sizeof(unsigned int), c->stream));
+    if (c->persist_bar) CUDA_TRY(c, cudaMemsetAsync(c->persist_bar, 0, 2 * sizeof(unsigned int), c->stream));
     if (c->fused) {  // the input of step 1 and the plans of steps 0 and 1
         CUDA_TRY(c, cudaMemsetAsync(c->net.accx, 0, (size_t)c->Np * 4, c->stream));
         CUDA_TRY(c, cudaMemsetAsync(c->tiled.step.hdr, 0, 4 * sizeof(uint32_t), c->stream));
@@ -778,18 +785,91 @@ snn_status setup_fused(snn_ctx* c)
 }
 
 // The receive forms a context can run.  Results do not depend on the form.
-enum RecvForm : int { kFormGlobal = 0, kFormTiled = 1, kFormFused = 2, kFormBulk = 3, kForms = 4 };
+enum RecvForm : int { kFormGlobal = 0, kFormTiled = 1, kFormFused = 2, kFormBulk = 3, kFormPersist = 4, kForms = 5 };
+
+// The persistent launch applies to the fixed models without plasticity (its
+// receive is the global form).
+bool persist_applies(const snn_ctx* c) { return !c->generic && !c->stdp; }
+
+// k_persistent<...> for the context's model and layout, as a function pointer.
+void* persist_kernel(const snn_ctx* c)
+{
+    const bool rw = c->net.roww != nullptr;
+#define SNN_PK(M, W, R, S, P) reinterpret_cast<void*>(&k_persistent<M, W, R, S, P>)
+#define SNN_PK_NPT(M, W, R, S) (c->npt == kUpdateNeuronsSmall ? SNN_PK(M, W, R, S, kUpdateNeuronsSmall) : SNN_PK(M, W, R, S, kUpdateNeurons))
+#define SNN_PK_S(M, W, R) (c->stats ? SNN_PK_NPT(M, W, R, true) : SNN_PK_NPT(M, W, R, false))
+#define SNN_PK_W(M) (c->w16 ? (rw ? SNN_PK_S(M, true, true) : SNN_PK_S(M, true, false)) : SNN_PK_S(M, false, false))
+    return c->vogels ? SNN_PK_W(0) : SNN_PK_W(1);
+#undef SNN_PK_W
+#undef SNN_PK_S
+#undef SNN_PK_NPT
+#undef SNN_PK
+}
+
+// n steps in one cooperative launch of c->persist_grid CTAs.
+snn_status launch_persistent(snn_ctx* c, uint32_t steps)
+{
+    if (!steps) return SNN_OK;
+    Net n = c->net;
+    n.k = 0;
+    unsigned int* bar = c->persist_bar;
+    uint32_t spin = c->cfg.wait_polls ? c->cfg.wait_polls : kPersistSpin;
+    void* args[] = {&n, &steps, &bar, &spin};
+    CUDA_TRY(c, cudaLaunchCooperativeKernel(persist_kernel(c), dim3(c->persist_grid), dim3(256), args, 0, c->stream));
+    return SNN_OK;
+}
+
+// The CTAs a persistent launch can hold at once, and its barrier words.
+snn_status setup_persistent(snn_ctx* c)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persist_kernel(c), 256, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return SNN_E_ARG;
+    }
+    int dev = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (!coop) return SNN_E_ARG;
+    c->persist_max = (uint32_t)(sm_count() * per_sm);
+    if (!c->persist_bar) c->persist_bar = alloc_n<unsigned int>(c, 2);
+    if (!c->persist_bar) return fail(c, SNN_E_NOMEM, "grid barrier");
+    CUDA_TRY(c, cudaMemsetAsync(c->persist_bar, 0, 2 * sizeof(unsigned int), c->stream));
+    return SNN_OK;
+}
+
+// Grid of a persistent launch: "small" covers the update's thread groups in
+// one pass (fewer CTAs: cheaper barriers), else every resident CTA.
+uint32_t persist_grid_for(const snn_ctx* c, bool small)
+{
+    const uint32_t groups = c->Np / (uint32_t)c->npt;
+    const uint32_t need = std::max<uint32_t>(1, (groups + 255) / 256);
+    return small ? std::min(need, c->persist_max) : c->persist_max;
+}
+
+// n steps of the context's form: CUDA graphs, or one persistent launch.
+snn_status run_steps(snn_ctx* c, uint32_t n)
+{
+    if (c->persistent) return launch_persistent(c, n);
+    while (c->gk && n >= c->k_steps) {
+        CUDA_TRY(c, cudaGraphLaunch(c->gk, c->stream));
+        n -= c->k_steps;
+    }
+    while (n--) CUDA_TRY(c, cudaGraphLaunch(c->g1, c->stream));
+    return SNN_OK;
+}
 
 // Switches the context to a receive form: builds what it reads (tiles and
 // split tables, packed edges, the fused step's buffers), frees the packed
 // edges when it does not read them, and captures the step graphs.  The
 // neuron state is not touched.  SNN_E_ARG when the form does not fit the
 // graph (the context then runs the global receive).
-snn_status use_form(snn_ctx* c, int form)
+snn_status use_form(snn_ctx* c, int form, uint32_t persist_grid = 0)
 {
     drop_graphs(c);
     c->fused = false;
-    c->use_tiled = form != kFormGlobal;
+    c->persistent = false;
+    c->use_tiled = form != kFormGlobal && form != kFormPersist;
     c->use_bulk = form == kFormBulk;
     snn_status st = SNN_OK;
     if (c->use_tiled) {
@@ -830,7 +910,16 @@ snn_status use_form(snn_ctx* c, int form)
         c->pk32 = nullptr;
     }
     c->net.pk = c->packed ? c->pk32 : nullptr;
-    c->form = c->fused ? kFormFused : (c->use_bulk ? kFormBulk : (c->use_tiled ? kFormTiled : kFormGlobal));
+    if (st == SNN_OK && form == kFormPersist) {
+        st = persist_applies(c) ? setup_persistent(c) : SNN_E_ARG;
+        if (st == SNN_OK) {
+            c->persistent = true;
+            c->persist_grid = persist_grid ? std::min(persist_grid, c->persist_max) : persist_grid_for(c, true);
+        }
+    }
+    c->form = c->persistent ? kFormPersist
+                            : (c->fused ? kFormFused : (c->use_bulk ? kFormBulk : (c->use_tiled ? kFormTiled : kFormGlobal)));
+    if (c->persistent) return SNN_OK;  // no graphs: one launch per snn_step
     snn_status cs = capture(c, 1, &c->g1);
     if (cs == SNN_OK && c->k_steps > 1) cs = capture(c, c->k_steps, &c->gk);
     return st != SNN_OK ? st : cs;
@@ -859,7 +948,10 @@ constexpr uint32_t kTuneSteps = 48;
 // starts from N_0 afterwards (init_state).
 snn_status tune_receive(snn_ctx* c)
 {
-    int cand[kForms];
+    // candidates: (form, persistent grid); the persistent launch twice, with
+    // the fewest CTAs that cover the update and with every resident CTA
+    int cand[kForms + 1];
+    uint32_t cgrid[kForms + 1] = {};
     int nc = 0;
     cand[nc++] = kFormGlobal;
     if (c->rows_sorted && c->tiled_fits) {
@@ -867,6 +959,16 @@ snn_status tune_receive(snn_ctx* c)
         c->use_tiled = true;
         c->use_bulk = false;
         if (!(c->cfg.flags & SNN_F_SERIAL) && fused_applies(c)) cand[nc++] = kFormFused;
+        c->use_tiled = false;
+    }
+    if (persist_applies(c) && !(c->cfg.flags & SNN_F_SERIAL) && setup_persistent(c) == SNN_OK) {
+        const uint32_t g0 = persist_grid_for(c, true), g1 = persist_grid_for(c, false);
+        cand[nc] = kFormPersist;
+        cgrid[nc++] = g0;
+        if (g1 != g0) {
+            cand[nc] = kFormPersist;
+            cgrid[nc++] = g1;
+        }
     }
     for (float& x : c->tune_ms) x = 0.f;
     if (nc == 1) return use_form(c, cand[0]);
@@ -877,18 +979,13 @@ snn_status tune_receive(snn_ctx* c)
         return fail(c, SNN_E_CUDA, "cudaEventCreate");
     }
     int best = -1;
+    uint32_t best_grid = 0;
+    float best_ms = 0.f;
     snn_status st = SNN_OK;
     const uint32_t warm = tune_warm_steps(c);
-    auto launch = [&](uint32_t n) -> snn_status {
-        while (c->gk && n >= c->k_steps) {
-            CUDA_TRY(c, cudaGraphLaunch(c->gk, c->stream));
-            n -= c->k_steps;
-        }
-        while (n--) CUDA_TRY(c, cudaGraphLaunch(c->g1, c->stream));
-        return SNN_OK;
-    };
+    auto launch = [&](uint32_t n) -> snn_status { return run_steps(c, n); };
     for (int i = 0; i < nc && st == SNN_OK; ++i) {
-        st = use_form(c, cand[i]);
+        st = use_form(c, cand[i], cgrid[i]);
         if (st == SNN_E_ARG) {  // the form does not fit after all: not a candidate
             st = SNN_OK;
             continue;
@@ -909,14 +1006,19 @@ snn_status tune_receive(snn_ctx* c)
         float ms = 0.f;
         if (st == SNN_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = fail(c, SNN_E_CUDA, "event time");
         if (st == SNN_OK) {
-            c->tune_ms[cand[i]] = ms / kTuneSteps;
-            if (best < 0 || c->tune_ms[cand[i]] < c->tune_ms[best]) best = cand[i];
+            const float per = ms / kTuneSteps;
+            if (c->tune_ms[cand[i]] == 0.f || per < c->tune_ms[cand[i]]) c->tune_ms[cand[i]] = per;
+            if (best < 0 || per < best_ms) {
+                best = cand[i];
+                best_grid = cgrid[i];
+                best_ms = per;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != SNN_OK) return st;
-    return use_form(c, best < 0 ? kFormGlobal : best);
+    return use_form(c, best < 0 ? kFormGlobal : best, best_grid);
 }
 
 }  // namespace
@@ -949,7 +1051,7 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     if ((cfg->flags & SNN_F_LAZY) &&
         (!(cfg->flags & SNN_F_STDP) || cfg->lazy_fifo == 1 || cfg->lazy_fifo > (uint32_t)kLazyMaxF))
         return SNN_E_ARG;
-    if (cfg->receive > SNN_RECV_BULK) return SNN_E_ARG;
+    if (cfg->receive > SNN_RECV_PERSISTENT) return SNN_E_ARG;
     uint64_t N = 0, Np = 0;
     for (uint32_t b = 0; b < cfg->n_inst; ++b) {
         const snn_params& p = params[b];
@@ -1340,6 +1442,8 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
         c->tuned = st == SNN_OK;
     } else if (c->cfg.receive == SNN_RECV_GLOBAL) {
         st = use_form(c, kFormGlobal);
+    } else if (c->cfg.receive == SNN_RECV_PERSISTENT) {
+        st = persist_applies(c) ? use_form(c, kFormPersist) : fail(c, SNN_E_ARG, "the persistent launch needs a fixed model without plasticity");
     } else if (!c->rows_sorted || !c->tiled_fits) {
         st = fail(c, SNN_E_ARG, c->rows_sorted ? "the tiled receive does not fit this graph"
                                                : "the tiled receive needs rows sorted by target");
@@ -1394,12 +1498,7 @@ snn_status snn_step(snn_ctx* c, uint32_t n_steps)
         c->tune_next *= 8;
     }
     c->host_steps += left;
-    while (c->gk && left >= c->k_steps) {
-        CUDA_TRY(c, cudaGraphLaunch(c->gk, c->stream));
-        left -= c->k_steps;
-    }
-    while (left--) CUDA_TRY(c, cudaGraphLaunch(c->g1, c->stream));
-    return SNN_OK;
+    return run_steps(c, left);
 }
 
 snn_status snn_step_profiled(snn_ctx* c, uint32_t n_steps, double* phase_ms)
@@ -1417,7 +1516,15 @@ snn_status snn_step_profiled(snn_ctx* c, uint32_t n_steps, double* phase_ms)
     for (uint32_t i = 0; i < n_steps && st == SNN_OK; ++i) {
         for (int k = 0; k <= kPhases; ++k)
             if (!ev[(size_t)i * (kPhases + 1) + k]) st = fail(c, SNN_E_CUDA, "cudaEventCreate failed");
-        if (st == SNN_OK) st = enqueue_step(c, c->stream, &ev[(size_t)i * (kPhases + 1)]);
+        if (st != SNN_OK) break;
+        cudaEvent_t* e = &ev[(size_t)i * (kPhases + 1)];
+        if (c->persistent) {  // the whole step is one launch: phase [3]
+            for (int k = 0; k <= 3; ++k) cudaEventRecord(e[k], c->stream);
+            st = launch_persistent(c, 1);
+            for (int k = 4; k <= kPhases; ++k) cudaEventRecord(e[k], c->stream);
+        } else {
+            st = enqueue_step(c, c->stream, e);
+        }
     }
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (st == SNN_OK && e != cudaSuccess) st = fail(c, SNN_E_CUDA, "profiled steps: %s", cudaGetErrorString(e));
@@ -1733,7 +1840,9 @@ snn_status snn_get_info(snn_ctx* c, snn_info* info)
     info->model_state_bytes = (uint32_t)c->mbytes;
     info->fused = c->fused ? 1u : 0u;
     info->tuned = c->tuned ? 1u : 0u;
-    for (int f = 0; f < 4; ++f) info->tune_ms[f] = c->tune_ms[f];
+    for (int f = 0; f < 5; ++f) info->tune_ms[f] = c->tune_ms[f];
+    info->persistent = c->persistent ? 1u : 0u;
+    info->persist_ctas = c->persistent ? c->persist_grid : 0u;
     return SNN_OK;
 }
 

@@ -455,9 +455,8 @@ __device__ __forceinline__ void piece_of(uint64_t beg, uint64_t end, uint32_t c,
 // paper's models: Section III-A-2, Table 2), held per row in n.roww, so the
 // walk reads the 4-byte targets alone.
 template <bool W16, bool ROWW>
-__global__ void __launch_bounds__(256) k_receive_global(Net n)
+__device__ __forceinline__ void receive_global(const Net& n, unsigned long long t)
 {
-    const unsigned long long t = n.ctl->t + n.k;
     if (t + 1 < n.d) return;
     const uint32_t lane = lane_id();
     unsigned long long ev = 0;
@@ -490,6 +489,12 @@ __global__ void __launch_bounds__(256) k_receive_global(Net n)
         }
     });
     if (lane == 0 && ev) atomicAdd(&n.ctl->events, ev);
+}
+
+template <bool W16, bool ROWW>
+__global__ void __launch_bounds__(256) k_receive_global(Net n)
+{
+    receive_global<W16, ROWW>(n, n.ctl->t + n.k);
 }
 
 // ---------------------------------------------------------------------------

@@ -13,7 +13,7 @@ import snn_inputs as si
 
 pytestmark = pytest.mark.gpu
 
-RECV = {"global": 1, "tiled": 2, "bulk": 3, "tiled_serial": 2}
+RECV = {"global": 1, "tiled": 2, "bulk": 3, "tiled_serial": 2, "persistent": 4}
 # "tiled_serial": the tiled receive as its own kernel after the update even
 # where the library would run both in one kernel per step (SNN_F_SERIAL)
 
@@ -88,7 +88,7 @@ def oracle_run(key, prob, **kw):
 
 # ------------------------------------------------------------------ the configs
 @pytest.mark.parametrize("w16", [True, False])
-@pytest.mark.parametrize("receive", ["global", "tiled", "bulk"])
+@pytest.mark.parametrize("receive", ["global", "tiled", "bulk", "persistent"])
 def test_vogels_4k_full(gpu, w16, receive):
     """Vogels-Abbott, 4,000 neurons, 2 % connectivity, 1,000 steps."""
     prob = si.vogels_4k(seed=1, n_steps=1000)
@@ -98,7 +98,7 @@ def test_vogels_4k_full(gpu, w16, receive):
     assert_parity(g, o, prob)
 
 
-@pytest.mark.parametrize("receive", ["global", "tiled", "bulk", "tiled_serial"])
+@pytest.mark.parametrize("receive", ["global", "tiled", "bulk", "tiled_serial", "persistent"])
 def test_brunel_12k5_full(gpu, receive):
     """Brunel, 12,500 neurons, C_E 1,000 / C_I 250, 15-step delay, 10,000 steps."""
     prob = si.brunel_12k5(seed=1, n_steps=10000)
@@ -120,7 +120,7 @@ def test_brunel_stdp_small(gpu, w16, receive):
     assert_parity(g, o, prob)
 
 
-@pytest.mark.parametrize("receive", ["global", "tiled", "bulk", "tiled_serial"])
+@pytest.mark.parametrize("receive", ["global", "tiled", "bulk", "tiled_serial", "persistent"])
 def test_batched_uneven_parity(gpu, receive):
     """A batch of uneven Brunel networks in one context equals the oracle
     on the whole batch."""
@@ -162,7 +162,7 @@ def test_forced_spike_arrives_after_d_steps(gpu, d, model):
     prob = si.from_edges(model, inst, edges, w, delay=d, n_steps=40)
     ov = [(7, 0, 1000.0), (9, 250, 1000.0)]
     o = oracle.run(prob, overrides=ov)
-    for receive in ("global", "tiled", "bulk", "tiled_serial"):
+    for receive in ("global", "tiled", "bulk", "tiled_serial", "persistent"):
         g = run_gpu(gpu, prob, overrides=ov, receive=receive)
         assert_parity(g, o, prob)
 
@@ -176,7 +176,7 @@ def test_largest_delay(gpu):
     prob.delay = 1000
     o = oracle.run(prob)
     assert int((o["steps"] >= 1000).sum()) > 100  # spikes after the first deliveries
-    for receive in ("global", "tiled", "bulk", "tiled_serial"):
+    for receive in ("global", "tiled", "bulk", "tiled_serial", "persistent"):
         assert_parity(run_gpu(gpu, prob, receive=receive), o, prob)
 
 
@@ -196,7 +196,7 @@ def test_relay_network(gpu, d):
               "r": np.zeros(200, np.int32), "x": np.zeros(200, np.float32), "y": np.zeros(200, np.float32),
               "acc0": acc0, "acc1": np.zeros(200, np.int32), "w": prob.w.copy()}
     o = oracle.run(prob, state=ostate)
-    for receive in ("tiled", "bulk", "tiled_serial"):
+    for receive in ("tiled", "bulk", "tiled_serial", "persistent"):
         g = run_gpu(gpu, prob, state=state, receive=receive)
         assert_parity(g, o, prob)
     assert len(o["ids"]) > 500
@@ -210,7 +210,7 @@ def test_empty_graph_and_ragged_instances(gpu):
     prob = si.problem(si.BRUNEL, insts, delay=2, n_steps=700, seed=9)
     assert prob.n_edges == 0
     o = oracle.run(prob)
-    for receive in ("global", "tiled", "bulk"):
+    for receive in ("global", "tiled", "bulk", "persistent"):
         assert_parity(run_gpu(gpu, prob, receive=receive), o, prob)
 
 
@@ -496,3 +496,38 @@ def test_row_weight_layout(gpu):
         net.close()
     assert_parity(g, o2, prob2)
     assert not np.array_equal(o2["ids"], o["ids"])  # the changed weight matters
+
+
+def test_persistent_launch_chunks_and_barrier_timeout(gpu):
+    """The persistent launch runs each snn_step call as one cooperative
+    launch: a run cut into calls of 1, 7 and 250 steps equals the oracle.  Its
+    grid-barrier waits are bounded: with a bound of one poll every CTA but the
+    last to arrive gives up, the launch ends with SNN_E_TIMEOUT, and the
+    context resets and the device answers."""
+    prob = si.vogels_4k(seed=3, n_steps=600)
+    o = oracle_run("v4k_s3", prob)
+    net = gpu.Network(prob, receive=RECV["persistent"], log_capacity=prob.n * 600)
+    try:
+        info = net.info()
+        assert info["persistent"] and info["persist_ctas"] >= 2
+        for k in (1, 7, 250, 342):
+            net.step(k)
+        g = {f: net.read(f) for f in _fields(prob)}
+        g["steps"], g["ids"] = net.spikes()
+        g["counters"] = net.counters()
+    finally:
+        net.close()
+    assert_parity(g, o, prob)
+    net = gpu.Network(prob, receive=RECV["persistent"], log_capacity=prob.n * 600, wait_polls=1)
+    try:
+        net.step(50)
+        with pytest.raises(gpu.SnnError) as e:
+            net.sync()
+        assert e.value.status == -5  # SNN_E_TIMEOUT
+        net.reset()
+        net.step(1)
+        with pytest.raises(gpu.SnnError) as e:
+            net.sync()
+        assert e.value.status == -5
+    finally:
+        net.close()
