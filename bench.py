@@ -587,7 +587,7 @@ def run_ours(args, rank, world, dist):
     deliv_main = delivered_spikes(net, prob, t0, t0 + args.steps)
     # ---- the same window again from a reset, with CUDA events around every
     # kernel (deterministic: the same spikes and events as the timed steps)
-    n_prof = min(args.steps, args.profile_steps)
+    n_prof = args.steps if args.profile_steps <= 0 else min(args.steps, args.profile_steps)
     net.reset()
     net.step(t0)
     net.sync()
@@ -797,8 +797,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="batched_sweep_256")
-    ap.add_argument("--profile-steps", type=int, default=2000,
-                    help="steps of the timed window profiled again from a reset (at most --steps)")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="steps of the timed window profiled again from a reset (0: all of --steps)")
     ap.add_argument("--settle", type=int, default=200,
                     help="untimed steps before the warm-up: the initial transient passes and the delay FIFO fills")
     ap.add_argument("--drift-steps", type=int, default=2000, help="window of the rate / ISI CV drift comparison")
