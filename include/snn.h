@@ -118,7 +118,11 @@ typedef struct {
     uint32_t delay;        /* d >= 1 steps; a spike of step t reaches the update of step t+d */
     uint32_t n_inst;       /* number of network instances, >= 1 */
     uint64_t seed;         /* Philox key word 0 (word 1 is inst_key0 + the instance index) */
-    uint64_t log_capacity; /* spikes the raster log keeps (0: no log) */
+    uint64_t log_capacity; /* spikes the raster log keeps (0: no log), shared out
+                              among the instances in proportion to their
+                              neurons: instance b keeps floor(log_capacity
+                              n_b / N) of its spikes; one that fills its share
+                              sets SNN_E_OVERFLOW */
     uint32_t receive;      /* SNN_RECV_* */
     uint32_t steps_per_graph; /* steps captured per CUDA graph (0: library default) */
     uint32_t tune_steps;   /* bulk-copy receive: at this step and at 8x this step of the
@@ -227,8 +231,9 @@ snn_status snn_sync(snn_ctx* ctx);
 /* Spikes of steps [t0, t1) from the raster log, sorted by (step, global
  * id), written to steps[] and ids[] (each of capacity cap).  *n_out gets the
  * number of such spikes; with cap == 0 only the count is returned, with
- * cap < count SNN_E_OVERFLOW is returned and nothing is written.
- * Synchronises. */
+ * cap < count SNN_E_OVERFLOW is returned and nothing is written.  If an
+ * instance filled its share of the log, *n_out counts the spikes kept and
+ * SNN_E_OVERFLOW is returned.  Synchronises. */
 snn_status snn_read_spikes(snn_ctx* ctx, uint32_t t0, uint32_t t1, uint32_t* steps, uint32_t* ids,
                            uint64_t cap, uint64_t* n_out);
 

@@ -44,6 +44,7 @@ struct snn_ctx {
     uint64_t E = 0;
     std::vector<uint32_t> g_off;   // global instance offsets (n_inst+1)
     std::vector<uint32_t> pbase;   // padded bases (n_inst+1)
+    std::vector<unsigned long long> log_lo, log_n;  // each instance's region of the raster log
     bool vogels = false, stdp = false, w16 = false, stats = false;
     bool lazy = false;             // lazy Update Synapses (SNN_F_LAZY)
     bool generic = false;          // a model of the generic update (snn_models.cuh)
@@ -491,9 +492,8 @@ snn_status init_state(snn_ctx* c)
         CUDA_TRY(c, cudaMemsetAsync(c->net.st_sum, 0, (size_t)c->Np * 8, c->stream));
         CUDA_TRY(c, cudaMemsetAsync(c->net.st_sq, 0, (size_t)c->Np * 8, c->stream));
     }
-    CUDA_TRY(c, cudaMemsetAsync(c->net.count, 0, (size_t)c->cr * 4, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->net.icount, 0, (size_t)c->cr * c->cfg.n_inst * 4, c->stream));
-    CUDA_TRY(c, cudaMemsetAsync(c->net.lbase, 0, (size_t)c->cr * 8, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->net.ilog, 0, 2 * (size_t)c->cfg.n_inst * 8, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->net.inst_spikes, 0, (size_t)c->cfg.n_inst * 8, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->net.tile_ctr, 0, 2 * sizeof(unsigned int), c->stream));
     if (c->persist_bar) CUDA_TRY(c, cudaMemsetAsync(c->persist_bar, 0, 2 * sizeof(unsigned int), c->stream));
@@ -1119,6 +1119,20 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
         if (cfg->model != SNN_VOGELS_CUBA) np = poisson_table(params[b].lambda, &hpois[(size_t)b * kPoissonCap], kPoissonCap);
         hinst[b] = make_inst(params[b], c->pbase[b], c->g_off[b], b * kPoissonCap, np);
     }
+    // the raster log is shared out in proportion to the instances' neurons
+    c->log_lo.assign(cfg->n_inst, 0);
+    c->log_n.assign(cfg->n_inst, 0);
+    {
+        unsigned long long lo = 0;
+        const unsigned long long N = c->g_off[cfg->n_inst];
+        for (uint32_t b = 0; b < cfg->n_inst; ++b) {
+            const unsigned long long share =
+                N ? (unsigned long long)((unsigned __int128)cfg->log_capacity * params[b].n / N) : 0ull;
+            c->log_lo[b] = hinst[b].log_lo = lo;
+            c->log_n[b] = hinst[b].log_n = share;
+            lo += share;
+        }
+    }
     // bucket table of every instance: thresholds below each 2^24 boundary
     std::vector<uint8_t> hstart((size_t)cfg->n_inst * kPoissonBuckets, 0);
     for (uint32_t b = 0; b < cfg->n_inst; ++b) {
@@ -1146,9 +1160,8 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     c->cr = 4;
     while (c->cr < c->D + 2) c->cr <<= 1;
     n.cr = c->cr;
-    n.count = alloc_n<unsigned int>(c, c->cr);
     n.icount = alloc_n<unsigned int>(c, (size_t)c->cr * cfg->n_inst);
-    n.lbase = alloc_n<unsigned long long>(c, c->cr);
+    n.ilog = alloc_n<unsigned long long>(c, 2 * (size_t)cfg->n_inst);
     n.inst_spikes = alloc_n<unsigned long long>(c, cfg->n_inst);
     n.tile_ctr = alloc_n<unsigned int>(c, 2);
     c->ctl = alloc_n<Ctl>(c, 1);
@@ -1160,7 +1173,7 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     n.r = alloc_n<uint8_t>(c, Npz);
     n.acc0 = alloc_n<int32_t>(c, Npz);
     n.q = alloc_n<uint32_t>(c, (size_t)c->D * Npz);
-    bool ok = c->ctl && c->inst && c->inst_of_w32 && c->pois && c->pois_start && n.V && n.r && n.acc0 && n.q && n.count && n.icount && n.lbase &&
+    bool ok = c->ctl && c->inst && c->inst_of_w32 && c->pois && c->pois_start && n.V && n.r && n.acc0 && n.q && n.icount && n.ilog &&
               n.inst_spikes && n.tile_ctr;
     if (c->generic) {
         c->mstate = dev_alloc(c, c->mbytes * Npz);
@@ -1557,45 +1570,60 @@ snn_status snn_read_spikes(snn_ctx* c, uint32_t t0, uint32_t t1, uint32_t* steps
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     Ctl h;
     CUDA_TRY(c, cudaMemcpy(&h, c->ctl, sizeof h, cudaMemcpyDeviceToHost));
-    // logged spikes: the last step's base plus its count (the next step's
-    // update would compute the same)
-    unsigned long long total = 0;
+    // logged spikes of each instance: its count before the last step plus the
+    // last step's queue index (the next step's update would compute the same)
+    const uint32_t B = c->cfg.n_inst;
+    std::vector<unsigned long long> avail(B, 0);
+    bool overflow = false;
     if (h.t > h.t_log0) {
-        unsigned long long lb = 0;
-        unsigned int cnt = 0;
-        CUDA_TRY(c, cudaMemcpy(&lb, c->net.lbase + ((h.t - 1) & (c->cr - 1)), 8, cudaMemcpyDeviceToHost));
-        CUDA_TRY(c, cudaMemcpy(&cnt, c->net.count + ((h.t - 1) & (c->cr - 1)), 4, cudaMemcpyDeviceToHost));
-        total = lb + cnt;
-    }
-    const uint64_t avail = std::min<uint64_t>(total, c->cfg.log_capacity);
-    // the log is in step order (steps append at increasing bases), so the
-    // entries of steps [t0, t1) are one range of it, found by bisection
-    auto first_at = [&](uint64_t t, uint64_t* idx) -> snn_status {
-        uint64_t lo = 0, hi = avail;
-        while (lo < hi) {
-            const uint64_t mid = (lo + hi) / 2;
-            unsigned long long v = 0;
-            CUDA_TRY(c, cudaMemcpy(&v, c->net.log + mid, 8, cudaMemcpyDeviceToHost));
-            if ((v >> 32) < t)
-                lo = mid + 1;
-            else
-                hi = mid;
+        std::vector<unsigned int> ic(B, 0);
+        CUDA_TRY(c, cudaMemcpy(avail.data(), c->net.ilog + (size_t)((h.t - 1) & 1ull) * B, B * 8, cudaMemcpyDeviceToHost));
+        CUDA_TRY(c, cudaMemcpy(ic.data(), c->net.icount + (size_t)((h.t - 1) & (c->cr - 1)) * B, B * 4,
+                               cudaMemcpyDeviceToHost));
+        for (uint32_t b = 0; b < B; ++b) {
+            avail[b] += ic[b];
+            overflow = overflow || avail[b] > c->log_n[b];
+            avail[b] = std::min<unsigned long long>(avail[b], c->log_n[b]);
         }
-        *idx = lo;
-        return SNN_OK;
-    };
-    uint64_t lo = 0, hi = 0;
-    snn_status st = first_at(t0, &lo);
-    if (st == SNN_OK) st = first_at(t1, &hi);
-    if (st != SNN_OK) return st;
-    const uint64_t n = hi > lo ? hi - lo : 0;
+    }
+    // each region is in step order (steps append after the previous ones), so
+    // the entries of steps [t0, t1) are one range of it, found by bisection
+    std::vector<unsigned long long> rng(2 * (size_t)B, 0);
+    {
+        unsigned long long* d_av = alloc_n<unsigned long long>(c, B);
+        unsigned long long* d_rg = alloc_n<unsigned long long>(c, 2 * (size_t)B);
+        cudaError_t e = (d_av && d_rg) ? cudaSuccess : cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_av, avail.data(), B * 8, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) {
+            k_log_ranges<<<grid_for(B, 128), 128, 0, c->stream>>>(c->net, d_av, t0, t1, d_rg);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rng.data(), d_rg, rng.size() * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        dev_free(c, d_av);
+        dev_free(c, d_rg);
+        if (e != cudaSuccess) return fail(c, SNN_E_CUDA, "raster ranges: %s", cudaGetErrorString(e));
+    }
+    uint64_t n = 0;
+    for (uint32_t b = 0; b < B; ++b) n += rng[2 * b + 1] - rng[2 * b];
     *n_out = n;
-    if (total > c->cfg.log_capacity)
-        return fail(c, SNN_E_OVERFLOW, "the spike log overflowed (%llu spikes, capacity %llu)",
-                    (unsigned long long)total, (unsigned long long)c->cfg.log_capacity);
+    if (overflow)
+        return fail(c, SNN_E_OVERFLOW, "the spike log overflowed (an instance filled its share; capacity %llu)",
+                    (unsigned long long)c->cfg.log_capacity);
     if (cap == 0 || n == 0) return SNN_OK;
     if (cap < n) return fail(c, SNN_E_OVERFLOW, "output capacity %llu < %llu spikes", (unsigned long long)cap,
                             (unsigned long long)n);
+    // the ranges in chunks of at most 4,096 entries, one block each
+    std::vector<LogChunk> hc;
+    {
+        unsigned long long dst = 0;
+        for (uint32_t b = 0; b < B; ++b)
+            for (unsigned long long i = rng[2 * b]; i < rng[2 * b + 1]; i += 4096) {
+                const unsigned long long len = std::min<unsigned long long>(4096, rng[2 * b + 1] - i);
+                hc.push_back(LogChunk{c->log_lo[b] + i, dst, (uint32_t)len, b});
+                dst += len;
+            }
+    }
     // keys (step - t0) << 32 | global id, radix-sorted on the device, split
     // into the two output arrays
     const uint64_t t_hi = std::min<uint64_t>(t1, h.t);
@@ -1608,8 +1636,16 @@ snn_status snn_read_spikes(snn_ctx* c, uint32_t t0, uint32_t t1, uint32_t* steps
     void* tmp = nullptr;
     cudaError_t e = cudaSuccess;
     if (ka && kb) {
-        k_raster_keys<<<grid_for(n, 256), 256, 0, c->stream>>>(c->net, c->net.log + lo, n, t0, ka);
-        e = cub::DeviceRadixSort::SortKeys(nullptr, tmp_bytes, db, (int64_t)n, 0, end_bit, c->stream);
+        LogChunk* d_ch = alloc_n<LogChunk>(c, hc.size());
+        e = d_ch ? cudaMemcpyAsync(d_ch, hc.data(), hc.size() * sizeof(LogChunk), cudaMemcpyHostToDevice, c->stream)
+                 : cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) {
+            k_raster_keys<<<(uint32_t)hc.size(), 256, 0, c->stream>>>(c->net, d_ch, t0, ka);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // the chunk list is freed next
+        dev_free(c, d_ch);
+        if (e == cudaSuccess) e = cub::DeviceRadixSort::SortKeys(nullptr, tmp_bytes, db, (int64_t)n, 0, end_bit, c->stream);
         if (e == cudaSuccess) tmp = dev_alloc(c, std::max<size_t>(tmp_bytes, 16));
     }
     if (!ka || !kb || !tmp) {
@@ -1641,10 +1677,8 @@ snn_status snn_log_clear(snn_ctx* c)
     Ctl* d = c->ctl;
     unsigned long long t = 0;
     CUDA_TRY(c, cudaMemcpy(&t, &d->t, 8, cudaMemcpyDeviceToHost));
-    const unsigned long long zero = 0;
     unsigned int err = 0;
     CUDA_TRY(c, cudaMemcpy(&d->t_log0, &t, 8, cudaMemcpyHostToDevice));
-    CUDA_TRY(c, cudaMemcpy(c->net.lbase + (t & (c->cr - 1)), &zero, 8, cudaMemcpyHostToDevice));
     CUDA_TRY(c, cudaMemcpy(&err, &d->err, 4, cudaMemcpyDeviceToHost));
     err &= ~kErrLogOverflow;
     CUDA_TRY(c, cudaMemcpy(&d->err, &err, 4, cudaMemcpyHostToDevice));
@@ -1780,8 +1814,13 @@ snn_status snn_counters(snn_ctx* c, uint64_t* steps, uint64_t* spikes, uint64_t*
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     Ctl h;
     CUDA_TRY(c, cudaMemcpy(&h, c->ctl, sizeof h, cudaMemcpyDeviceToHost));
-    unsigned int last = 0;  // the last step's spikes are folded in by the next update
-    if (h.t > 0) CUDA_TRY(c, cudaMemcpy(&last, c->net.count + ((h.t - 1) & (c->cr - 1)), 4, cudaMemcpyDeviceToHost));
+    unsigned long long last = 0;  // the last step's spikes are folded in by the next update
+    if (h.t > 0) {
+        std::vector<unsigned int> ic(c->cfg.n_inst, 0);
+        CUDA_TRY(c, cudaMemcpy(ic.data(), c->net.icount + (size_t)((h.t - 1) & (c->cr - 1)) * c->cfg.n_inst,
+                               ic.size() * 4, cudaMemcpyDeviceToHost));
+        for (unsigned int x : ic) last += x;
+    }
     if (steps) *steps = h.t;
     if (spikes) *spikes = h.spikes + last;
     if (events) *events = h.events;

@@ -21,6 +21,11 @@
 //              with its own index icount[t % CR][b], so a consumer can take
 //              one network's spikes alone.  With STDP a ring of D spike
 //              bitmasks uint32[D][Np/32] sits beside it (Section III-A-1).
+//   log      : the raster log, (step << 32 | padded id) per spike; instance b
+//              appends to its own region [log_lo_b, log_lo_b + log_n_b) in
+//              step order, a warp's spikes at the instance's logged count
+//              before the step plus the warp's queue position, so filing a
+//              spike takes the one queue-index atomic and no step-wide one.
 //   lazy     : lazy Update Synapses (Section III-A-1): per neuron a 128-bit
 //              spike history hist[2 Np] (bit k: spiked at step t - k; words
 //              2i and 2i+1 hold bits 0..63 and 64..127 of neuron i), a ring
@@ -58,6 +63,7 @@ struct InstDev {
     uint32_t pois_off, pois_n;
     float Pm, Pe, Pi, Pp, Pn, Ap, Am;
     float v_th, v_reset, e_l, v0_lo, v0_span;
+    unsigned long long log_lo, log_n;  // the instance's region of the raster log: first entry, entries
 };
 
 // Device control block: the step counter and the work-queue indices.
@@ -80,9 +86,8 @@ struct Net {
     uint32_t key0;             // Philox key word 1 of instance 0 (instance b uses key0 + b)
     uint32_t pad0;
     uint64_t seed;
-    unsigned int* count;       // |S_t| over all instances at [t % cr]
     unsigned int* icount;      // |S_t| of instance b at [(t % cr) * n_inst + b]
-    unsigned long long* lbase; // log position of S_t's first spike at [t % cr]
+    unsigned long long* ilog;  // spikes of instance b logged before step t, at [(t & 1) * n_inst + b]
     unsigned long long* inst_spikes; // spikes of each instance since the last reset
     unsigned int* tile_ctr;    // tiled receive: next tile to take, at [t & 1]
     const InstDev* inst;

@@ -46,28 +46,80 @@ __device__ __forceinline__ uint32_t poisson_count(const uint32_t* __restrict__ T
     return k;
 }
 
+// Spikes of instance b logged before step t (its raster-log entries of steps
+// [t_log0, t)): the count the bookkeeping of step t-1 kept plus the queue
+// index of step t-1.  Both are final before step t's update starts, so every
+// warp of that update reads the same value while the bookkeeping of step t
+// stores it in the other parity for step t+1.
+__device__ __forceinline__ unsigned long long log_base(const Net& n, unsigned long long t, uint32_t b)
+{
+    if (t <= n.ctl->t_log0) return 0ull;
+    return n.ilog[(size_t)((t - 1) & 1ull) * n.n_inst + b] + n.icount[(size_t)((t - 1) & (n.cr - 1)) * n.n_inst + b];
+}
+
 // Per-step bookkeeping of the previous step, done once per step by the
 // threads gt (grid-wide index) of the step's update (its kernels have
 // finished): fold its queue indices into the counters, clear the next step's
-// indices and the tile counter of the next receive, and set the log position
-// of this step's first spike (the previous step's base plus its count; 0 at
-// the first step of the log).
+// indices and the tile counter of the next receive, and keep each instance's
+// logged count for the next step.
 __device__ __forceinline__ void step_bookkeeping(const Net& n, unsigned long long t, uint32_t gt, bool lazy)
 {
     const uint32_t sn = (uint32_t)((t + 1) & (n.cr - 1));
     if (gt < n.n_inst) {
-        if (t > 0) n.inst_spikes[gt] += n.icount[(size_t)((t - 1) & (n.cr - 1)) * n.n_inst + gt];
+        if (t > 0) {
+            const unsigned int c = n.icount[(size_t)((t - 1) & (n.cr - 1)) * n.n_inst + gt];
+            n.inst_spikes[gt] += c;
+            if (c) atomicAdd(&n.ctl->spikes, (unsigned long long)c);
+        }
         n.icount[(size_t)sn * n.n_inst + gt] = 0;
+        if (n.log_cap) n.ilog[(size_t)(t & 1ull) * n.n_inst + gt] = log_base(n, t, gt);
     }
     if (gt == 0) {
-        if (t > 0) n.ctl->spikes += n.count[(t - 1) & (n.cr - 1)];
-        n.count[sn] = 0;
         n.tile_ctr[(t + 1) & 1ull] = 0;
         if (lazy) n.xcount[(t + 1) & 1ull] = 0;
+    }
+}
+
+// Where a warp's spikes of step t go in the raster log: its instance's
+// logged count before the step (lb) and the instance's log region (lo, cap).
+// Loaded while the warp's queue-index atomic is in flight.
+struct LogSlot {
+    unsigned long long lb, lo, cap;
+};
+
+__device__ __forceinline__ LogSlot log_slot(const Net& n, unsigned long long t, uint32_t b)
+{
+    LogSlot s{0ull, 0ull, 0ull};
+    if (n.log_cap) {
+        s.lb = log_base(n, t, b);
+        s.lo = __ldg(&n.inst[b].log_lo);
+        s.cap = __ldg(&n.inst[b].log_n);
+    }
+    return s;
+}
+
+// A warp's spikes into the queue and the raster log: the lane's spikes (bit
+// k of spk: neuron id0 + k) at offset off of the warp's range, which starts
+// at wbase in instance b's region of queue slot slot_q and at the same place
+// after the instance's logged spikes in its log region.
+__device__ __forceinline__ void file_spikes(const Net& n, unsigned long long t, uint32_t id0, uint32_t spk, uint32_t off,
+                                            uint32_t slot_q, uint32_t pbase, uint32_t wbase, const LogSlot& L)
+{
+    uint32_t* q = n.q + (size_t)slot_q * n.Np + pbase + wbase + off;
+    const unsigned long long lp = L.lb + wbase + off;
+    uint32_t m = spk, k = 0;
+    while (m) {
+        const int bit = __ffs(m) - 1;
+        m &= m - 1;
+        const uint32_t id = id0 + bit;
+        q[k] = id;
         if (n.log_cap) {
-            const unsigned long long tp = t - 1;
-            n.lbase[t & (n.cr - 1)] = (t > n.ctl->t_log0) ? n.lbase[tp & (n.cr - 1)] + n.count[tp & (n.cr - 1)] : 0ull;
+            if (lp + k < L.cap)
+                n.log[L.lo + lp + k] = (t << 32) | id;
+            else
+                atomicOr(&n.ctl->err, kErrLogOverflow);
         }
+        ++k;
     }
 }
 
@@ -314,7 +366,7 @@ __device__ __forceinline__ void update_neurons(const Net& n, unsigned long long 
         }
     }
     // warp compaction: exclusive scan of the per-thread spike counts, one
-    // atomicAdd on the instance's queue index and one on the step's total
+    // atomicAdd on the instance's queue index
     const uint32_t c = __popc(spk);
     uint32_t incl = c;
 #pragma unroll
@@ -323,12 +375,9 @@ __device__ __forceinline__ void update_neurons(const Net& n, unsigned long long 
         if (lane >= (uint32_t)o) incl += v;
     }
     const uint32_t total = __shfl_sync(kFull, incl, 31);
-    uint32_t wbase = 0, lpos = 0;
-    if (lane == 31 && total) {
-        wbase = atomicAdd(&n.icount[(size_t)slot_c * n.n_inst + b], total);
-        lpos = atomicAdd(&n.count[slot_c], total);
-    }
-    // the state goes back while the atomics are in flight
+    uint32_t wbase = 0;
+    if (lane == 31 && total) wbase = atomicAdd(&n.icount[(size_t)slot_c * n.n_inst + b], total);
+    // the state goes back while the atomic is in flight
     if (have) {
 #pragma unroll
         for (int h = 0; h < NPT / 4; ++h) {
@@ -338,34 +387,9 @@ __device__ __forceinline__ void update_neurons(const Net& n, unsigned long long 
         }
     }
     if (total == 0) return;
+    const LogSlot L = spk ? log_slot(n, t, b) : LogSlot{0ull, 0ull, 0ull};
     wbase = __shfl_sync(kFull, wbase, 31);
-    lpos = __shfl_sync(kFull, lpos, 31);
-    if (!spk) return;
-    // log position of this step's first spike: the previous step's base plus
-    // its count (0 at the first step of the log)
-    unsigned long long lb = 0;
-    if (n.log_cap) {
-        const unsigned long long tp = t - 1;
-        lb = (t > n.ctl->t_log0) ? n.lbase[tp & (n.cr - 1)] + n.count[tp & (n.cr - 1)] : 0ull;
-        lb += lpos;
-    }
-    const uint32_t off = incl - c;
-    uint32_t* q = n.q + (size_t)slot_q * n.Np + pbase + wbase + off;
-    uint32_t m = spk, k = 0;
-    while (m) {
-        const int bit = __ffs(m) - 1;
-        m &= m - 1;
-        const uint32_t id = id0 + bit;
-        q[k] = id;
-        if (n.log_cap) {
-            const unsigned long long lp = lb + off + k;
-            if (lp < n.log_cap)
-                n.log[lp] = (t << 32) | id;
-            else
-                atomicOr(&n.ctl->err, kErrLogOverflow);
-        }
-        ++k;
-    }
+    if (spk) file_spikes(n, t, id0, spk, incl - c, slot_q, pbase, wbase, L);
 }
 
 template <int MODEL, int SYN, bool STATS, int NPT>
@@ -380,16 +404,43 @@ __global__ void __launch_bounds__(256) k_update(Net n)
     update_neurons<MODEL, SYN, STATS, NPT>(n, t, g, n.acc0);
 }
 
-// Raster readout: log entries (step << 32 | padded id) -> sortable keys
-// (step - t0) << 32 | global id.
-__global__ void k_raster_keys(Net n, const unsigned long long* __restrict__ log, uint64_t count, uint64_t t0,
-                              unsigned long long* __restrict__ keys)
+// Raster readout: chunks of instances' log regions (a chunk: len entries
+// from log index src, instance inst, written at key index dst) -> sortable
+// keys (step - t0) << 32 | global id, one block per chunk.
+struct LogChunk {
+    unsigned long long src, dst;
+    uint32_t len, inst;
+};
+
+__global__ void k_raster_keys(Net n, const LogChunk* __restrict__ chunks, uint64_t t0, unsigned long long* __restrict__ keys)
 {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
-        const unsigned long long v = log[i];
-        const uint32_t pid = (uint32_t)v;
-        const InstDev& I = n.inst[n.inst_of_w32[pid >> 5]];
-        keys[i] = (((v >> 32) - t0) << 32) | (unsigned long long)(pid - I.pbase + I.goff);
+    const LogChunk C = chunks[blockIdx.x];
+    const uint32_t pbase = n.inst[C.inst].pbase, goff = n.inst[C.inst].goff;
+    for (uint32_t i = threadIdx.x; i < C.len; i += blockDim.x) {
+        const unsigned long long v = n.log[C.src + i];
+        keys[C.dst + i] = (((v >> 32) - t0) << 32) | (unsigned long long)((uint32_t)v - pbase + goff);
+    }
+}
+
+// Per instance b, the first entries of its log region (avail[b] entries in
+// step order) at steps >= t0 and >= t1, by bisection: out[2b], out[2b+1].
+__global__ void k_log_ranges(Net n, const unsigned long long* __restrict__ avail, uint64_t t0, uint64_t t1,
+                             unsigned long long* __restrict__ out)
+{
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < n.n_inst; b += gridDim.x * blockDim.x) {
+        const unsigned long long lo0 = n.inst[b].log_lo, m = avail[b];
+        for (int e = 0; e < 2; ++e) {
+            const uint64_t t = e ? t1 : t0;
+            unsigned long long lo = 0, hi = m;
+            while (lo < hi) {
+                const unsigned long long mid = (lo + hi) / 2;
+                if ((n.log[lo0 + mid] >> 32) < t)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            out[2 * b + e] = lo;
+        }
     }
 }
 

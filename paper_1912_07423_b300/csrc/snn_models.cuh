@@ -159,19 +159,7 @@ __global__ void __launch_bounds__(256) k_update_model(Net n, typename M::neuron*
 {
     constexpr int NPT = kUpdateNeurons;
     const unsigned long long t = n.ctl->t + n.k;
-    {  // per-step bookkeeping of the previous step, as in k_update
-        const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
-        const uint32_t sn = (uint32_t)((t + 1) & (n.cr - 1));
-        if (gt < n.n_inst) {
-            if (t > 0) n.inst_spikes[gt] += n.icount[(size_t)((t - 1) & (n.cr - 1)) * n.n_inst + gt];
-            n.icount[(size_t)sn * n.n_inst + gt] = 0;
-        }
-        if (gt == 0) {
-            if (t > 0) n.ctl->spikes += n.count[(t - 1) & (n.cr - 1)];
-            n.count[sn] = 0;
-            n.tile_ctr[(t + 1) & 1ull] = 0;
-        }
-    }
+    step_bookkeeping(n, t, blockIdx.x * blockDim.x + threadIdx.x, false);  // of the previous step, as in k_update
     if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const uint32_t G = n.Np / NPT;
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -225,10 +213,6 @@ __global__ void __launch_bounds__(256) k_update_model(Net n, typename M::neuron*
     const uint32_t lane = lane_id();
     const uint32_t slot_q = (uint32_t)(t % n.D);
     const uint32_t slot_c = (uint32_t)(t & (n.cr - 1));
-    if (blockIdx.x == 0 && threadIdx.x == 0 && n.log_cap) {
-        const unsigned long long tp = t - 1;
-        n.lbase[slot_c] = (t > n.ctl->t_log0) ? n.lbase[tp & (n.cr - 1)] + n.count[tp & (n.cr - 1)] : 0ull;
-    }
     const uint32_t c = __popc(spk);
     uint32_t incl = c;
 #pragma unroll
@@ -238,37 +222,11 @@ __global__ void __launch_bounds__(256) k_update_model(Net n, typename M::neuron*
     }
     const uint32_t total = __shfl_sync(kFull, incl, 31);
     if (total == 0) return;
-    uint32_t wbase = 0, lpos = 0;
-    if (lane == 31) {
-        wbase = atomicAdd(&n.icount[(size_t)slot_c * n.n_inst + b], total);
-        lpos = atomicAdd(&n.count[slot_c], total);
-    }
+    uint32_t wbase = 0;
+    if (lane == 31) wbase = atomicAdd(&n.icount[(size_t)slot_c * n.n_inst + b], total);
+    const LogSlot L = spk ? log_slot(n, t, b) : LogSlot{0ull, 0ull, 0ull};
     wbase = __shfl_sync(kFull, wbase, 31);
-    lpos = __shfl_sync(kFull, lpos, 31);
-    if (!spk) return;
-    unsigned long long lb = 0;
-    if (n.log_cap) {
-        const unsigned long long tp = t - 1;
-        lb = (t > n.ctl->t_log0) ? n.lbase[tp & (n.cr - 1)] + n.count[tp & (n.cr - 1)] : 0ull;
-        lb += lpos;
-    }
-    const uint32_t off = incl - c;
-    uint32_t* q = n.q + (size_t)slot_q * n.Np + pbase + wbase + off;
-    uint32_t m = spk, k = 0;
-    while (m) {
-        const int bit = __ffs(m) - 1;
-        m &= m - 1;
-        const uint32_t id = id0 + bit;
-        q[k] = id;
-        if (n.log_cap) {
-            const unsigned long long lp = lb + off + k;
-            if (lp < n.log_cap)
-                n.log[lp] = (t << 32) | id;
-            else
-                atomicOr(&n.ctl->err, kErrLogOverflow);
-        }
-        ++k;
-    }
+    if (spk) file_spikes(n, t, id0, spk, incl - c, slot_q, pbase, wbase, L);
 }
 
 // ---------------------------------------------------------------------------
