@@ -201,10 +201,14 @@ class Network:
     its model may be VOGELS, BRUNEL or a generic-update model (MODEL_RELAY,
     MODEL_BRUNEL_LIF), whose state records ``read("model")`` returns.
     w16: 16-bit weight codes (else binary32).  receive: RECV_*.
-    packed: let the tiled receive read 4-byte packed edges where it can.
+    log_capacity: raster-log entries (default 64 per neuron, at least 65,536),
+    shared out among the instances in proportion to their neurons.
+    packed: let the receives read compressed edges (row weights, 16-bit
+    target offsets, packed offset + code) where they can.
     lazy, lazy_fifo: with STDP, the lazy Update Synapses and its history
     length in steps (0: 128).  stats: keep spike counts and ISI moments.
-    wait_polls: bound of the bulk receive's mbarrier waits (0: the default).
+    wait_polls: bound of the bulk receive's mbarrier waits and of the
+    persistent launch's grid barrier (0: the defaults).
     inst_key0: Philox instance key of the first instance (to re-run network b
     of a batch alone with its own random numbers, pass b).
     serial: run Update Neurons and Receive Spikes as separate kernels even

@@ -36,6 +36,7 @@ struct snn_ctx {
     cudaStream_t stream = nullptr;   // user stream (may be the legacy default)
     cudaStream_t cap_stream = nullptr;
     cudaStream_t side = nullptr;       // the per-step plan, beside the update when the delay allows
+    int plan_priority = 0;             // the greatest stream priority: the plan's block goes before the update's
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
 
@@ -339,7 +340,7 @@ snn_status enqueue_step(snn_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr, u
     if (fork) {
         CUDA_TRY(c, cudaEventRecord(c->ev_fork, s));
         CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-        CUDA_TRY(c, enqueue_tiled_plan(c->tiled, n, c->side));
+        CUDA_TRY(c, enqueue_tiled_plan(c->tiled, n, c->side, c->plan_priority));
         CUDA_TRY(c, cudaEventRecord(c->ev_join, c->side));
     }
     // eager plasticity: depression before the update, potentiation after it;
@@ -422,7 +423,7 @@ snn_status capture(snn_ctx* c, uint32_t steps, cudaGraphExec_t* out)
         return st;
     }
     if (e != cudaSuccess) return fail(c, SNN_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(out, g, 0);
+    e = cudaGraphInstantiate(out, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(c, SNN_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
     return SNN_OK;
@@ -1097,8 +1098,14 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
         c->g_off[b + 1] = c->g_off[b] + params[b].n;
         c->pbase[b + 1] = c->pbase[b] + (params[b].n + kPad - 1) / kPad * kPad;
     }
+    int prio_low = 0, prio_high = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
+        cudaGetLastError();
+        prio_high = 0;
+    }
+    c->plan_priority = prio_high;
     if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();

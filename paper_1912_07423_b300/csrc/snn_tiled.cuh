@@ -110,7 +110,8 @@ constexpr uint32_t kMaxParts = 255;
 constexpr uint32_t kMergeChunk = 4096;
 constexpr int kPlanThreads = 1024;
 constexpr uint32_t kPlanMaxTiles = 4096;
-constexpr uint32_t kRankSortMax = 1024;  // up to this many tiles the plan sorts by rank, above by a bitonic network
+constexpr uint32_t kRankSortMax = 1024;  // most keys the rank sort's per-thread slots hold
+constexpr uint32_t kRankSortUse = 128;   // up to this many tiles the plan sorts by rank, above by a bitonic network
 constexpr float kItemsPerCta = 1.5f;     // per-step plan: items per CTA at the target size
 constexpr float kSpikeCost = 8.0f;     // fixed work of one arriving spike, in edges
 constexpr uint32_t kMaxLogPieces = 3;
@@ -427,7 +428,7 @@ __device__ __forceinline__ void plan_step(const Net& n, unsigned long long t, co
     }
     __syncthreads();
     const uint32_t n_act = s_act;  // the active keys sort first
-    if (n_pad <= kRankSortMax) {
+    if (n_pad <= kRankSortUse) {
         // rank of key k = keys below it; g threads per key, each over n_pad / g keys
         uint32_t* rank = at;
         for (uint32_t k = threadIdx.x; k < n_pad; k += blockDim.x) rank[k] = 0;
@@ -886,12 +887,21 @@ inline snn_status tiled_plan(TiledPlan& P, const Net& n, const snn_params* param
 }
 
 // The per-step plan of one step.
-inline cudaError_t enqueue_tiled_plan(const TiledPlan& P, const Net& n, cudaStream_t s)
+inline cudaError_t enqueue_tiled_plan(const TiledPlan& P, const Net& n, cudaStream_t s, int priority = 0)
 {
     uint32_t n_pad = 1;
     while (n_pad < P.n_tiles) n_pad <<= 1;
-    k_plan<<<1, kPlanThreads, plan_smem(n_pad), s>>>(n, P.tiles, P.n_tiles, P.step, P.grid, P.cap, P.items_cap);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(kPlanThreads);
+    cfg.dynamicSmemBytes = plan_smem(n_pad);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = priority;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_plan, n, (const TileDev*)P.tiles, P.n_tiles, P.step, P.grid, P.cap, P.items_cap);
 }
 
 // The receive of one step under its plan; wm: the edge layout to read; pdl:
