@@ -445,7 +445,7 @@ snn_status check_device_errors(snn_ctx* c)
     if (err & kErrPlan) return fail(c, SNN_E_OVERFLOW, "the receive plan of a step did not fit its buffer");
     if (err & kErrLazyAge) return fail(c, SNN_E_STATE, "a lazily updated row outlived its spike history");
     if (err & kErrLogOverflow)
-        return fail(c, SNN_E_OVERFLOW, "the spike log is full (log_capacity = %llu)",
+        return fail(c, SNN_E_OVERFLOW, "the spike log is full (an instance filled its share of log_capacity = %llu)",
                     (unsigned long long)c->cfg.log_capacity);
     return SNN_OK;
 }
