@@ -729,7 +729,9 @@ inline void tiled_free(TiledPlan& P, const std::function<void(void*)>& release)
 // true): the buffers k_plan fills, sized for the most it can write --
 // sum_k P_k <= kItemsPerCta CTAs + tiles, since P_k <= w_k / target + 1, and
 // likewise for the partial words.  Needs sorted rows when an instance has
-// several tiles.
+// several tiles.  A tile's row segments are cut into 2^lpieces pieces only
+// where the mean segment reaches 1.5 piece_edges (and again at each doubling),
+// so that every unit keeps a warp busy for a few rounds of loads.
 inline snn_status tiled_plan(TiledPlan& P, const Net& n, const snn_params* params, const uint32_t* pbase,
                              uint32_t n_inst, int channels, uint32_t max_len, const double* work,
                              const uint64_t* inst_edges, int sms, const std::function<void*(size_t)>& alloc,
@@ -765,8 +767,7 @@ inline snn_status tiled_plan(TiledPlan& P, const Net& n, const snn_params* param
             d.ntiles = T;
             d.nparts = 1;
             d.pbase = pbase[b];
-            // mean segment of a row in this tile, plus the fixed cost of a spike;
-            // pieces of about one vector pass each
+            // mean segment of a row in this tile, plus the fixed cost of a spike
             const double mseg = params[b].n ? (double)inst_edges[b] / params[b].n * d.len / npad : 0.0;
             d.seg = (float)mseg + kSpikeCost;
             d.lpieces = 0;

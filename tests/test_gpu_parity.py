@@ -271,6 +271,49 @@ def test_log_overflow_is_reported(gpu):
     net.close()
 
 
+def test_raster_log_regions(gpu):
+    """The raster log keeps each instance's spikes in its own region, its
+    share of log_capacity by neurons: step ranges of an uneven batch read back
+    as the oracle's raster cut to them, after snn_log_clear the log restarts
+    at the current step, and when instances fill their shares the readout
+    counts the spikes kept (each instance's own up to its share) and reports
+    SNN_E_OVERFLOW."""
+    import ctypes
+    prob = si.batched_sweep(n_nets=12, base_seed=3, n_steps=1500, n_lo=37, n_hi=6000)
+    o = oracle_run("batch12", prob)
+    net = gpu.Network(prob, receive=RECV["tiled"], log_capacity=prob.n * 1500)
+    try:
+        net.step(600)
+        for t0, t1 in [(0, 600), (0, 1), (137, 138), (250, 599), (599, 10_000), (600, 700)]:
+            s, i = net.spikes(t0, t1)
+            m = (o["steps"] >= t0) & (o["steps"] < min(t1, 600))
+            assert np.array_equal(s, o["steps"][m]) and np.array_equal(i, o["ids"][m]), (t0, t1)
+        net.log_clear()
+        net.step(400)
+        s, i = net.spikes()
+        m = (o["steps"] >= 600) & (o["steps"] < 1000)
+        assert len(i) > 0 and np.array_equal(s, o["steps"][m]) and np.array_equal(i, o["ids"][m])
+    finally:
+        net.close()
+    cap = prob.n * 15  # 15 spikes per neuron: the busier instances (up to 27) overflow within 1,500 steps
+    sizes = np.diff(prob.inst_off.astype(np.int64))
+    share = cap * sizes // int(sizes.sum())
+    per_inst = np.bincount(np.searchsorted(prob.inst_off[1:], o["ids"], side="right"), minlength=len(sizes))
+    kept = np.minimum(per_inst, share)
+    assert (per_inst > share).any() and (per_inst < share).any()
+    net = gpu.Network(prob, receive=RECV["tiled"], log_capacity=cap)
+    try:
+        net.step(1500)
+        with pytest.raises(gpu.SnnError) as ei:
+            net.sync()
+        assert ei.value.status == -4
+        n = ctypes.c_uint64(0)
+        st = net.lib.snn_read_spikes(net.ctx, 0, 2**32 - 1, None, None, 0, ctypes.byref(n))
+        assert st == -4 and n.value == int(kept.sum())
+    finally:
+        net.close()
+
+
 def test_reset_repeats_the_run(gpu):
     prob = si.brunel_stdp_100k(seed=5, n_steps=600, n=2000, k=200)
     net = gpu.Network(prob, receive=RECV["tiled"], log_capacity=1 << 20)
