@@ -751,13 +751,15 @@ def run_ours(args, rank, world, dist):
         del net
         torch.cuda.empty_cache()
         n_all = t0 + args.steps
-        h2d = prob.row_off.nbytes + prob.tgt.nbytes + prob.w.nbytes
+        w_row = prob.row_weights()  # the Network above loaded the graph from one weight per row when it could
+        h2d = prob.row_off.nbytes + prob.tgt.nbytes + (w_row.nbytes if w_row is not None else prob.w.nbytes)
         d2h = 8 * int(c["spikes"])
         out["e2e"] = {"value": sum_over_ranks(c["events"]) / max_over_ranks(t_e2e), "unit": "synaptic events/s",
                       "seconds": t_e2e, "steps": n_all, "h2d_bytes_per_step": h2d / n_all,
                       "d2h_bytes_per_step": d2h / n_all,
-                      "includes": "snn_create + snn_build_graph from host arrays + snn_step(settle + warm-up + K) "
-                                  "+ snn_read_spikes",
+                      "includes": "snn_create + " + ("snn_build_graph_rows (targets, one weight per row)" if w_row is not None
+                                                     else "snn_build_graph (targets, weight per synapse)")
+                                  + " from host arrays + snn_step(settle + warm-up + K) + snn_read_spikes",
                       "parts": parts}
 
     # ---- binary32 lattice run against the binary64 float-weight oracle

@@ -201,6 +201,16 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
  * (the paper's Init stage, Fig. 1) and the step counter is 0. */
 snn_status snn_build_graph(snn_ctx* ctx, const uint64_t* row_off, const uint32_t* tgt, const int32_t* w_q);
 
+/* snn_build_graph for a graph whose rows each carry one weight, the
+ * population-typed synapses of Table 2 (Section III-A-2: the Vogels and
+ * Brunel networks store no weight per synapse): w_row[N] is the weight of
+ * every synapse of row j, in lattice units.  The result is that of
+ * snn_build_graph with w_q[e] = w_row[j] for e in [row_off[j], row_off[j+1]),
+ * including what snn_read_state(SNN_FIELD_W) returns, but only the targets
+ * and N weights cross the bus.  The caller vouches that the rows are of
+ * that form; the same argument checks apply otherwise. */
+snn_status snn_build_graph_rows(snn_ctx* ctx, const uint64_t* row_off, const uint32_t* tgt, const int32_t* w_row);
+
 /* (Re)initialise the neuron state N_0 and restore the weights loaded by
  * snn_build_graph; the step counter returns to 0 and the log is cleared. */
 snn_status snn_reset(snn_ctx* ctx);

@@ -88,6 +88,7 @@ def load():
             sigs = {
                 "snn_create": (S, [ctypes.POINTER(Config), _vp, ctypes.POINTER(Device), ctypes.POINTER(_vp)]),
                 "snn_build_graph": (S, [_vp, _vp, _vp, _vp]),
+                "snn_build_graph_rows": (S, [_vp, _vp, _vp, _vp]),
                 "snn_reset": (S, [_vp]),
                 "snn_step": (S, [_vp, ctypes.c_uint32]),
                 "snn_sync": (S, [_vp]),
@@ -119,7 +120,7 @@ def load():
 
 
 def exported_symbols() -> list:
-    return ["snn_create", "snn_build_graph", "snn_reset", "snn_step", "snn_step_profiled", "snn_sync",
+    return ["snn_create", "snn_build_graph", "snn_build_graph_rows", "snn_reset", "snn_step", "snn_step_profiled", "snn_sync",
             "snn_read_spikes",
             "snn_log_clear", "snn_read_state", "snn_write_state", "snn_counters", "snn_stats", "snn_stats_clear",
             "snn_get_info", "snn_rate_cv_static", "snn_expand_jobs", "snn_last_error", "snn_status_string",
@@ -247,7 +248,11 @@ class Network:
         self.ctx = ctx
         self.n = int(problem.inst_off[-1]) if problem.inst_off is not None else sum(i.n for i in problem.instances)
         if build_graph:
-            self.build_graph(problem.row_off, problem.tgt, problem.w)
+            w_row = problem.row_weights() if hasattr(problem, "row_weights") else None
+            if w_row is not None:
+                self.build_graph_rows(problem.row_off, problem.tgt, w_row)
+            else:
+                self.build_graph(problem.row_off, problem.tgt, problem.w)
 
     # -- plumbing -----------------------------------------------------------
     def _check(self, st: int, what: str):
@@ -280,6 +285,16 @@ class Network:
         self.n_edges = int(ro[-1])
         self._check(self.lib.snn_build_graph(self.ctx, ro.ctypes.data, tg.ctypes.data if tg.size else None,
                                              wq.ctypes.data if wq.size else None), "snn_build_graph")
+
+    def build_graph_rows(self, row_off, tgt, w_row):
+        """build_graph for rows that each carry one weight: w_row[j] for every
+        synapse of row j (only the targets and one weight per row are copied)."""
+        ro = np.ascontiguousarray(row_off, dtype=np.uint64)
+        tg = np.ascontiguousarray(tgt, dtype=np.uint32)
+        wr = np.ascontiguousarray(w_row, dtype=np.int32)
+        self.n_edges = int(ro[-1])
+        self._check(self.lib.snn_build_graph_rows(self.ctx, ro.ctypes.data, tg.ctypes.data if tg.size else None,
+                                                  wr.ctypes.data if wr.size else None), "snn_build_graph_rows")
 
     def reset(self):
         self._check(self.lib.snn_reset(self.ctx), "snn_reset")

@@ -1252,7 +1252,9 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     return SNN_OK;
 }
 
-snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* tgt_h, const int32_t* w_q)
+// snn_build_graph with one weight per edge (w_q) or per row (w_row).
+snn_status build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* tgt_h, const int32_t* w_q,
+                       const int32_t* w_row)
 {
     if (!c) return SNN_E_ARG;
     if (!row_off) return fail(c, SNN_E_ARG, "row_off is NULL");
@@ -1261,7 +1263,7 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
     for (uint32_t j = 0; j < N; ++j)
         if (row_off[j + 1] < row_off[j]) return fail(c, SNN_E_ARG, "row_off decreases at row %u", j);
     const uint64_t E = row_off[N];
-    if (E && (!tgt_h || !w_q)) return fail(c, SNN_E_ARG, "tgt/w_q is NULL");
+    if (E && (!tgt_h || (!w_q && !w_row))) return fail(c, SNN_E_ARG, "tgt/w_q is NULL");
     if (c->stdp && E >= (1ull << 32)) return fail(c, SNN_E_ARG, "STDP needs fewer than 2^32 edges");
 
     // drop a previous graph
@@ -1348,7 +1350,21 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
     CUDA_TRY(c, cudaMemcpyAsync(dnexc, hnexc.data(), hnexc.size() * 4, cudaMemcpyHostToDevice, s));
     if (E) {
         snn_status up = upload(c, c->tgt, tgt_h, E * 4, s);
-        if (up == SNN_OK) up = upload(c, wtmp, w_q, E * 4, s);
+        if (up == SNN_OK && w_q) up = upload(c, wtmp, w_q, E * 4, s);
+        if (up == SNN_OK && !w_q) {  // one weight per row: spread over the row's edges on the device
+            int32_t* dwr = alloc_n<int32_t>(c, N);
+            if (!dwr) {
+                up = fail(c, SNN_E_NOMEM, "row weights");
+            } else {
+                up = upload(c, dwr, w_row, (size_t)N * 4, s);
+                if (up == SNN_OK) {
+                    k_spread_row_weights<<<(uint32_t)sm_count() * 16, 256, 0, s>>>(c->roff, dsrc, dwr, Np, wtmp);
+                    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+                        up = fail(c, SNN_E_CUDA, "row weights");
+                }
+                dev_free(c, dwr);
+            }
+        }
         if (up != SNN_OK) {
             cleanup_tmp();
             return up;
@@ -1486,6 +1502,17 @@ snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* 
     if (st != SNN_OK) return st;
     CUDA_TRY(c, cudaStreamSynchronize(s));
     return SNN_OK;
+}
+
+snn_status snn_build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* tgt, const int32_t* w_q)
+{
+    return build_graph(c, row_off, tgt, w_q, nullptr);
+}
+
+snn_status snn_build_graph_rows(snn_ctx* c, const uint64_t* row_off, const uint32_t* tgt, const int32_t* w_row)
+{
+    if (c && c->N && !w_row) return fail(c, SNN_E_ARG, "w_row is NULL");
+    return build_graph(c, row_off, tgt, nullptr, w_row);
 }
 
 snn_status snn_reset(snn_ctx* c)

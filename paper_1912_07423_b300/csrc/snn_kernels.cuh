@@ -918,6 +918,23 @@ __global__ void k_init_state(Net n, int vogels, int stdp, int lazy)
 // they stay inside the source's instance), picks the row's weight shift and
 // writes the stored weights.
 // ---------------------------------------------------------------------------
+// One weight per row spread over the row's edges: w[e] = w_row[row_src[pj]]
+// for the edges e of padded row pj (row_src: the global id of a padded
+// row, ~0 for padding, whose rows are empty).  A warp per row.
+__global__ void k_spread_row_weights(const uint64_t* __restrict__ roff, const uint32_t* __restrict__ row_src,
+                                     const int32_t* __restrict__ w_row, uint32_t Np, int32_t* __restrict__ w)
+{
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t pj = warp; pj < Np; pj += nwarps) {
+        const uint64_t beg = roff[pj], end = roff[pj + 1];
+        if (beg == end) continue;
+        const int32_t x = w_row[row_src[pj]];
+        for (uint64_t e = beg + lane; e < end; e += 32) w[e] = x;
+    }
+}
+
 // The weight of every row whose edges all carry the same 16-bit code:
 // roww[pj] = code << shift (0 for an empty row); *mixed is set when some row
 // carries two or more codes.  A warp per row.

@@ -55,6 +55,8 @@ def _load():
             lib.gen_fixed_indegree.argtypes = [u64, u32, u32, u32, u32, u32, u32, u64, vp, vp, ctypes.c_int]
             lib.gen_fill_weights.restype = None
             lib.gen_fill_weights.argtypes = [vp, u32, u32, i32, i32, vp]
+            lib.gen_row_weights.restype = ctypes.c_int
+            lib.gen_row_weights.argtypes = [vp, u32, vp, vp, ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -124,6 +126,9 @@ class Problem:
     row_off: np.ndarray = None    # uint64 [N+1]
     tgt: np.ndarray = None        # uint32 [E] global ids
     w: np.ndarray = None          # int32 [E] lattice units
+    # one weight per row, with the weight array it was read from (row_weights)
+    _w_row: np.ndarray = dataclasses.field(default=None, repr=False, compare=False)
+    _w_row_of: object = dataclasses.field(default=None, repr=False, compare=False)
 
     @property
     def n(self) -> int:
@@ -132,6 +137,24 @@ class Problem:
     @property
     def n_edges(self) -> int:
         return int(self.row_off[-1])
+
+    def row_weights(self):
+        """int32 [N]: the weight every synapse of row j carries, when each
+        row carries one (the recipes here: one weight per source
+        population), else None.  Read once per weight array: assign a new
+        `w` rather than changing it in place."""
+        if self.w is None or self.row_off is None:
+            return None
+        if self._w_row_of is self.w:
+            return self._w_row
+        n = len(self.row_off) - 1
+        out = np.zeros(max(n, 1), dtype=np.int32)[:n]
+        w = np.ascontiguousarray(self.w, dtype=np.int32)
+        ro = np.ascontiguousarray(self.row_off, dtype=np.uint64)
+        ok = _load().gen_row_weights(ro.ctypes.data, n, w.ctypes.data if w.size else None, out.ctypes.data,
+                                     max(1, len(os.sched_getaffinity(0))))
+        self._w_row, self._w_row_of = (out if ok else None), self.w
+        return self._w_row
 
     def w_mV(self) -> np.ndarray:
         """Unquantised weights (mV, float64) for the binary64 comparison."""
@@ -182,7 +205,15 @@ def build_graph(prob: Problem, threads: int | None = None, inst_index0: int = 0)
                              w.ctypes.data)
         ebase += counts[b]
     assert int(row_off[N]) == E
+    # every row carries its source population's weight (gen_fill_weights)
+    w_row = np.zeros(N, dtype=np.int32)
+    for b, inst in enumerate(prob.instances):
+        lo = int(inst_off[b])
+        w_row[lo:lo + inst.n_exc] = inst.w_exc_q
+        w_row[lo + inst.n_exc:lo + inst.n] = inst.w_inh_q
+    w_row[np.diff(row_off) == 0] = 0
     prob.inst_off, prob.row_off, prob.tgt, prob.w = inst_off, row_off, tgt, w
+    prob._w_row, prob._w_row_of = w_row, w
     return prob
 
 

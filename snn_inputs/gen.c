@@ -273,3 +273,68 @@ void gen_fill_weights(const uint64_t* row_off, uint32_t n, uint32_t n_exc, int32
         for (uint64_t e = row_off[j]; e < row_off[j + 1]; ++e) w[e] = v;
     }
 }
+
+/* ------------------------------------------------------------------------
+ * Row weights: out[j] = the weight every synapse of row j carries (0 for an
+ * empty row).  Returns 1 when every row carries one weight, else 0 (out is
+ * then incomplete).  Rows are split among `threads` workers.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    const uint64_t* row_off;
+    const int32_t* w;
+    int32_t* out;
+    uint32_t j0, j1;
+    int ok;
+} rw_job;
+
+static void* rw_worker(void* arg)
+{
+    rw_job* J = (rw_job*)arg;
+    J->ok = 1;
+    for (uint32_t j = J->j0; j < J->j1; ++j) {
+        const uint64_t b = J->row_off[j], e = J->row_off[j + 1];
+        const int32_t x = b < e ? J->w[b] : 0;
+        for (uint64_t k = b + 1; k < e; ++k)
+            if (J->w[k] != x) {
+                J->ok = 0;
+                return NULL;
+            }
+        J->out[j] = x;
+    }
+    return NULL;
+}
+
+int gen_row_weights(const uint64_t* row_off, uint32_t n, const int32_t* w, int32_t* out, int threads)
+{
+    const uint32_t T = threads < 1 ? 1u : (uint32_t)threads;
+    rw_job* jobs = (rw_job*)calloc(T, sizeof(rw_job));
+    pthread_t* th = (pthread_t*)calloc(T, sizeof(pthread_t));
+    int* started = (int*)calloc(T, sizeof(int));
+    if (!jobs || !th || !started) {
+        free(jobs);
+        free(th);
+        free(started);
+        return 0;
+    }
+    for (uint32_t t = 0; t < T; ++t) {
+        jobs[t].row_off = row_off;
+        jobs[t].w = w;
+        jobs[t].out = out;
+        jobs[t].j0 = (uint32_t)((uint64_t)n * t / T);
+        jobs[t].j1 = (uint32_t)((uint64_t)n * (t + 1) / T);
+        if (t > 0 && pthread_create(&th[t], NULL, rw_worker, &jobs[t]) == 0) started[t] = 1;
+    }
+    rw_worker(&jobs[0]);
+    int ok = jobs[0].ok;
+    for (uint32_t t = 1; t < T; ++t) {
+        if (started[t])
+            pthread_join(th[t], NULL);
+        else
+            rw_worker(&jobs[t]);
+        ok = ok && jobs[t].ok;
+    }
+    free(jobs);
+    free(th);
+    free(started);
+    return ok;
+}

@@ -60,6 +60,8 @@ def test_argument_errors_without_device():
     # NULL-safe calls
     lib.snn_destroy(None)
     assert lib.snn_step(None, 1) == -1
+    assert lib.snn_build_graph(None, None, None, None) == -1
+    assert lib.snn_build_graph_rows(None, None, None, None) == -1
     assert lib.snn_last_error(None) == b""
     assert lib.snn_status_string(-4) == b"overflow"
 

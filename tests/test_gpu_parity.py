@@ -271,6 +271,39 @@ def test_log_overflow_is_reported(gpu):
     net.close()
 
 
+@pytest.mark.parametrize("name", ["vogels_4k", "brunel_stdp"])
+def test_build_graph_rows_equals_per_synapse_weights(gpu, name):
+    """snn_build_graph_rows (one weight per row, Table 2's population-typed
+    synapses) loads the graph snn_build_graph loads from the same weights
+    spread over the synapses: the weights read back, and the raster, V and
+    (with STDP) the weights after a run are the same, and equal the oracle's."""
+    if name == "vogels_4k":
+        prob = si.vogels_4k(seed=4, n_steps=300)
+    else:
+        prob = si.brunel_stdp_100k(seed=2, n_steps=300, n=4000, k=400)
+    o = oracle.run(prob)
+    out = []
+    for rows in (False, True):
+        net = gpu.Network(prob, log_capacity=prob.n * 300, build_graph=False)
+        try:
+            if rows:
+                net.build_graph_rows(prob.row_off, prob.tgt, prob.row_weights())
+            else:
+                net.build_graph(prob.row_off, prob.tgt, prob.w)
+            w0 = net.read("w")
+            net.step(300)
+            steps, ids = net.spikes()
+            out.append((w0, steps, ids, net.read("V"), net.read("w"), net.info()["edge_bytes"]))
+        finally:
+            net.close()
+    (w0a, sa, ia, va, wa, ea), (w0b, sb, ib, vb, wb, eb) = out
+    assert np.array_equal(w0a, prob.w) and np.array_equal(w0b, prob.w)
+    assert np.array_equal(sa, sb) and np.array_equal(ia, ib) and ea == eb
+    assert np.array_equal(va.view(np.uint32), vb.view(np.uint32)) and np.array_equal(wa, wb)
+    assert np.array_equal(sb, o["steps"]) and np.array_equal(ib, o["ids"])
+    assert np.array_equal(wb, o["w"])
+
+
 def test_raster_log_regions(gpu):
     """The raster log keeps each instance's spikes in its own region, its
     share of log_capacity by neurons: step ranges of an uneven batch read back
