@@ -102,7 +102,9 @@ typedef enum {
                               SNN_F_SERIAL leaves the fused and persistent forms out) from the initial
                               state over the same
                               delay + 150 steps (at most 1,100) and times the last 48 with CUDA events;
-                              the fastest is kept (snn_info.tune_ms) and the state returns to N_0.
+                              the fastest is kept (snn_info.tune_ms) and the state returns to N_0.  A
+                              form whose first 32 steps already took twice the best ms/step so far
+                              stops there (tune_ms holds that estimate).
                               Results do not depend on the form.  The bulk form is not a candidate */
 #define SNN_RECV_GLOBAL 1u /* a warp per row piece (rows cut into up to 16 pieces when a step has few
                               spikes), red.global.add into L2-resident accumulators */

@@ -998,12 +998,16 @@ snn_status reset_state(snn_ctx* c)
 // Steps of a tuning run before its timed window, and in it.
 uint32_t tune_warm_steps(const snn_ctx* c) { return std::min<uint32_t>(c->cfg.delay + 150u, 1100u); }
 constexpr uint32_t kTuneSteps = 48;
+constexpr uint32_t kTuneProbe = 32;   // steps after which a clearly slower form is dropped
+constexpr float kTuneAbort = 2.0f;    // ... when its steps took this many times the best so far
 
 // SNN_RECV_AUTO: every form that applies runs from the initial state N_0
 // over the same steps (past the first deliveries), timed with CUDA events
 // over the last kTuneSteps of them; the fastest is kept.  The simulation is
 // deterministic, so every form meets the same spikes; the caller's run
-// starts from N_0 afterwards (init_state).
+// starts from N_0 afterwards (init_state).  The tiled forms go first; a
+// later form whose first kTuneProbe steps already took kTuneAbort times the
+// best ms/step so far stops there (its estimate is what snn_info reports).
 snn_status tune_receive(snn_ctx* c)
 {
     // candidates: (form, persistent grid); the persistent launch twice, with
@@ -1011,7 +1015,6 @@ snn_status tune_receive(snn_ctx* c)
     int cand[kForms + 1];
     uint32_t cgrid[kForms + 1] = {};
     int nc = 0;
-    cand[nc++] = kFormGlobal;
     if (c->rows_sorted && c->tiled_fits) {
         cand[nc++] = kFormTiled;
         c->use_tiled = true;
@@ -1019,6 +1022,7 @@ snn_status tune_receive(snn_ctx* c)
         if (!(c->cfg.flags & SNN_F_SERIAL) && fused_applies(c)) cand[nc++] = kFormFused;
         c->use_tiled = false;
     }
+    cand[nc++] = kFormGlobal;
     if (persist_applies(c) && !(c->cfg.flags & SNN_F_SERIAL) && setup_persistent(c) == SNN_OK) {
         const uint32_t g0 = persist_grid_for(c, true), g1 = persist_grid_for(c, false);
         cand[nc] = kFormPersist;
@@ -1049,7 +1053,24 @@ snn_status tune_receive(snn_ctx* c)
             continue;
         }
         if (st == SNN_OK) st = reset_state(c);
-        if (st == SNN_OK) st = launch(warm);
+        // a form already kTuneAbort times slower than the best so far over its
+        // first kTuneProbe steps is not timed further
+        uint32_t left = warm;
+        if (st == SNN_OK && best >= 0 && kTuneProbe < warm) {
+            float pms = 0.f;
+            if (cudaEventRecord(e0, c->stream) != cudaSuccess) st = fail(c, SNN_E_CUDA, "event record");
+            if (st == SNN_OK) st = launch(kTuneProbe);
+            if (st == SNN_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                 cudaEventElapsedTime(&pms, e0, e1) != cudaSuccess))
+                st = fail(c, SNN_E_CUDA, "tuning probe");
+            if (st == SNN_OK && pms / kTuneProbe > kTuneAbort * best_ms) {
+                const float per = pms / kTuneProbe;
+                if (c->tune_ms[cand[i]] == 0.f || per < c->tune_ms[cand[i]]) c->tune_ms[cand[i]] = per;
+                continue;
+            }
+            left = warm - kTuneProbe;
+        }
+        if (st == SNN_OK) st = launch(left);
         if (st == SNN_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) st = fail(c, SNN_E_CUDA, "event record");
         if (st == SNN_OK) st = launch(kTuneSteps);
         if (st == SNN_OK && cudaEventRecord(e1, c->stream) != cudaSuccess) st = fail(c, SNN_E_CUDA, "event record");
