@@ -27,6 +27,7 @@
 #include "snn_persistent.cuh"
 
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
 
 using namespace snn;
 
@@ -1328,6 +1329,52 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     return SNN_OK;
 }
 
+// The STDP column index (coff, cedge, cpre) of the loaded graph: k_col_count,
+// an exclusive scan, k_col_fill.  Needs the mapped targets and meta.
+snn_status build_columns(snn_ctx* c)
+{
+    const uint32_t Np = c->Np;
+    cudaStream_t s = c->stream;
+    Net n = c->net;
+    n.roff = c->roff;
+    n.tgt = c->tgt;
+    n.meta = c->meta;
+    unsigned long long* cnt = alloc_n<unsigned long long>(c, (size_t)Np + 1);
+    unsigned long long* cur = alloc_n<unsigned long long>(c, (size_t)Np + 1);
+    c->coff = alloc_n<uint64_t>(c, (size_t)Np + 1);
+    void* tmp = nullptr;
+    auto done = [&](snn_status st) {
+        dev_free(c, cnt);
+        dev_free(c, cur);
+        dev_free(c, tmp);
+        return st;
+    };
+    if (!cnt || !cur || !c->coff) return done(fail(c, SNN_E_NOMEM, "STDP column index allocation failed"));
+    const uint32_t grid = (uint32_t)sm_count() * 16;
+    size_t tmp_bytes = 0;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, ((size_t)Np + 1) * 8, s);
+    if (e == cudaSuccess) {
+        k_col_count<<<grid, 256, 0, s>>>(n, cnt);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, cnt, cur, (int64_t)Np + 1, s);
+    if (e == cudaSuccess && !(tmp = dev_alloc(c, std::max<size_t>(tmp_bytes, 16)))) e = cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) e = cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, cnt, cur, (int64_t)Np + 1, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->coff, cur, ((size_t)Np + 1) * 8, cudaMemcpyDeviceToDevice, s);
+    unsigned long long P = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&P, cur + Np, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return done(fail(c, SNN_E_CUDA, "STDP column index: %s", cudaGetErrorString(e)));
+    c->cedge = alloc_n<uint32_t>(c, P ? P : 1);
+    c->cpre = alloc_n<uint32_t>(c, P ? P : 1);
+    if (!c->cedge || !c->cpre) return done(fail(c, SNN_E_NOMEM, "STDP column index allocation failed"));
+    k_col_fill<<<grid, 256, 0, s>>>(n, cur, c->cedge, c->cpre);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return done(fail(c, SNN_E_CUDA, "STDP column index: %s", cudaGetErrorString(e)));
+    return done(SNN_OK);
+}
+
 // snn_build_graph with one weight per edge (w_q) or per row (w_row).
 snn_status build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* tgt_h, const int32_t* w_q,
                        const int32_t* w_row)
@@ -1470,41 +1517,10 @@ snn_status build_graph(snn_ctx* c, const uint64_t* row_off, const uint32_t* tgt_
     }
 
     // STDP column index: plastic in-edges (exc -> exc) of every padded post id
-    // (eager potentiation only; the lazy replay walks rows)
+    // (eager potentiation only; the lazy replay walks rows), built on the device
     if (c->stdp && !c->lazy) {
-        std::vector<uint64_t> hcoff((size_t)Np + 1, 0);
-        for (uint32_t b = 0; b < c->cfg.n_inst; ++b)
-            for (uint32_t jl = 0; jl < c->params[b].n_exc; ++jl) {
-                const uint32_t j = c->g_off[b] + jl;
-                for (uint64_t e = row_off[j]; e < row_off[j + 1]; ++e) {
-                    const uint32_t il = tgt_h[e] - c->g_off[b];
-                    if (il < c->params[b].n_exc) hcoff[c->pbase[b] + il + 1]++;
-                }
-            }
-        for (uint32_t i = 0; i < Np; ++i) hcoff[i + 1] += hcoff[i];
-        const uint64_t P = hcoff[Np];
-        std::vector<uint32_t> hce(P ? P : 1), hcp(P ? P : 1);
-        std::vector<uint64_t> fill(hcoff.begin(), hcoff.end() - 1);
-        for (uint32_t b = 0; b < c->cfg.n_inst; ++b)
-            for (uint32_t jl = 0; jl < c->params[b].n_exc; ++jl) {
-                const uint32_t j = c->g_off[b] + jl;
-                for (uint64_t e = row_off[j]; e < row_off[j + 1]; ++e) {
-                    const uint32_t il = tgt_h[e] - c->g_off[b];
-                    if (il < c->params[b].n_exc) {
-                        const uint64_t k = fill[c->pbase[b] + il]++;
-                        hce[k] = (uint32_t)e;
-                        hcp[k] = c->pbase[b] + jl;
-                    }
-                }
-            }
-        c->coff = alloc_n<uint64_t>(c, (size_t)Np + 1);
-        c->cedge = alloc_n<uint32_t>(c, P);
-        c->cpre = alloc_n<uint32_t>(c, P);
-        if (!c->coff || !c->cedge || !c->cpre) return fail(c, SNN_E_NOMEM, "STDP column index allocation failed");
-        CUDA_TRY(c, cudaMemcpyAsync(c->coff, hcoff.data(), hcoff.size() * 8, cudaMemcpyHostToDevice, s));
-        CUDA_TRY(c, cudaMemcpyAsync(c->cedge, hce.data(), P * 4, cudaMemcpyHostToDevice, s));
-        CUDA_TRY(c, cudaMemcpyAsync(c->cpre, hcp.data(), P * 4, cudaMemcpyHostToDevice, s));
-        CUDA_TRY(c, cudaStreamSynchronize(s));
+        snn_status cs = build_columns(c);
+        if (cs != SNN_OK) return cs;
     }
 
     c->rinfo = alloc_n<uint4>(c, Np);

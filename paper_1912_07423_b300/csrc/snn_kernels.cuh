@@ -918,6 +918,51 @@ __global__ void k_init_state(Net n, int vogels, int stdp, int lazy)
 // they stay inside the source's instance), picks the row's weight shift and
 // writes the stored weights.
 // ---------------------------------------------------------------------------
+// STDP column index (eager potentiation): the plastic (exc -> exc) in-edges
+// of every padded post id, as a counting sort on the device.  k_col_count
+// counts them per post id (cnt[Np], zeroed), an exclusive scan of cnt gives
+// the column offsets, k_col_fill files each edge (its index, its padded
+// source) at its post id's next slot (cur: a copy of the offsets).  The
+// order inside a column is the order the atomics hand out; potentiation
+// updates every edge of a column on its own, so results do not depend on it.
+// A warp per row; tgt holds padded ids, meta bit 6 marks an excitatory source.
+__global__ void k_col_count(Net n, unsigned long long* __restrict__ cnt)
+{
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t pj = warp; pj < n.Np; pj += nwarps) {
+        if (!(n.meta[pj] & 0x40u)) continue;
+        const InstDev& I = n.inst[n.inst_of_w32[pj >> 5]];
+        const uint32_t pb = I.pbase, ne = I.n_exc;
+        for (uint64_t e = n.roff[pj] + lane; e < n.roff[pj + 1]; e += 32) {
+            const uint32_t i = n.tgt[e];
+            if (i - pb < ne) atomicAdd(cnt + i, 1ull);
+        }
+    }
+}
+
+__global__ void k_col_fill(Net n, unsigned long long* __restrict__ cur, uint32_t* __restrict__ cedge,
+                           uint32_t* __restrict__ cpre)
+{
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t pj = warp; pj < n.Np; pj += nwarps) {
+        if (!(n.meta[pj] & 0x40u)) continue;
+        const InstDev& I = n.inst[n.inst_of_w32[pj >> 5]];
+        const uint32_t pb = I.pbase, ne = I.n_exc;
+        for (uint64_t e = n.roff[pj] + lane; e < n.roff[pj + 1]; e += 32) {
+            const uint32_t i = n.tgt[e];
+            if (i - pb < ne) {
+                const unsigned long long k = atomicAdd(cur + i, 1ull);
+                cedge[k] = (uint32_t)e;
+                cpre[k] = pj;
+            }
+        }
+    }
+}
+
 // One weight per row spread over the row's edges: w[e] = w_row[row_src[pj]]
 // for the edges e of padded row pj (row_src: the global id of a padded
 // row, ~0 for padding, whose rows are empty).  A warp per row.
