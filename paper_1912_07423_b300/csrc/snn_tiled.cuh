@@ -589,6 +589,8 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledCtasPerSm) k_receive_tile
         // which reads them out before they are cleared
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
+        // the CTA's last item (no next one taken): its accumulators need no
+        // clearing, and the copy is waited for once, before the CTA exits
         {  // warp w copies out and clears slice w of the CH * len words (1/16 of a
            // channel or more: slices are multiples of 16 words, inside one channel)
             const uint32_t nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5;
@@ -601,11 +603,13 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledCtasPerSm) k_receive_tile
                 const uint32_t ch = CH == 2 && w0 >= T.len ? 1u : 0u;
                 bulk_out((ch ? n.acc1 : n.acc0) + T.lo + (w0 - ch * T.len), acc_s + w0, per * 4u, I.P > 1);
                 asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                if (s_ok[b ^ 1u]) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
             }
-            __syncwarp();
-            for (uint32_t i = lane; i < per / 4; i += 32)
-                reinterpret_cast<int4*>(acc_s + w0)[i] = make_int4(0, 0, 0, 0);
+            if (s_ok[b ^ 1u]) {
+                __syncwarp();
+                for (uint32_t i = lane; i < per / 4; i += 32)
+                    reinterpret_cast<int4*>(acc_s + w0)[i] = make_int4(0, 0, 0, 0);
+            }
         }
         __syncthreads();
     }
