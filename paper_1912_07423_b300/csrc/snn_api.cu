@@ -71,6 +71,7 @@ struct snn_ctx {
     bool rows_sorted = true;
     InstDev* inst = nullptr;
     uint32_t* inst_of_w32 = nullptr;
+    uint4* wdesc = nullptr;
     uint32_t* pois = nullptr;
     uint8_t* pois_start = nullptr;
     uint64_t* roff = nullptr;
@@ -1232,8 +1233,12 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
         }
     }
     std::vector<uint32_t> hmap(c->Np / 32, 0);
+    std::vector<uint4> hdesc(c->Np / 32);
     for (uint32_t b = 0; b < cfg->n_inst; ++b)
-        for (uint32_t w = c->pbase[b] / 32; w < c->pbase[b + 1] / 32; ++w) hmap[w] = b;
+        for (uint32_t w = c->pbase[b] / 32; w < c->pbase[b + 1] / 32; ++w) {
+            hmap[w] = b;
+            hdesc[w] = make_uint4(b, c->pbase[b], params[b].n, 0u);
+        }
 
     const size_t Npz = c->Np;
     Net& n = c->net;
@@ -1253,13 +1258,14 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     c->ctl = alloc_n<Ctl>(c, 1);
     c->inst = alloc_n<InstDev>(c, cfg->n_inst);
     c->inst_of_w32 = alloc_n<uint32_t>(c, Npz / 32);
+    c->wdesc = alloc_n<uint4>(c, Npz / 32);
     c->pois = alloc_n<uint32_t>(c, hpois.size());
     c->pois_start = alloc_n<uint8_t>(c, hstart.size());
     n.V = alloc_n<float>(c, Npz);
     n.r = alloc_n<uint8_t>(c, Npz);
     n.acc0 = alloc_n<int32_t>(c, Npz);
     n.q = alloc_n<uint32_t>(c, (size_t)c->D * Npz);
-    bool ok = c->ctl && c->inst && c->inst_of_w32 && c->pois && c->pois_start && n.V && n.r && n.acc0 && n.q && n.icount && n.ilog &&
+    bool ok = c->ctl && c->inst && c->inst_of_w32 && c->wdesc && c->pois && c->pois_start && n.V && n.r && n.acc0 && n.q && n.icount && n.ilog &&
               n.inst_spikes && n.tile_ctr;
     if (c->generic) {
         c->mstate = dev_alloc(c, c->mbytes * Npz);
@@ -1309,11 +1315,14 @@ snn_status snn_create(const snn_config* cfg, const snn_params* params, const snn
     n.ctl = c->ctl;
     n.inst = c->inst;
     n.inst_of_w32 = c->inst_of_w32;
+    n.wdesc = c->wdesc;
     n.pois = c->pois;
     n.pois_start = c->pois_start;
     cudaError_t e = cudaMemcpyAsync(c->inst, hinst.data(), hinst.size() * sizeof(InstDev), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->inst_of_w32, hmap.data(), hmap.size() * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->wdesc, hdesc.data(), hdesc.size() * sizeof(uint4), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->pois, hpois.data(), hpois.size() * 4, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)

@@ -92,6 +92,7 @@ struct Net {
     unsigned int* tile_ctr;    // tiled receive: next tile to take, at [t & 1]
     const InstDev* inst;
     const uint32_t* inst_of_w32;  // instance of each 32-neuron word
+    const uint4* wdesc;           // per 32-neuron word: instance, its pbase, its n (the update's first load)
     const uint32_t* pois;         // Poisson thresholds, kPoissonCap per instance
     const uint8_t* pois_start;    // per instance kPoissonBuckets counts: thresholds < h 2^24
     float* V;

@@ -151,12 +151,15 @@ __device__ __forceinline__ void update_neurons(const Net& n, unsigned long long 
             *reinterpret_cast<int4*>(a0 + 4 * h) = *reinterpret_cast<const int4*>(acc0 + id0 + 4 * h);
         }
     }
-    const uint32_t b = active ? __ldg(n.inst_of_w32 + (id0 >> 5)) : 0u;  // uniform across the warp
+    // the word's instance, its base and size in one load (uniform across the
+    // warp), so the Philox block can start while the instance's constants load
+    const uint4 wd = active ? __ldg(n.wdesc + (id0 >> 5)) : make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t b = wd.x;
     const InstDev* I = n.inst + b;
-    const uint32_t pbase = active ? __ldg(&I->pbase) : 0u;
+    const uint32_t pbase = wd.y;
 
     if (active) {
-        const uint32_t nloc = __ldg(&I->n);
+        const uint32_t nloc = wd.z;
         const uint32_t local0 = id0 - pbase;
         if (local0 < nloc) {
             const float v_th = __ldg(&I->v_th), v_reset = __ldg(&I->v_reset), Pm = __ldg(&I->Pm);
@@ -393,7 +396,7 @@ __device__ __forceinline__ void update_neurons(const Net& n, unsigned long long 
 }
 
 template <int MODEL, int SYN, bool STATS, int NPT>
-__global__ void __launch_bounds__(256) k_update(Net n)
+__global__ void __launch_bounds__(256, (MODEL == 1 && SYN == 0) ? 5 : 1) k_update(Net n)
 {
     const unsigned long long t = n.ctl->t + n.k;
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
