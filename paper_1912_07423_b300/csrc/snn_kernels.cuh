@@ -57,6 +57,14 @@ __device__ __forceinline__ unsigned long long log_base(const Net& n, unsigned lo
     return n.ilog[(size_t)((t - 1) & 1ull) * n.n_inst + b] + n.icount[(size_t)((t - 1) & (n.cr - 1)) * n.n_inst + b];
 }
 
+// poisson_count on tables in shared memory.
+__device__ __forceinline__ uint32_t poisson_count_s(const uint32_t* T, const uint8_t* S, uint32_t nT, uint32_t u)
+{
+    uint32_t k = S[u >> 24];
+    while (k < nT && T[k] <= u) ++k;
+    return k;
+}
+
 // Per-step bookkeeping of the previous step, done once per step by the
 // threads gt (grid-wide index) of the step's update (its kernels have
 // finished): fold its queue indices into the counters, clear the next step's
@@ -128,7 +136,7 @@ __device__ __forceinline__ void file_spikes(const Net& n, unsigned long long t, 
 // the step's update advances neurons g*NPT .. g*NPT+NPT-1 (whole warps: a
 // warp covers 32*NPT slots inside one instance); acc0 is the channel-0 input
 // it reads and clears.
-template <int MODEL, int SYN, bool STATS, int NPT>
+template <int MODEL, int SYN, bool STATS, int NPT, bool SPOIS = false>
 __device__ __forceinline__ void update_neurons(const Net& n, unsigned long long t, uint32_t g, int32_t* acc0)
 {
     static_assert(NPT == 4 || NPT == 8, "one Philox block serves 8 neurons");
@@ -157,6 +165,24 @@ __device__ __forceinline__ void update_neurons(const Net& n, unsigned long long 
     const uint32_t b = wd.x;
     const InstDev* I = n.inst + b;
     const uint32_t pbase = wd.y;
+    // SPOIS (blocks of at most 8 warps): the warp copies its instance's Poisson
+    // tables (64 thresholds, 256 bucket counts: 512 bytes) into shared memory
+    // while its Philox block is drawn, so the draws' lookups are shared-memory
+    // loads (the instance's thresholds sit at pois + kPoissonCap b)
+    const uint32_t* Ts = nullptr;
+    const uint8_t* Ss = nullptr;
+    if constexpr (SPOIS && MODEL == 1) {
+        static_assert(kPoissonCap == 64 && kPoissonBuckets == 256, "one 16-byte vector per lane");
+        __shared__ uint4 s_pois[8][32];
+        const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+        if (active)  // whole warps
+            s_pois[warp][lane] = lane < 16 ? __ldg(reinterpret_cast<const uint4*>(n.pois + (size_t)b * kPoissonCap) + lane)
+                                           : __ldg(reinterpret_cast<const uint4*>(n.pois_start + (size_t)b * kPoissonBuckets) +
+                                                   (lane - 16));
+        __syncwarp();
+        Ts = reinterpret_cast<const uint32_t*>(&s_pois[warp][0]);
+        Ss = reinterpret_cast<const uint8_t*>(&s_pois[warp][16]);
+    }
 
     if (active) {
         const uint32_t nloc = wd.z;
@@ -224,7 +250,8 @@ __device__ __forceinline__ void update_neurons(const Net& n, unsigned long long 
                         rk -= 1;
                         v = v_reset;
                     } else {
-                        const uint32_t next = poisson_count(T, S, nT, words[(wofs + k) & 7u]);
+                        const uint32_t next = SPOIS ? poisson_count_s(Ts, Ss, nT, words[(wofs + k) & 7u])
+                                                    : poisson_count(T, S, nT, words[(wofs + k) & 7u]);
                         const int32_t in = a0[k] + (int32_t)next * jext;
                         v = __fadd_rn(__fmul_rn(v, Pm), __fmul_rn(__int2float_rn(in), kLattice));
                         if (v >= v_th) {
@@ -404,7 +431,7 @@ __global__ void __launch_bounds__(256, (MODEL == 1 && SYN == 0) ? 5 : 1) k_updat
     // a receive launched as this kernel's programmatic dependent may start
     // (it waits for this kernel before touching what it writes)
     if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    update_neurons<MODEL, SYN, STATS, NPT>(n, t, g, n.acc0);
+    update_neurons<MODEL, SYN, STATS, NPT, true>(n, t, g, n.acc0);
 }
 
 // Raster readout: chunks of instances' log regions (a chunk: len entries
